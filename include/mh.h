@@ -1,0 +1,149 @@
+/*
+ * mh.h -- C ABI of the GB300 multi-hit weighted-set-cover library (libmh).
+ *
+ * The library finds multi-hit gene combinations with the greedy weighted set
+ * cover of Dash et al. as used by the paper (Algorithm 1), whose argmax step is
+ * evaluated by Pruned Depth-First Search (P-DFS, §III-D, Algorithm 2) over
+ * bit-packed gene x sample mutation bitmaps.  All arithmetic is exact integer
+ * arithmetic; every step of a solve runs in the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns MH_OK (0) or one of the MH_E* codes below; a
+ *     readable message for the calling thread is available from mh_last_error().
+ *     No entry point exits, traps or aborts the process.
+ *   - Bitmap layout ("packed rows"): gene-major, one row per gene,
+ *       row g = [Wt tumor words | Wn normal words],  Wt = ceil(Nt/64), Wn = ceil(Nn/64),
+ *     as uint64_t; sample s of a block is bit (s % 64) of word (s / 64), least
+ *     significant bit first; bits at and past Nt (resp. Nn) must be zero.
+ *     Bit x[g][s] = 1 means sample s carries a mutation in gene g (§II-B).
+ *   - Gene indices in results are the caller's row indices ("original" indices),
+ *     ascending inside each combination.
+ *   - Limits: 1 <= G <= 65535, 0 <= Nt <= 2048, 0 <= Nn <= 2048, 1 <= h <= 9.
+ *   - Streams: a handle runs all its work on one CUDA stream (the legacy default
+ *     stream unless one is given).  Handles are not thread-safe; distinct handles
+ *     may be used from distinct threads.
+ */
+#ifndef MH_H
+#define MH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MH_API __attribute__((visibility("default")))
+#else
+#define MH_API
+#endif
+
+/* status codes */
+#define MH_OK 0
+#define MH_EINVAL 1   /* bad argument: sizes out of range, h outside [1, 9], den <= 0, non-zero padding bits */
+#define MH_ENOMEM 2   /* a host or device allocation failed, or the frontier budget was exceeded */
+#define MH_ECUDA 3    /* a CUDA runtime call failed (the message names it) */
+#define MH_ETIMEOUT 4 /* a bounded device-side wait expired; the kernel returned early */
+#define MH_EAGAIN 5   /* the result is not ready yet (served mode) */
+#define MH_EREJECT 6  /* a request does not fit the server's memory budget */
+
+#define MH_MAX_H 9
+
+typedef struct mh_handle mh_handle;
+
+/* alpha = num / den of the weight function F (§II-B; "often set to 0.1", i.e. {1, 10}).
+ * Requires 0 <= num and 0 < den, both below 2^31. */
+typedef struct {
+    int32_t num;
+    int32_t den;
+} mh_rational;
+
+/* Pruning mode of the search.
+ *   MH_PRUNE_PAPER: cut every prefix whose tumor intersection with the still
+ *                   uncovered tumors is empty, at every depth (§III-D).
+ *   MH_PRUNE_OFF:   exhaustive enumeration of every h-subset (the paper's
+ *                   BOUND=OFF baseline); the result is identical, the counters
+ *                   are the closed forms C(G-h+l, l). */
+#define MH_PRUNE_PAPER 0
+#define MH_PRUNE_OFF 1
+
+/* Options of a solve; zero-initialise and set what you need. */
+typedef struct {
+    int32_t h;            /* hits per combination, 1..9 */
+    mh_rational alpha;    /* weight of true positives */
+    int32_t prune;        /* MH_PRUNE_PAPER (default 0) or MH_PRUNE_OFF */
+    int32_t max_rounds;   /* stop after this many greedy rounds; <= 0 means no limit */
+    int32_t time_kernels; /* non-zero: time every leaf-kernel launch with CUDA events */
+} mh_solve_opts;
+
+/* Result of a solve, allocated by the library; release with mh_result_free.
+ * Round r of the greedy loop searched the tree once; visited[r*h + l-1] counts the
+ * depth-l nodes whose intersection was computed, pruned[r*h + l-1] those found
+ * empty (scored leaves = visited - pruned at l = h).  rounds = k, or k + 1 when
+ * the last round found no combination covering an uncovered tumor. */
+typedef struct {
+    int32_t h;
+    int32_t k;           /* number of selected combinations */
+    int32_t rounds;      /* greedy rounds searched */
+    int32_t *genes;      /* k*h original gene indices, ascending per combination */
+    int32_t *tp;         /* k: uncovered tumors covered when selected */
+    int32_t *fp;         /* k: normals covered */
+    uint64_t *visited;   /* rounds*h */
+    uint64_t *pruned;    /* rounds*h */
+    double solve_ms;     /* wall time of the solve measured with CUDA events on the handle's stream */
+    double leaf_ms;      /* sum of leaf-kernel durations (CUDA events), if time_kernels */
+    int64_t leaf_launches;   /* leaf-kernel launches in this solve */
+    int64_t kernel_launches; /* all kernel launches of this solve */
+    uint64_t leaf_words;     /* 64-bit column words OR-ed by the leaf kernel (sibling tests) */
+    uint64_t leaf_prefixes;  /* prefixes (depth h-1 nodes) the leaf kernel expanded */
+} mh_result;
+
+/* Create a handle for one cohort from packed rows in HOST memory.
+ * bitmaps: G * (Wt + Wn) uint64_t words (see layout above); copied, the caller
+ * keeps ownership.  The library sorts genes from most to least sparse (§III-C,
+ * ascending tumor mutation count, ties by row index), uploads the sorted rows and
+ * a sample-major copy of the tumor bits, and owns that device memory until
+ * mh_destroy.  Errors: MH_EINVAL (NULL pointers, sizes out of range, padding bits
+ * set), MH_ENOMEM, MH_ECUDA.  On error *out is set to NULL. */
+MH_API int mh_create(const uint64_t *bitmaps, int32_t G, int32_t Nt, int32_t Nn, mh_handle **out);
+
+/* Same as mh_create, with the packed rows in DEVICE memory (e.g. a torch tensor's
+ * data pointer) and the CUDA stream (a cudaStream_t, or NULL for the legacy
+ * default stream) that the handle will use.  The rows are read once, during this
+ * call; the caller keeps ownership. */
+MH_API int mh_create_device(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, int32_t Nn, void *stream,
+                            mh_handle **out);
+
+/* Select the CUDA stream (cudaStream_t or NULL) used by later calls on the handle. */
+MH_API int mh_set_stream(mh_handle *handle, void *stream);
+
+/* Run the greedy loop (Algorithm 1) to completion: every round evaluates
+ * argmax_gamma F(gamma) by P-DFS on the device, appends the winner and clears the
+ * tumors it covers, until every tumor is covered or no h-combination covers an
+ * uncovered tumor.  Scores are compared as the integers
+ *   S = alpha.num * TP + alpha.den * (Nn - FP)
+ * (F scaled by alpha.den * (Nt + Nn)); equal scores go to the lexicographically
+ * smallest tuple of original indices.  Synchronous: returns when the result is on
+ * the host.  Each call starts from "no tumor covered".  *out receives a result to
+ * release with mh_result_free.  Errors: MH_EINVAL, MH_ENOMEM, MH_ECUDA,
+ * MH_ETIMEOUT. */
+MH_API int mh_solve(mh_handle *handle, int32_t h, mh_rational alpha, mh_result **out);
+
+/* mh_solve with options (pruning mode, round limit, kernel timing). */
+MH_API int mh_solve_ex(mh_handle *handle, const mh_solve_opts *opts, mh_result **out);
+
+MH_API void mh_result_free(mh_result *result);
+MH_API void mh_destroy(mh_handle *handle);
+
+/* Message of the last error on the calling thread ("" if none). */
+MH_API const char *mh_last_error(void);
+
+/* Cohort dimensions of a handle (any pointer may be NULL). */
+MH_API int mh_handle_info(const mh_handle *handle, int32_t *G, int32_t *Nt, int32_t *Nn,
+                          int64_t *device_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MH_H */

@@ -1,0 +1,490 @@
+// Host runtime and C ABI of libmh (declared in include/mh.h).
+//
+// mh_create packs one cohort for the device (sparsity sort of §III-C, padded
+// gene-major rows, sample-major tumor copy).  mh_solve runs the greedy loop of
+// Algorithm 1; each round is a fixed sequence of kernel launches on the
+// handle's stream (depth 1, depths 2..h-1, leaves, finalize) and one 16-byte
+// read-back of the round state.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mh.h"
+#include "mh_internal.h"
+
+using namespace mh;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define MH_CUDA(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? MH_ENOMEM : MH_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+    } while (0)
+
+constexpr size_t kFrontierBudgetDefault = size_t(16) << 30;  // bytes for all frontiers of a handle
+
+size_t frontier_budget()
+{
+    const char *v = getenv("MH_FRONTIER_BUDGET_MB");
+    if (v && *v) {
+        const long long mb = atoll(v);
+        if (mb > 0) return size_t(mb) << 20;
+    }
+    return kFrontierBudgetDefault;
+}
+
+template <typename T>
+int dalloc(T **p, size_t n, int64_t *acct)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    MH_CUDA(cudaMalloc((void **)p, n * sizeof(T)));
+    if (acct) *acct += (int64_t)(n * sizeof(T));
+    return MH_OK;
+}
+
+}  // namespace
+
+struct mh_handle {
+    int G = 0, Nt = 0, Nn = 0;
+    Cohort c{};
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int64_t device_bytes = 0;
+    // cohort store
+    u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr;
+    u16 *dOrig = nullptr;
+    u32 *dInv = nullptr;
+    // solve workspace (grown on demand)
+    int ws_h = 0, ws_rounds = 0, ws_slots = 0;
+    u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr;
+    int *dState = nullptr, *dRes = nullptr;
+    Key *dSlots = nullptr;
+    u32 *dCounts = nullptr;               // frontier sizes, one per depth
+    Prefix *dF[kMaxH] = {};               // frontier of depth l at index l
+    u32 cap[kMaxH] = {};
+    int *hState = nullptr;                // pinned: state + frontier counts
+    int64_t frontier_bytes = 0;
+
+    ~mh_handle()
+    {
+        cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dOrig); cudaFree(dInv);
+        cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
+        cudaFree(dSlots); cudaFree(dCounts);
+        for (int l = 0; l < kMaxH; ++l) cudaFree(dF[l]);
+        if (hState) cudaFreeHost(hState);
+    }
+};
+
+namespace {
+
+int popcount_words(const uint64_t *w, int n)
+{
+    int c = 0;
+    for (int i = 0; i < n; ++i) c += __builtin_popcountll(w[i]);
+    return c;
+}
+
+int validate_dims(int32_t G, int32_t Nt, int32_t Nn)
+{
+    if (G < 1 || G > kMaxGenes) return fail(MH_EINVAL, "G=%d outside [1, %d]", G, kMaxGenes);
+    if (Nt < 0 || Nt > kMaxSamples) return fail(MH_EINVAL, "Nt=%d outside [0, %d]", Nt, kMaxSamples);
+    if (Nn < 0 || Nn > kMaxWords * 64) return fail(MH_EINVAL, "Nn=%d outside [0, %d]", Nn, kMaxWords * 64);
+    return MH_OK;
+}
+
+// Builds the device store from host rows (already validated).
+int build_store(mh_handle *H, const uint64_t *bm)
+{
+    const int G = H->G, Nt = H->Nt, Nn = H->Nn;
+    const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64, W = Wt + Wn;
+    for (int g = 0; g < G; ++g) {
+        const uint64_t *row = bm + (size_t)g * W;
+        if (Nt % 64 && Wt && (row[Wt - 1] >> (Nt % 64)))
+            return fail(MH_EINVAL, "gene %d: tumor padding bits past Nt=%d are set", g, Nt);
+        if (Nn % 64 && Wn && (row[Wt + Wn - 1] >> (Nn % 64)))
+            return fail(MH_EINVAL, "gene %d: normal padding bits past Nn=%d are set", g, Nn);
+    }
+    // search order: ascending tumor mutation count, ties by original index (§III-C)
+    std::vector<int> order(G);
+    std::vector<int> pc(G);
+    for (int g = 0; g < G; ++g) {
+        order[g] = g;
+        pc[g] = popcount_words(bm + (size_t)g * W, Wt);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pc[a] < pc[b]; });
+
+    Cohort &c = H->c;
+    c.G = G; c.Nt = Nt; c.Nn = Nn; c.Wt = Wt; c.Wn = Wn;
+    c.WTp = std::max(2, (Wt + 1) & ~1);
+    c.WNp = std::max(2, (Wn + 1) & ~1);
+    c.GW = std::max(2, (((G + 63) / 64) + 1) & ~1);
+
+    std::vector<u64> T((size_t)G * c.WTp, 0), N((size_t)G * c.WNp, 0);
+    std::vector<u16> orig(G);
+    std::vector<u32> inv(G);
+    for (int i = 0; i < G; ++i) {
+        const int g = order[i];
+        const uint64_t *row = bm + (size_t)g * W;
+        for (int w = 0; w < Wt; ++w) T[(size_t)i * c.WTp + w] = row[w];
+        for (int w = 0; w < Wn; ++w) N[(size_t)i * c.WNp + w] = row[Wt + w];
+        orig[i] = (u16)g;
+        inv[g] = (u32)i;
+    }
+    int rc;
+    if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes))) return rc;
+    if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes))) return rc;
+    if ((rc = dalloc(&H->dCT, (size_t)Nt * c.GW, &H->device_bytes))) return rc;
+    if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes))) return rc;
+    if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes))) return rc;
+    MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
+    MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
+    MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, H->stream));
+    MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, H->stream));
+    c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.orig = H->dOrig; c.inv = H->dInv;
+    launch_transpose(c, H->dCT, H->stream);
+    MH_CUDA(cudaGetLastError());
+    MH_CUDA(cudaStreamSynchronize(H->stream));  // host vectors go out of scope
+    return MH_OK;
+}
+
+int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStream_t stream, mh_handle **out)
+{
+    mh_handle *H = new (std::nothrow) mh_handle();
+    if (!H) return fail(MH_ENOMEM, "host allocation of the handle failed");
+    H->G = G; H->Nt = Nt; H->Nn = Nn;
+    H->stream = stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete H;
+        return fail(MH_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    int rc = build_store(H, bm);
+    if (rc) {
+        delete H;
+        return rc;
+    }
+    *out = H;
+    return MH_OK;
+}
+
+// Grows the frontier of depth l to hold at least n entries (within the budget).
+int ensure_frontier(mh_handle *H, int l, u64 n)
+{
+    if (n <= H->cap[l]) return MH_OK;
+    u64 want = std::max<u64>(n + n / 4, 1u << 16);
+    if (want > 0xffffffffull) want = 0xffffffffull;
+    const int64_t old_bytes = (int64_t)H->cap[l] * (int64_t)sizeof(Prefix);
+    const int64_t new_bytes = (int64_t)want * (int64_t)sizeof(Prefix);
+    if ((size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget() || n > 0xffffffffull)
+        return fail(MH_ENOMEM, "depth-%d frontier needs %llu entries (%.1f GB), above the frontier budget", l,
+                    (unsigned long long)n, (double)n * sizeof(Prefix) / 1e9);
+    MH_CUDA(cudaStreamSynchronize(H->stream));
+    cudaFree(H->dF[l]);
+    H->dF[l] = nullptr;
+    H->frontier_bytes -= old_bytes;
+    H->device_bytes -= old_bytes;
+    H->cap[l] = 0;
+    int rc = dalloc(&H->dF[l], (size_t)want, &H->device_bytes);
+    if (rc) return rc;
+    H->cap[l] = (u32)want;
+    H->frontier_bytes += new_bytes;
+    return MH_OK;
+}
+
+int leaf_grid(const mh_handle *H) { return std::max(1, H->num_sms * 4); }
+
+int ensure_workspace(mh_handle *H, int h)
+{
+    const int rounds = H->Nt + 2;
+    const int slots = std::max(level1_grid(H->c), leaf_grid(H));
+    int rc;
+    if (!H->dU) {
+        if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dState, 4, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dWork, 2, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dCounts, (size_t)kMaxH, &H->device_bytes))) return rc;
+        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (4 + kMaxH)));
+    }
+    if (h > H->ws_h || rounds > H->ws_rounds) {
+        cudaFree(H->dCnt);
+        cudaFree(H->dRes);
+        H->dCnt = nullptr;
+        H->dRes = nullptr;
+        const int hh = std::max(h, H->ws_h);
+        if ((rc = dalloc(&H->dCnt, (size_t)rounds * hh * 2, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dRes, (size_t)rounds * (hh + 2), &H->device_bytes))) return rc;
+        H->ws_h = hh;
+        H->ws_rounds = rounds;
+    }
+    if (slots > H->ws_slots) {
+        cudaFree(H->dSlots);
+        H->dSlots = nullptr;
+        if ((rc = dalloc(&H->dSlots, (size_t)slots, &H->device_bytes))) return rc;
+        H->ws_slots = slots;
+    }
+    if ((rc = ensure_frontier(H, 1, (u64)H->G))) return rc;
+    for (int l = 2; l < h; ++l)
+        if ((rc = ensure_frontier(H, l, 1))) return rc;
+    return MH_OK;
+}
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace
+
+extern "C" {
+
+MH_API const char *mh_last_error(void) { return g_last_error.c_str(); }
+
+MH_API int mh_create(const uint64_t *bitmaps, int32_t G, int32_t Nt, int32_t Nn, mh_handle **out)
+{
+    if (!out) return fail(MH_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_dims(G, Nt, Nn);
+    if (rc) return rc;
+    if (!bitmaps) return fail(MH_EINVAL, "bitmaps is NULL");
+    return create_common(bitmaps, G, Nt, Nn, nullptr, out);
+}
+
+MH_API int mh_create_device(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, int32_t Nn, void *stream,
+                            mh_handle **out)
+{
+    if (!out) return fail(MH_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_dims(G, Nt, Nn);
+    if (rc) return rc;
+    if (!d_bitmaps) return fail(MH_EINVAL, "d_bitmaps is NULL");
+    const size_t words = (size_t)G * (size_t)((Nt + 63) / 64 + (Nn + 63) / 64);
+    std::vector<uint64_t> host(words);
+    cudaStream_t st = (cudaStream_t)stream;
+    MH_CUDA(cudaMemcpyAsync(host.data(), d_bitmaps, words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    return create_common(host.data(), G, Nt, Nn, st, out);
+}
+
+MH_API int mh_set_stream(mh_handle *H, void *stream)
+{
+    if (!H) return fail(MH_EINVAL, "handle is NULL");
+    H->stream = (cudaStream_t)stream;
+    return MH_OK;
+}
+
+MH_API int mh_handle_info(const mh_handle *H, int32_t *G, int32_t *Nt, int32_t *Nn, int64_t *device_bytes)
+{
+    if (!H) return fail(MH_EINVAL, "handle is NULL");
+    if (G) *G = H->G;
+    if (Nt) *Nt = H->Nt;
+    if (Nn) *Nn = H->Nn;
+    if (device_bytes) *device_bytes = H->device_bytes;
+    return MH_OK;
+}
+
+MH_API void mh_destroy(mh_handle *H)
+{
+    if (!H) return;
+    if (H->stream) cudaStreamSynchronize(H->stream);
+    else cudaDeviceSynchronize();
+    delete H;
+}
+
+MH_API void mh_result_free(mh_result *r)
+{
+    if (!r) return;
+    free(r->genes);
+    free(r->tp);
+    free(r->fp);
+    free(r->visited);
+    free(r->pruned);
+    free(r);
+}
+
+MH_API int mh_solve(mh_handle *H, int32_t h, mh_rational alpha, mh_result **out)
+{
+    mh_solve_opts o;
+    memset(&o, 0, sizeof o);
+    o.h = h;
+    o.alpha = alpha;
+    return mh_solve_ex(H, &o, out);
+}
+
+MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
+{
+    if (!out) return fail(MH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!H || !opts) return fail(MH_EINVAL, "handle or opts is NULL");
+    const int h = opts->h;
+    if (h < 1 || h > kMaxH) return fail(MH_EINVAL, "h=%d outside [1, %d]", h, kMaxH);
+    if (opts->alpha.num < 0 || opts->alpha.den <= 0)
+        return fail(MH_EINVAL, "alpha=%d/%d: need num >= 0 and den > 0", opts->alpha.num, opts->alpha.den);
+    if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
+        return fail(MH_EINVAL, "prune=%d is not a pruning mode", opts->prune);
+    int rc = ensure_workspace(H, h);
+    if (rc) return rc;
+    cudaStream_t st = H->stream;
+    const Cohort &c = H->c;
+    Solve s;
+    s.h = h;
+    s.prune = opts->prune;
+    s.a_num = (u64)opts->alpha.num;
+    s.a_den = (u64)opts->alpha.den;
+    s.U = H->dU;
+    s.state = H->dState;
+    s.res = H->dRes;
+    s.cnt = H->dCnt;
+    s.slots = H->dSlots;
+    s.nslots = H->ws_slots;
+    s.work = H->dWork;
+    int max_rounds = H->Nt + 1;
+    if (opts->max_rounds > 0) max_rounds = std::min(max_rounds, (int)opts->max_rounds);
+
+    EventPair total;
+    MH_CUDA(cudaEventCreate(&total.a));
+    MH_CUDA(cudaEventCreate(&total.b));
+    std::vector<EventPair> leaf_ev;
+    int64_t launches = 0, leaf_launches = 0;
+    const int grid = leaf_grid(H);
+
+    MH_CUDA(cudaEventRecord(total.a, st));
+    launch_solve_init(c, s, H->ws_rounds, st);
+    ++launches;
+    int rounds = 0;
+    bool done = H->Nt == 0;  // every tumor covered from the start
+    while (!done && rounds < max_rounds) {
+        const int r = rounds;
+        MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kMaxH, st));
+        launch_level1(c, s, r, H->dF[1], H->dCounts + 1, H->cap[1], st);
+        ++launches;
+        for (int l = 2; l <= h - 1; ++l) {
+            for (;;) {
+                launch_expand(c, s, r, l, H->dF[l - 1], H->dCounts + (l - 1), H->dF[l], H->dCounts + l,
+                              H->cap[l], grid, st);
+                ++launches;
+                MH_CUDA(cudaGetLastError());
+                MH_CUDA(cudaMemcpyAsync(H->hState, H->dCounts, sizeof(u32) * kMaxH, cudaMemcpyDeviceToHost, st));
+                MH_CUDA(cudaStreamSynchronize(st));
+                const u64 need = (u64)((u32 *)H->hState)[l];
+                if (need <= H->cap[l]) break;
+                // frontier too small: grow it, forget this depth's counters and redo the depth
+                if ((rc = ensure_frontier(H, l, need))) {
+                    cudaEventDestroy(total.a);
+                    cudaEventDestroy(total.b);
+                    for (auto &e : leaf_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+                    return rc;
+                }
+                MH_CUDA(cudaMemsetAsync(H->dCounts + l, 0, sizeof(u32), st));
+                MH_CUDA(cudaMemsetAsync(H->dCnt + ((size_t)r * h + (l - 1)) * 2, 0, 2 * sizeof(u64), st));
+            }
+        }
+        if (h >= 2) {
+            EventPair ev;
+            if (opts->time_kernels) {
+                MH_CUDA(cudaEventCreate(&ev.a));
+                MH_CUDA(cudaEventCreate(&ev.b));
+                MH_CUDA(cudaEventRecord(ev.a, st));
+            }
+            launch_leaf(c, s, r, H->dF[h - 1], H->dCounts + (h - 1), grid, st);
+            ++launches;
+            ++leaf_launches;
+            if (opts->time_kernels) {
+                MH_CUDA(cudaEventRecord(ev.b, st));
+                leaf_ev.push_back(ev);
+            }
+        }
+        launch_finalize(c, s, r, st);
+        ++launches;
+        MH_CUDA(cudaGetLastError());
+        MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(cudaStreamSynchronize(st));
+        ++rounds;
+        done = H->hState[1] != 0;
+    }
+    MH_CUDA(cudaEventRecord(total.b, st));
+    MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    const int k = H->hState[0];
+
+    mh_result *R = (mh_result *)calloc(1, sizeof(mh_result));
+    if (!R) return fail(MH_ENOMEM, "host allocation of the result failed");
+    R->h = h;
+    R->k = k;
+    R->rounds = rounds;
+    R->genes = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k * h));
+    R->tp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
+    R->fp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
+    R->visited = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
+    R->pruned = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
+    if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned) {
+        mh_result_free(R);
+        return fail(MH_ENOMEM, "host allocation of the result failed");
+    }
+    std::vector<int> res((size_t)std::max(1, k) * (h + 2));
+    std::vector<u64> cnt((size_t)std::max(1, rounds) * h * 2);
+    std::vector<u64> work(2);
+    cudaError_t e = cudaSuccess;
+    if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && rounds)
+        e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        mh_result_free(R);
+        return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < k; ++i) {
+        for (int j = 0; j < h; ++j) R->genes[i * h + j] = res[(size_t)i * (h + 2) + j];
+        R->tp[i] = res[(size_t)i * (h + 2) + h];
+        R->fp[i] = res[(size_t)i * (h + 2) + h + 1];
+    }
+    for (int i = 0; i < rounds * h; ++i) {
+        R->visited[i] = cnt[(size_t)i * 2];
+        R->pruned[i] = cnt[(size_t)i * 2 + 1];
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, total.a, total.b);
+    R->solve_ms = ms;
+    double leaf_ms = 0.0;
+    for (auto &ev : leaf_ev) {
+        float x = 0.f;
+        cudaEventElapsedTime(&x, ev.a, ev.b);
+        leaf_ms += x;
+        cudaEventDestroy(ev.a);
+        cudaEventDestroy(ev.b);
+    }
+    cudaEventDestroy(total.a);
+    cudaEventDestroy(total.b);
+    R->leaf_ms = leaf_ms;
+    R->leaf_launches = leaf_launches;
+    R->kernel_launches = launches;
+    R->leaf_words = work[0];
+    R->leaf_prefixes = work[1];
+    *out = R;
+    return MH_OK;
+}
+
+}  // extern "C"

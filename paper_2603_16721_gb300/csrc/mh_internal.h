@@ -1,0 +1,74 @@
+// Internal definitions shared by the host runtime and the kernels of libmh.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mh {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+typedef unsigned short u16;
+
+constexpr int kMaxH = 9;
+constexpr int kMaxWords = 32;      // per-block row words: Nt, Nn <= 2048
+constexpr int kMaxSamples = 2048;  // Nt <= 2048
+constexpr int kMaxGenes = 65535;   // gene indices are 16-bit in prefixes and keys
+constexpr int kWarpsPerBlock = 8;
+constexpr int kThreads = kWarpsPerBlock * 32;
+
+// Device view of one cohort, genes in search order (most sparse first, §III-C).
+struct Cohort {
+    int G, Nt, Nn;
+    int Wt, Wn;     // words holding Nt / Nn bits
+    int WTp, WNp;   // row strides in words (even: 16-byte aligned rows)
+    int GW;         // words of one sample-major column over the G sorted genes (even)
+    const u64 *T;   // G x WTp   tumor rows, gene-major
+    const u64 *N;   // G x WNp   normal rows, gene-major
+    const u64 *CT;  // Nt x GW   tumor bits, sample-major: bit g of column s = T[g] bit s
+    const u16 *orig;  // G: search position -> original row index
+    const u32 *inv;   // G: original row index -> search position
+};
+
+// Best candidate of a search, compared as (score desc, original tuple asc).
+// s = S + 1 (0 = no candidate); t0..t2 pack the ascending original indices,
+// 16 bits each, first index in the high bits of t0 (so the tuple's
+// lexicographic order is the numeric order of (t0, t1, t2)).
+struct Key {
+    u64 s, t0, t1, t2;
+};
+
+// A prefix of the search tree (genes g_1 < ... < g_l in search order),
+// 16 bits per gene: gene i in word i / 4 at bits 16 * (i % 4).
+struct Prefix {
+    u64 w0, w1;
+};
+
+// Per-solve device state.
+struct Solve {
+    int h;
+    int prune;          // 0 = paper (cut empty intersections), 1 = off
+    u64 a_num, a_den;
+    u64 *U;             // WTp words: uncovered tumors
+    int *state;         // [0] = k selected, [1] = done flag, [2] = error flag
+    int *res;           // per round: h original indices, TP, FP
+    u64 *cnt;           // per round, per level: visited, pruned
+    Key *slots;         // per-block best candidates of the current round
+    int nslots;
+    u64 *work;          // [0] column words OR-ed by leaf kernels, [1] prefixes expanded by leaf kernels
+};
+
+// Launchers (mh_kernels.cu).
+void launch_transpose(const Cohort &c, u64 *CT, cudaStream_t st);
+void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st);
+void launch_level1(const Cohort &c, const Solve &s, int round, Prefix *F1, u32 *n1, u32 cap1, cudaStream_t st);
+void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Prefix *Fin, const u32 *nin,
+                   Prefix *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st);
+void launch_leaf(const Cohort &c, const Solve &s, int round, const Prefix *Fin, const u32 *nin, int grid,
+                 cudaStream_t st);
+void launch_finalize(const Cohort &c, const Solve &s, int round, cudaStream_t st);
+int level1_grid(const Cohort &c);
+
+}  // namespace mh

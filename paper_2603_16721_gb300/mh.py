@@ -1,0 +1,221 @@
+"""Python binding of libmh (argument marshalling only; declared in include/mh.h).
+
+Every function here forwards to the C ABI of ``libmh.so``; no step of a solve runs
+in Python.  The library must have been built (``__graft_entry__.build()``); if it
+cannot be loaded, every call raises ``MHLibraryError`` -- there is no fallback.
+
+Names follow the C ABI: ``mh_create``, ``mh_create_device``, ``mh_set_stream``,
+``mh_solve``, ``mh_solve_ex``, ``mh_destroy``, ``mh_last_error``,
+``mh_handle_info``.  Results come back as ``Result`` objects holding numpy
+copies of the library's arrays (the C result is released immediately).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+MH_OK, MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT, MH_EAGAIN, MH_EREJECT = range(7)
+MH_PRUNE_PAPER, MH_PRUNE_OFF = 0, 1
+_NAMES = {0: "MH_OK", 1: "MH_EINVAL", 2: "MH_ENOMEM", 3: "MH_ECUDA", 4: "MH_ETIMEOUT", 5: "MH_EAGAIN",
+          6: "MH_EREJECT"}
+
+
+class MHLibraryError(RuntimeError):
+    """libmh.so is missing or cannot be loaded."""
+
+
+class MHError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mh_rational(ctypes.Structure):
+    _fields_ = [("num", ctypes.c_int32), ("den", ctypes.c_int32)]
+
+
+class mh_solve_opts(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_int32), ("alpha", mh_rational), ("prune", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("time_kernels", ctypes.c_int32)]
+
+
+class mh_result(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_int32), ("k", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("genes", ctypes.POINTER(ctypes.c_int32)), ("tp", ctypes.POINTER(ctypes.c_int32)),
+                ("fp", ctypes.POINTER(ctypes.c_int32)), ("visited", ctypes.POINTER(ctypes.c_uint64)),
+                ("pruned", ctypes.POINTER(ctypes.c_uint64)), ("solve_ms", ctypes.c_double),
+                ("leaf_ms", ctypes.c_double), ("leaf_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("leaf_words", ctypes.c_uint64),
+                ("leaf_prefixes", ctypes.c_uint64)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libmh.so (built beforehand by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise MHLibraryError(f"{path} is missing: build it with __graft_entry__.build()")
+    try:
+        lib = ctypes.CDLL(path)
+    except OSError as e:
+        raise MHLibraryError(f"cannot load {path}: {e}") from e
+    lib.mh_create.restype = ctypes.c_int
+    lib.mh_create.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]
+    lib.mh_create_device.restype = ctypes.c_int
+    lib.mh_create_device.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.POINTER(_P)]
+    lib.mh_set_stream.restype = ctypes.c_int
+    lib.mh_set_stream.argtypes = [_P, _P]
+    lib.mh_solve.restype = ctypes.c_int
+    lib.mh_solve.argtypes = [_P, ctypes.c_int32, mh_rational, ctypes.POINTER(ctypes.POINTER(mh_result))]
+    lib.mh_solve_ex.restype = ctypes.c_int
+    lib.mh_solve_ex.argtypes = [_P, ctypes.POINTER(mh_solve_opts), ctypes.POINTER(ctypes.POINTER(mh_result))]
+    lib.mh_result_free.restype = None
+    lib.mh_result_free.argtypes = [ctypes.POINTER(mh_result)]
+    lib.mh_destroy.restype = None
+    lib.mh_destroy.argtypes = [_P]
+    lib.mh_last_error.restype = ctypes.c_char_p
+    lib.mh_last_error.argtypes = []
+    lib.mh_handle_info.restype = ctypes.c_int
+    lib.mh_handle_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    _lib = lib
+    return lib
+
+
+def mh_last_error() -> str:
+    return load().mh_last_error().decode()
+
+
+def _check(rc):
+    if rc != MH_OK:
+        raise MHError(rc, mh_last_error())
+
+
+@dataclass
+class Result:
+    """A solve's ordered selections plus per-round counters and timings."""
+    h: int
+    genes: np.ndarray     # [k, h] original indices, ascending per row
+    tp: np.ndarray        # [k]
+    fp: np.ndarray        # [k]
+    visited: np.ndarray   # [rounds, h]
+    pruned: np.ndarray    # [rounds, h]
+    solve_ms: float
+    leaf_ms: float
+    leaf_launches: int
+    kernel_launches: int
+    leaf_words: int
+    leaf_prefixes: int
+
+    @property
+    def k(self) -> int:
+        return int(self.tp.shape[0])
+
+    @property
+    def rounds(self) -> int:
+        return int(self.visited.shape[0])
+
+    def records(self):
+        return [(tuple(int(g) for g in self.genes[i]), int(self.tp[i]), int(self.fp[i])) for i in range(self.k)]
+
+
+def _to_result(p) -> Result:
+    r = p.contents
+    k, h, rounds = r.k, r.h, r.rounds
+    arr = lambda ptr, n, dt: np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt, copy=True) if n else np.zeros(0, dt)
+    out = Result(h=h,
+                 genes=arr(r.genes, k * h, np.int32).reshape(k, h),
+                 tp=arr(r.tp, k, np.int32), fp=arr(r.fp, k, np.int32),
+                 visited=arr(r.visited, rounds * h, np.uint64).reshape(rounds, h),
+                 pruned=arr(r.pruned, rounds * h, np.uint64).reshape(rounds, h),
+                 solve_ms=float(r.solve_ms), leaf_ms=float(r.leaf_ms), leaf_launches=int(r.leaf_launches),
+                 kernel_launches=int(r.kernel_launches), leaf_words=int(r.leaf_words),
+                 leaf_prefixes=int(r.leaf_prefixes))
+    load().mh_result_free(p)
+    return out
+
+
+class Handle:
+    """Owns an ``mh_handle*``; destroyed with ``mh_destroy`` when closed or collected."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            load().mh_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mh_create(bitmaps: np.ndarray, G: int, Nt: int, Nn: int) -> Handle:
+    """Handle from packed rows in host memory (uint64, G x (Wt + Wn))."""
+    bm = np.ascontiguousarray(bitmaps, dtype=np.uint64)
+    W = (Nt + 63) // 64 + (Nn + 63) // 64
+    if bm.size != G * W:
+        raise MHError(MH_EINVAL, f"bitmaps hold {bm.size} words, expected {G * W}")
+    out = _P()
+    _check(load().mh_create(bm.ctypes.data, G, Nt, Nn, ctypes.byref(out)))
+    return Handle(out)
+
+
+def mh_create_device(d_bitmaps_ptr: int, G: int, Nt: int, Nn: int, stream: int = 0) -> Handle:
+    """Handle from packed rows in device memory (a raw device pointer, e.g.
+    ``tensor.data_ptr()``) and a raw ``cudaStream_t`` (e.g. ``torch_stream.cuda_stream``)."""
+    out = _P()
+    _check(load().mh_create_device(_P(d_bitmaps_ptr), G, Nt, Nn, _P(stream or None), ctypes.byref(out)))
+    return Handle(out)
+
+
+def mh_set_stream(handle: Handle, stream: int = 0) -> None:
+    _check(load().mh_set_stream(handle.ptr, _P(stream or None)))
+
+
+def mh_solve(handle: Handle, h: int, alpha=(1, 10)) -> Result:
+    p = ctypes.POINTER(mh_result)()
+    _check(load().mh_solve(handle.ptr, h, mh_rational(*alpha), ctypes.byref(p)))
+    return _to_result(p)
+
+
+def mh_solve_ex(handle: Handle, h: int, alpha=(1, 10), prune: int = MH_PRUNE_PAPER, max_rounds: int = 0,
+                time_kernels: bool = False) -> Result:
+    o = mh_solve_opts(h, mh_rational(*alpha), prune, max_rounds, int(bool(time_kernels)))
+    p = ctypes.POINTER(mh_result)()
+    _check(load().mh_solve_ex(handle.ptr, ctypes.byref(o), ctypes.byref(p)))
+    return _to_result(p)
+
+
+def mh_destroy(handle: Handle) -> None:
+    handle.close()
+
+
+def mh_handle_info(handle: Handle):
+    G, Nt, Nn, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().mh_handle_info(handle.ptr, ctypes.byref(G), ctypes.byref(Nt), ctypes.byref(Nn), ctypes.byref(b)))
+    return G.value, Nt.value, Nn.value, b.value
