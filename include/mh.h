@@ -138,6 +138,34 @@ MH_API void mh_destroy(mh_handle *handle);
 /* Message of the last error on the calling thread ("" if none). */
 MH_API const char *mh_last_error(void);
 
+/* Greedy solve that allocates nothing (the paper has no counterpart: this is a
+ * deployment variant of mh_solve).  For callers that cannot call cudaMalloc --
+ * code running while another component owns all device memory through its own
+ * pool, plug-ins handed fixed buffers by a host framework, or latency-critical
+ * streams that must not see allocator traffic -- every piece of scratch lives
+ * in one file-scope __device__ array of about 21 MB that every GPU loading this
+ * library keeps until the process exits.  It returns the same selections as
+ * mh_solve(h, alpha) with MH_PRUNE_PAPER.
+ *   d_bitmaps : DEVICE pointer to packed rows (layout above), caller-owned, read only.
+ *   d_genes   : DEVICE int32 buffer of capacity*h entries (original indices, ascending per row).
+ *   d_tp, d_fp: DEVICE int32 buffers of capacity entries.
+ *   capacity  : rows available in the outputs; must be >= Nt (each selection covers >= 1 tumor).
+ *   k_out     : HOST pointer receiving the number of selections; rounds_out (HOST, may be NULL)
+ *               receives the number of greedy rounds searched.
+ *   stream    : cudaStream_t (NULL = legacy default stream); the call is synchronous.
+ * Limits: G <= 8192, Nt <= 1024, Nn <= 1024, 1 <= h <= 4, and at most 2^19
+ * prefixes per intermediate depth of the search; larger inputs return MH_EINVAL,
+ * a larger frontier MH_ENOMEM, each with a message naming the limit.  The first
+ * call on a device looks up the array's device address (once per device); make
+ * that first call before any CUDA stream capture.  All calls share the array and
+ * each leaves its contents behind (every call clears what must start at zero):
+ * calls whose GPU work overlaps, on different streams or host threads, race on
+ * it and must be serialised by the caller.  No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, int32_t Nn, int32_t h,
+                            mh_rational alpha, void *stream, int32_t *d_genes, int32_t *d_tp, int32_t *d_fp,
+                            int32_t capacity, int32_t *k_out, int32_t *rounds_out);
+
 /* Cohort dimensions of a handle (any pointer may be NULL). */
 MH_API int mh_handle_info(const mh_handle *handle, int32_t *G, int32_t *Nt, int32_t *Nn,
                           int64_t *device_bytes);

@@ -66,6 +66,10 @@ int dalloc(T **p, size_t n, int64_t *acct)
 
 }  // namespace
 
+namespace mh {
+void set_error_text(const char *text) { g_last_error = text; }
+}  // namespace mh
+
 struct mh_handle {
     int G = 0, Nt = 0, Nn = 0;
     Cohort c{};

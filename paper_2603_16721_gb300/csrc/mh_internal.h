@@ -71,4 +71,7 @@ void launch_leaf(const Cohort &c, const Solve &s, int round, const Prefix *Fin, 
 void launch_finalize(const Cohort &c, const Solve &s, int round, cudaStream_t st);
 int level1_grid(const Cohort &c);
 
+// Message returned by mh_last_error() on the calling thread.
+void set_error_text(const char *text);
+
 }  // namespace mh

@@ -219,3 +219,22 @@ def mh_handle_info(handle: Handle):
     G, Nt, Nn, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().mh_handle_info(handle.ptr, ctypes.byref(G), ctypes.byref(Nt), ctypes.byref(Nn), ctypes.byref(b)))
     return G.value, Nt.value, Nn.value, b.value
+
+
+def mh_solve_noalloc(d_bitmaps_ptr: int, G: int, Nt: int, Nn: int, h: int, alpha, stream: int,
+                     d_genes_ptr: int, d_tp_ptr: int, d_fp_ptr: int, capacity: int):
+    """Allocation-free greedy solve (see include/mh.h): device input rows, device
+    output buffers (int32: capacity*h genes, capacity TP, capacity FP).  Returns
+    (k, rounds)."""
+    lib = load()
+    if not hasattr(lib, "_noalloc_typed"):
+        lib.mh_solve_noalloc.restype = ctypes.c_int
+        lib.mh_solve_noalloc.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         mh_rational, _P, _P, _P, _P, ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib._noalloc_typed = True
+    k, rounds = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.mh_solve_noalloc(_P(d_bitmaps_ptr), G, Nt, Nn, h, mh_rational(*alpha), _P(stream or None),
+                                _P(d_genes_ptr), _P(d_tp_ptr), _P(d_fp_ptr), capacity, ctypes.byref(k),
+                                ctypes.byref(rounds)))
+    return k.value, rounds.value
