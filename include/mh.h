@@ -94,8 +94,11 @@ typedef struct {
     double leaf_ms;      /* sum of leaf-kernel durations (CUDA events), if time_kernels */
     int64_t leaf_launches;   /* leaf-kernel launches in this solve */
     int64_t kernel_launches; /* all kernel launches of this solve */
-    uint64_t leaf_words;     /* 64-bit column words OR-ed by the leaf kernel (sibling tests) */
+    uint64_t leaf_words;     /* 64-bit sample-major column words read by the leaf kernel */
     uint64_t leaf_prefixes;  /* prefixes (depth h-1 nodes) the leaf kernel expanded */
+    uint64_t leaf_scored;    /* leaves whose TP / FP the leaf kernel evaluated exactly */
+    uint64_t leaf_alu_ops;   /* 32-bit integer operations of the leaf kernel's tests and scores */
+    uint64_t leaf_dense;     /* prefixes the leaf kernel took on its row (dense) path */
 } mh_result;
 
 /* Create a handle for one cohort from packed rows in HOST memory.
@@ -143,7 +146,7 @@ MH_API const char *mh_last_error(void);
  * code running while another component owns all device memory through its own
  * pool, plug-ins handed fixed buffers by a host framework, or latency-critical
  * streams that must not see allocator traffic -- every piece of scratch lives
- * in one file-scope __device__ array of about 21 MB that every GPU loading this
+ * in one file-scope __device__ array of about 22 MB that every GPU loading this
  * library keeps until the process exits.  It returns the same selections as
  * mh_solve(h, alpha) with MH_PRUNE_PAPER.
  *   d_bitmaps : DEVICE pointer to packed rows (layout above), caller-owned, read only.

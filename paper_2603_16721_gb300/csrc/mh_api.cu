@@ -77,7 +77,7 @@ struct mh_handle {
     int num_sms = 0;
     int64_t device_bytes = 0;
     // cohort store
-    u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr;
+    u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr, *dCN = nullptr;
     u16 *dOrig = nullptr;
     u32 *dInv = nullptr;
     // solve workspace (grown on demand)
@@ -85,7 +85,7 @@ struct mh_handle {
     u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr;
     int *dState = nullptr, *dRes = nullptr;
     Key *dSlots = nullptr;
-    u32 *dCounts = nullptr;               // frontier sizes, one per depth
+    u32 *dCounts = nullptr;               // frontier sizes, one per depth, then work-distribution counters
     Prefix *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
     int *hState = nullptr;                // pinned: state + frontier counts
@@ -93,7 +93,7 @@ struct mh_handle {
 
     ~mh_handle()
     {
-        cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dOrig); cudaFree(dInv);
+        cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dCN); cudaFree(dOrig); cudaFree(dInv);
         cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
         cudaFree(dSlots); cudaFree(dCounts);
         for (int l = 0; l < kMaxH; ++l) cudaFree(dF[l]);
@@ -160,14 +160,16 @@ int build_store(mh_handle *H, const uint64_t *bm)
     if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes))) return rc;
     if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes))) return rc;
     if ((rc = dalloc(&H->dCT, (size_t)Nt * c.GW, &H->device_bytes))) return rc;
+    if ((rc = dalloc(&H->dCN, (size_t)Nn * c.GW, &H->device_bytes))) return rc;
     if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes))) return rc;
     if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes))) return rc;
     MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
     MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
     MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, H->stream));
     MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, H->stream));
-    c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.orig = H->dOrig; c.inv = H->dInv;
-    launch_transpose(c, H->dCT, H->stream);
+    c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.CN = H->dCN; c.orig = H->dOrig; c.inv = H->dInv;
+    launch_transpose(c, H->dT, c.WTp, Nt, H->dCT, H->stream);
+    launch_transpose(c, H->dN, c.WNp, Nn, H->dCN, H->stream);
     MH_CUDA(cudaGetLastError());
     MH_CUDA(cudaStreamSynchronize(H->stream));  // host vectors go out of scope
     return MH_OK;
@@ -229,9 +231,9 @@ int ensure_workspace(mh_handle *H, int h)
     if (!H->dU) {
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dState, 4, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dWork, 2, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)kMaxH, &H->device_bytes))) return rc;
-        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (4 + kMaxH)));
+        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dCounts, (size_t)2 * kCountStride, &H->device_bytes))) return rc;
+        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (4 + kCountStride)));
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
         cudaFree(H->dCnt);
@@ -364,6 +366,8 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     s.slots = H->dSlots;
     s.nslots = H->ws_slots;
     s.work = H->dWork;
+    s.best_hint = H->dWork + kWorkCount;
+    s.fetch = H->dCounts + kCountStride;
     int max_rounds = H->Nt + 1;
     if (opts->max_rounds > 0) max_rounds = std::min(max_rounds, (int)opts->max_rounds);
 
@@ -381,7 +385,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     bool done = H->Nt == 0;  // every tumor covered from the start
     while (!done && rounds < max_rounds) {
         const int r = rounds;
-        MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kMaxH, st));
+        MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * 2 * kCountStride, st));
         launch_level1(c, s, r, H->dF[1], H->dCounts + 1, H->cap[1], st);
         ++launches;
         for (int l = 2; l <= h - 1; ++l) {
@@ -402,6 +406,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                     return rc;
                 }
                 MH_CUDA(cudaMemsetAsync(H->dCounts + l, 0, sizeof(u32), st));
+                MH_CUDA(cudaMemsetAsync(s.fetch + l, 0, sizeof(u32), st));
                 MH_CUDA(cudaMemsetAsync(H->dCnt + ((size_t)r * h + (l - 1)) * 2, 0, 2 * sizeof(u64), st));
             }
         }
@@ -449,12 +454,12 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     }
     std::vector<int> res((size_t)std::max(1, k) * (h + 2));
     std::vector<u64> cnt((size_t)std::max(1, rounds) * h * 2);
-    std::vector<u64> work(2);
+    std::vector<u64> work(kWorkCount);
     cudaError_t e = cudaSuccess;
     if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && rounds)
         e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         mh_result_free(R);
@@ -485,8 +490,11 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     R->leaf_ms = leaf_ms;
     R->leaf_launches = leaf_launches;
     R->kernel_launches = launches;
-    R->leaf_words = work[0];
-    R->leaf_prefixes = work[1];
+    R->leaf_words = work[kWorkColWords];
+    R->leaf_prefixes = work[kWorkPrefixes];
+    R->leaf_scored = work[kWorkScored];
+    R->leaf_alu_ops = work[kWorkAluOps];
+    R->leaf_dense = work[kWorkDense];
     *out = R;
     return MH_OK;
 }

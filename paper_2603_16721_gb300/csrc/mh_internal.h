@@ -18,6 +18,7 @@ constexpr int kMaxSamples = 2048;  // Nt <= 2048
 constexpr int kMaxGenes = 65535;   // gene indices are 16-bit in prefixes and keys
 constexpr int kWarpsPerBlock = 8;
 constexpr int kThreads = kWarpsPerBlock * 32;
+constexpr int kCountStride = 16;   // u32 slots per counter array (>= kMaxH + 1)
 
 // Device view of one cohort, genes in search order (most sparse first, §III-C).
 struct Cohort {
@@ -28,6 +29,7 @@ struct Cohort {
     const u64 *T;   // G x WTp   tumor rows, gene-major
     const u64 *N;   // G x WNp   normal rows, gene-major
     const u64 *CT;  // Nt x GW   tumor bits, sample-major: bit g of column s = T[g] bit s
+    const u64 *CN;  // Nn x GW   normal bits, sample-major
     const u16 *orig;  // G: search position -> original row index
     const u32 *inv;   // G: original row index -> search position
 };
@@ -57,11 +59,23 @@ struct Solve {
     u64 *cnt;           // per round, per level: visited, pruned
     Key *slots;         // per-block best candidates of the current round
     int nslots;
-    u64 *work;          // [0] column words OR-ed by leaf kernels, [1] prefixes expanded by leaf kernels
+    u64 *work;          // leaf-kernel work counters, see kWork*
+    u32 *fetch;         // per-depth work-distribution counters, zeroed every round
+    u64 *best_hint;     // best score (s field) found so far in the round, for skipping hopeless scoring
+};
+
+// Leaf-kernel work counters (Solve::work).
+enum {
+    kWorkColWords = 0,   // 64-bit sample-major column words read in sibling tests
+    kWorkPrefixes = 1,   // depth-(h-1) prefixes expanded by the leaf kernel
+    kWorkScored = 2,     // leaves whose TP / FP were evaluated exactly
+    kWorkAluOps = 3,     // 32-bit integer operations of those steps (see mh_kernels.cu)
+    kWorkDense = 4,      // prefixes taken by the dense (row) path
+    kWorkCount = 8
 };
 
 // Launchers (mh_kernels.cu).
-void launch_transpose(const Cohort &c, u64 *CT, cudaStream_t st);
+void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
 void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st);
 void launch_level1(const Cohort &c, const Solve &s, int round, Prefix *F1, u32 *n1, u32 cap1, cudaStream_t st);
 void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Prefix *Fin, const u32 *nin,

@@ -14,8 +14,17 @@
 //     OR over s in y_{l-1} of CT[s]      restricted to the child range,
 // which one lane evaluates 64 siblings at a time.  This is the same emptiness
 // test as AND-ing y_{l-1} with every sibling row, bit-sliced over the siblings.
-// Surviving leaves are scored from row popcounts over the non-zero words of the
-// prefix only (the other words of the AND are zero).
+//
+// Leaf scores.  For a sparse prefix (few samples in y_{l-1} and n_{l-1}) the same
+// column words, summed in bit-sliced counters (one 64-bit plane per bit of the
+// count), give TP(g) = |y_{l-1} & x_g| and FP(g) = |n_{l-1} & x^N_g| for 64
+// siblings at once, so a leaf is scored without touching its rows.  Prefixes
+// with many samples take a row path: popcounts over the non-zero words only.
+//
+// Work distribution.  A warp takes 32 prefixes at a time from a per-depth atomic
+// counter (the analogue of the paper's chunked lambda dispatch, §III-E); each lane
+// first lists the samples of one prefix, then four groups of eight lanes sweep the
+// sparse prefixes' child ranges, and the whole warp takes the dense ones.
 #include "mh_internal.h"
 
 namespace mh {
@@ -23,6 +32,13 @@ namespace mh {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBatch = 32;       // prefixes taken per warp
+constexpr int kGroup = 8;        // lanes per prefix on the sparse path
+constexpr int kGroups = 32 / kGroup;
+constexpr int kListT = 20;       // tumor samples listed per sparse prefix
+constexpr int kListN = 12;       // normal samples listed per sparse prefix
+constexpr int kPlanesT = 5;      // bit planes for counts <= 20
+constexpr int kPlanesN = 4;      // bit planes for counts <= 12
 
 __device__ __forceinline__ int prefix_gene(const Prefix &p, int i)
 {
@@ -66,6 +82,26 @@ __device__ __forceinline__ int key_get(const Key &k, int pos)
     return (int)((w >> (16 * (3 - (pos & 3)))) & 0xffffull);
 }
 
+// Key of a leaf: the prefix's original indices (ascending, po[0..L)) with o inserted.
+__device__ __forceinline__ Key leaf_key(u64 s1, const int *po, int L, int o)
+{
+    Key k;
+    k.s = s1;
+    k.t0 = k.t1 = k.t2 = 0;
+    int pos = 0;
+    bool placed = false;
+    for (int q = 0; q < L; ++q) {
+        const int v = po[q];
+        if (!placed && o < v) {
+            key_put(k, pos++, o);
+            placed = true;
+        }
+        key_put(k, pos++, v);
+    }
+    if (!placed) key_put(k, pos, o);
+    return k;
+}
+
 __device__ __forceinline__ Key warp_max_key(Key k)
 {
     for (int off = 16; off; off >>= 1) {
@@ -82,6 +118,15 @@ __device__ __forceinline__ Key warp_max_key(Key k)
 __device__ __forceinline__ u64 warp_sum_u64(u64 v)
 {
     for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+__device__ __forceinline__ u64 warp_max_u64(u64 v)
+{
+    for (int off = 16; off; off >>= 1) {
+        const u64 o = __shfl_xor_sync(kFull, v, off);
+        v = o > v ? o : v;
+    }
     return v;
 }
 
@@ -120,19 +165,121 @@ __device__ __forceinline__ void count_level(const Solve &s, int round, int level
     if (pruned) atomicAdd(c + 1, pruned);
 }
 
-// Per-warp scratch of the prefix being expanded.
-struct WarpScratch {
-    u64 ys[kMaxWords];      // y_{l-1} words
-    u64 ns[kMaxWords];      // n_{l-1} words
-    u16 samp[kMaxSamples];  // samples set in y_{l-1}
-    int po[kMaxH];          // original indices of the prefix genes, ascending
+__device__ __forceinline__ u64 range_word(int wi, int lo, int hi)
+{
+    u64 m = ~0ull;
+    if (wi == (lo >> 6)) m &= ~0ull << (lo & 63);
+    if (wi == (hi >> 6)) m &= ~0ull >> (63 - (hi & 63));
+    return m;
+}
+
+// Adds the 64 one-bit values of x to the bit-sliced counters p[0..P).
+template <int P>
+__device__ __forceinline__ void planes_add(u64 (&p)[P], u64 x, int used)
+{
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (i < used) {
+            const u64 c = p[i] & x;
+            p[i] ^= x;
+            x = c;
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ int planes_get(const u64 (&p)[P], int b, int used)
+{
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < P; ++i)
+        if (i < used) v |= (int)((p[i] >> b) & 1ull) << i;
+    return v;
+}
+
+__device__ __forceinline__ int bit_length(int v) { return 32 - __clz(v); }
+
+// Per-warp scratch: one batch of prefixes and their sample lists.
+struct BatchScratch {
+    Prefix p[kBatch];
+    u16 ky[kBatch], kn[kBatch];
+    u16 ids[kBatch][kListT + kListN];
+    int po[kGroups][kMaxH];  // ascending original indices of each group's current prefix
+    u64 ys[kMaxWords];       // dense path: y_{l-1} and n_{l-1} words
+    u64 ns[kMaxWords];
 };
 
-// Loads the prefix, forms y_{l-1} / n_{l-1} (lane w holds word w), lists the
-// samples of y_{l-1} in ws.samp and returns their number.
-__device__ __forceinline__ int warp_prefix_setup(const Cohort &c, const Solve &s, const Prefix &p, int L,
-                                                 WarpScratch &ws, unsigned &by, unsigned &bn, int lane,
-                                                 bool want_orig)
+// Lane j of the warp lists the samples of prefix base+j: its tumor intersection
+// with U and its normal intersection, as sample indices when few, else only counts.
+template <bool kNormals>
+__device__ __forceinline__ void batch_load(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 count,
+                                           int L, BatchScratch &b, int lane)
+{
+    const u32 i = base + lane;
+    int ky = 0, kn = 0;
+    if (i < count) {
+        const Prefix p = Fin[i];
+        b.p[lane] = p;
+        int g[kMaxH];
+#pragma unroll
+        for (int q = 0; q < kMaxH - 1; ++q) g[q] = q < L ? prefix_gene(p, q) : 0;
+        for (int w = 0; w < c.Wt; ++w) {
+            u64 y = s.U[w];
+#pragma unroll
+            for (int q = 0; q < kMaxH - 1; ++q)
+                if (q < L) y &= c.T[(size_t)g[q] * c.WTp + w];
+            const int n = __popcll(y);
+            if (ky + n <= kListT) {
+                int k = ky;
+                while (y) {
+                    const int bt = __ffsll((long long)y) - 1;
+                    y &= y - 1;
+                    b.ids[lane][k++] = (u16)(w * 64 + bt);
+                }
+            }
+            ky += n;
+        }
+        for (int w = 0; kNormals && w < c.Wn; ++w) {
+            u64 y = ~0ull;
+#pragma unroll
+            for (int q = 0; q < kMaxH - 1; ++q)
+                if (q < L) y &= c.N[(size_t)g[q] * c.WNp + w];
+            const int n = __popcll(y);
+            if (kn + n <= kListN) {
+                int k = kn;
+                while (y) {
+                    const int bt = __ffsll((long long)y) - 1;
+                    y &= y - 1;
+                    b.ids[lane][kListT + k++] = (u16)(w * 64 + bt);
+                }
+            }
+            kn += n;
+        }
+    }
+    b.ky[lane] = (u16)(ky < 0xffff ? ky : 0xffff);
+    b.kn[lane] = (u16)(kn < 0xffff ? kn : 0xffff);
+    __syncwarp();
+}
+
+__device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT || kn > kListN; }
+
+// Ascending original indices of a prefix's genes (L <= 8), written by one lane.
+__device__ __forceinline__ void prefix_orig(const Cohort &c, const Prefix &p, int L, int *po)
+{
+    for (int i = 0; i < L; ++i) {
+        const int v = c.orig[prefix_gene(p, i)];
+        int j = i - 1;
+        while (j >= 0 && po[j] > v) {
+            po[j + 1] = po[j];
+            --j;
+        }
+        po[j + 1] = v;
+    }
+}
+
+// Dense path: lane w forms word w of y_{l-1} / n_{l-1} into the warp scratch.
+__device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, const Prefix &p, int L,
+                                            BatchScratch &b, unsigned &by, unsigned &bn, int lane)
 {
     u64 y = 0, n = 0;
     if (lane < c.Wt) {
@@ -143,101 +290,69 @@ __device__ __forceinline__ int warp_prefix_setup(const Cohort &c, const Solve &s
         n = ~0ull;
         for (int i = 0; i < L; ++i) n &= c.N[(size_t)prefix_gene(p, i) * c.WNp + lane];
     }
-    ws.ys[lane] = y;
-    ws.ns[lane] = n;
+    b.ys[lane] = y;
+    b.ns[lane] = n;
     by = __ballot_sync(kFull, y != 0);
     bn = __ballot_sync(kFull, n != 0);
-    const int cnt = __popcll(y);
-    const int incl = warp_incl_scan(cnt, lane);
-    const int total = __shfl_sync(kFull, incl, 31);
-    int off = incl - cnt;
-    u64 yy = y;
-    while (yy) {
-        const int b = __ffsll((long long)yy) - 1;
-        yy &= yy - 1;
-        ws.samp[off++] = (u16)(lane * 64 + b);
-    }
-    if (want_orig && lane == 0) {
-        // insertion sort of the prefix's original indices (L <= 8)
-        for (int i = 0; i < L; ++i) {
-            const int v = c.orig[prefix_gene(p, i)];
-            int j = i - 1;
-            while (j >= 0 && ws.po[j] > v) {
-                ws.po[j + 1] = ws.po[j];
-                --j;
-            }
-            ws.po[j + 1] = v;
+    __syncwarp();
+}
+
+// OR of the sample-major columns of y_{l-1} at word wi (dense path: samples from the y words).
+__device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const BatchScratch &b, unsigned by, int wi)
+{
+    u64 m = 0;
+    for (unsigned bits = by; bits; bits &= bits - 1) {
+        const int w = __ffs(bits) - 1;
+        u64 y = b.ys[w];
+        while (y) {
+            const int bt = __ffsll((long long)y) - 1;
+            y &= y - 1;
+            m |= c.CT[(size_t)(w * 64 + bt) * c.GW + wi];
         }
     }
-    __syncwarp();
-    return total;
-}
-
-// OR over the prefix's samples of the 64-gene column word wi, restricted to [lo, hi].
-__device__ __forceinline__ u64 sibling_word(const Cohort &c, const WarpScratch &ws, int ky, int wi, int lo,
-                                            int hi)
-{
-    const u64 *col = c.CT + wi;
-    u64 m0 = 0, m1 = 0, m2 = 0, m3 = 0;
-    int j = 0;
-    for (; j + 4 <= ky; j += 4) {
-        m0 |= col[(size_t)ws.samp[j] * c.GW];
-        m1 |= col[(size_t)ws.samp[j + 1] * c.GW];
-        m2 |= col[(size_t)ws.samp[j + 2] * c.GW];
-        m3 |= col[(size_t)ws.samp[j + 3] * c.GW];
-    }
-    for (; j < ky; ++j) m0 |= col[(size_t)ws.samp[j] * c.GW];
-    u64 m = (m0 | m1) | (m2 | m3);
-    if (wi == (lo >> 6)) m &= ~0ull << (lo & 63);
-    if (wi == (hi >> 6)) m &= ~0ull >> (63 - (hi & 63));
     return m;
 }
 
-__device__ __forceinline__ u64 range_word(int wi, int lo, int hi)
-{
-    u64 m = ~0ull;
-    if (wi == (lo >> 6)) m &= ~0ull << (lo & 63);
-    if (wi == (hi >> 6)) m &= ~0ull >> (63 - (hi & 63));
-    return m;
-}
-
-// Appends the set bits of `a` (children of prefix p at position L) to Fout with
-// one atomic per warp.  Entries beyond cap are dropped; the count still grows so
-// the host can see the size it needs.
-__device__ __forceinline__ void warp_append(u64 a, int wi, const Prefix &p, int L, Prefix *Fout, u32 *nout,
-                                            u32 cap, int lane)
+// Appends the set bits of `a` (children g = wi*64+bit of prefix p at position L) to
+// Fout with one atomic per group of `width` lanes (all lanes of the group call it).
+__device__ __forceinline__ void group_append(u64 a, int wi, const Prefix &p, int L, Prefix *Fout, u32 *nout,
+                                             u32 cap, unsigned mask, int width, int gl)
 {
     const int cnt = __popcll(a);
-    const int incl = warp_incl_scan(cnt, lane);
-    const int total = __shfl_sync(kFull, incl, 31);
+    int incl = cnt;
+    for (int off = 1; off < width; off <<= 1) {
+        const int o = __shfl_up_sync(mask, incl, off, width);
+        if (gl >= off) incl += o;
+    }
+    const int total = __shfl_sync(mask, incl, width - 1, width);
     if (total == 0) return;
     u32 base = 0;
-    if (lane == 0) base = atomicAdd(nout, (u32)total);
-    base = __shfl_sync(kFull, base, 0);
+    if (gl == 0) base = atomicAdd(nout, (u32)total);
+    base = __shfl_sync(mask, base, 0, width);
     u32 pos = base + (u32)(incl - cnt);
     while (a) {
-        const int b = __ffsll((long long)a) - 1;
+        const int bt = __ffsll((long long)a) - 1;
         a &= a - 1;
-        if (pos < cap) Fout[pos] = prefix_with(p, L, wi * 64 + b);
+        if (pos < cap) Fout[pos] = prefix_with(p, L, wi * 64 + bt);
         ++pos;
     }
 }
 
 // ---------------------------------------------------------------------------
 
-__global__ void k_transpose(Cohort c, u64 *CT)
+__global__ void k_transpose(int G, const u64 *rows, int row_stride, int samples, int GW, u64 *cols)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)c.Nt * c.GW;
+    const long long total = (long long)samples * GW;
     if (t >= total) return;
-    const int s = (int)(t / c.GW), wi = (int)(t % c.GW);
+    const int s = (int)(t / GW), wi = (int)(t % GW);
     const int sw = s >> 6, sb = s & 63;
     u64 word = 0;
     for (int b = 0; b < 64; ++b) {
         const int g = wi * 64 + b;
-        if (g < c.G) word |= ((c.T[(size_t)g * c.WTp + sw] >> sb) & 1ull) << b;
+        if (g < G) word |= ((rows[(size_t)g * row_stride + sw] >> sb) & 1ull) << b;
     }
-    CT[t] = word;
+    cols[t] = word;
 }
 
 __global__ void k_solve_init(Cohort c, Solve s)
@@ -298,123 +413,238 @@ __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int roun
     }
 }
 
-// Depths 2 .. h-1: one warp per prefix of the depth-(level-1) frontier; the
-// non-empty children (all children with pruning off) go to the depth-level frontier.
+// Depths 2 .. h-1: the non-empty children (all children with pruning off) of
+// every depth-(level-1) prefix go to the depth-level frontier.
 __global__ void __launch_bounds__(kThreads) k_expand(Cohort c, Solve s, int round, int level, const Prefix *Fin,
                                                      const u32 *nin, Prefix *Fout, u32 *nout, u32 cap)
 {
-    __shared__ WarpScratch scratch[kWarpsPerBlock];
+    __shared__ BatchScratch scratch[kWarpsPerBlock];
     if (s.state[1]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpScratch &ws = scratch[warp];
+    BatchScratch &b = scratch[warp];
     const u32 count = *nin;
     const int L = level - 1;
     const int hi = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
-    u64 visited = 0, pruned = 0;
-    const u32 gw = blockIdx.x * kWarpsPerBlock + warp, nw = gridDim.x * kWarpsPerBlock;
-    for (u32 i = gw; i < count; i += nw) {
-        const Prefix p = Fin[i];
-        unsigned by, bn;
-        const int ky = warp_prefix_setup(c, s, p, L, ws, by, bn, lane, false);
-        const int lo = prefix_gene(p, L - 1) + 1;
-        if (hi >= lo) {
-            visited += (u64)(hi - lo + 1);
-            u64 alive = 0;
+    const int gi = lane / kGroup, gl = lane % kGroup;
+    const unsigned gmask = 0xffu << (gi * kGroup);
+    u32 *fetch = s.fetch + level;
+    u64 visited = 0, alive = 0;
+    for (;;) {
+        u32 base = 0;
+        if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= count) break;
+        const int nb = count - base < (u32)kBatch ? (int)(count - base) : kBatch;
+        batch_load<false>(c, s, Fin, base, count, L, b, lane);
+        unsigned dense = __ballot_sync(kFull, lane < nb && is_dense(b.ky[lane], b.kn[lane]));
+        // sparse prefixes: one group of 8 lanes each
+        for (int j = gi; j < nb; j += kGroups) {
+            if ((dense >> j) & 1u) continue;
+            const Prefix p = b.p[j];
+            const int lo = prefix_gene(p, L - 1) + 1;
+            if (hi < lo) continue;
+            if (gl == 0) visited += (u64)(hi - lo + 1);
+            const int ky = b.ky[j];
+            const u16 *ids = b.ids[j];
+            for (int wb = lo >> 6; wb <= (hi >> 6); wb += kGroup) {
+                const int wi = wb + gl;
+                u64 m = 0, a = 0;
+                if (wi <= (hi >> 6)) {
+                    for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
+                    const u64 r = range_word(wi, lo, hi);
+                    m &= r;
+                    a = s.prune ? r : m;
+                }
+                alive += (u64)__popcll(m);
+                group_append(a, wi, p, L, Fout, nout, cap, gmask, kGroup, gl);
+            }
+        }
+        __syncwarp();
+        // dense prefixes: the whole warp
+        while (dense) {
+            const int j = __ffs(dense) - 1;
+            dense &= dense - 1;
+            const Prefix p = b.p[j];
+            const int lo = prefix_gene(p, L - 1) + 1;
+            if (hi < lo) continue;
+            unsigned by, bn;
+            dense_setup(c, s, p, L, b, by, bn, lane);
+            if (lane == 0) visited += (u64)(hi - lo + 1);
             for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
                 const int wi = wb + lane;
                 u64 m = 0, a = 0;
                 if (wi <= (hi >> 6)) {
-                    m = ky ? sibling_word(c, ws, ky, wi, lo, hi) : 0;
-                    a = s.prune ? range_word(wi, lo, hi) : m;
+                    const u64 r = range_word(wi, lo, hi);
+                    m = dense_sibling_word(c, b, by, wi) & r;
+                    a = s.prune ? r : m;
                 }
                 alive += (u64)__popcll(m);
-                warp_append(a, wi, p, L, Fout, nout, cap, lane);
+                group_append(a, wi, p, L, Fout, nout, cap, kFull, 32, lane);
             }
-            alive = warp_sum_u64(alive);
-            pruned += (u64)(hi - lo + 1) - alive;
+            __syncwarp();
         }
-        __syncwarp();
     }
-    if (lane == 0) count_level(s, round, level, visited, pruned);
+    visited = warp_sum_u64(visited);
+    alive = warp_sum_u64(alive);
+    if (lane == 0) count_level(s, round, level, visited, visited - alive);
 }
 
-// Depth h (leaves): one warp per prefix of the depth-(h-1) frontier; every
-// non-empty leaf is scored S = a_num * TP + a_den * (Nn - FP) and the best
-// (score desc, original tuple asc) is kept.
+// Depth h (leaves): every non-empty leaf is a candidate with score
+// S = a_num * TP + a_den * (Nn - FP); the best (score desc, original tuple asc)
+// goes to the block's slot.  A prefix whose bound a_num * |y| + a_den * Nn is
+// below the best score already found anywhere cannot hold the round's winner,
+// so its leaves are tested (and counted) but not scored.
 __global__ void __launch_bounds__(kThreads) k_leaf(Cohort c, Solve s, int round, const Prefix *Fin, const u32 *nin)
 {
-    __shared__ WarpScratch scratch[kWarpsPerBlock];
+    __shared__ BatchScratch scratch[kWarpsPerBlock];
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpScratch &ws = scratch[warp];
+    BatchScratch &b = scratch[warp];
     const bool done = s.state[1] != 0;
-    u64 visited = 0, pruned = 0, words = 0, prefixes = 0;
+    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, ops = 0, dense_n = 0;
+    const int h = s.h, L = h - 1;
     if (!done) {
         const u32 count = *nin;
-        const int h = s.h, L = h - 1;
         const int hi = c.G - 1;
-        const u32 gw = blockIdx.x * kWarpsPerBlock + warp, nw = gridDim.x * kWarpsPerBlock;
-        for (u32 i = gw; i < count; i += nw) {
-            const Prefix p = Fin[i];
-            unsigned by, bn;
-            const int ky = warp_prefix_setup(c, s, p, L, ws, by, bn, lane, true);
-            const int lo = prefix_gene(p, L - 1) + 1;
-            ++prefixes;
-            if (hi < lo) continue;
-            visited += (u64)(hi - lo + 1);
-            u64 alive = 0;
-            if (ky) {
+        const int gi = lane / kGroup, gl = lane % kGroup;
+        u32 *fetch = s.fetch + h;
+        const u64 nn_term = s.a_den * (u64)c.Nn + 1;
+        for (;;) {
+            u32 base = 0;
+            if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= count) break;
+            const int nb = count - base < (u32)kBatch ? (int)(count - base) : kBatch;
+            batch_load<true>(c, s, Fin, base, count, L, b, lane);
+            unsigned dense = __ballot_sync(kFull, lane < nb && is_dense(b.ky[lane], b.kn[lane]));
+            // the warp's threshold: best score seen by any block (only candidates >= it can win)
+            u64 thr = 0;
+            if (lane == 0) thr = *(volatile u64 *)s.best_hint;
+            thr = warp_max_u64(thr > best.s ? thr : best.s);
+            prefixes += (u64)(lane < nb);
+            for (int j = gi; j < nb; j += kGroups) {
+                if ((dense >> j) & 1u) continue;
+                const Prefix p = b.p[j];
+                const int lo = prefix_gene(p, L - 1) + 1;
+                if (hi < lo) continue;
+                if (gl == 0) visited += (u64)(hi - lo + 1);
+                const int ky = b.ky[j], kn = b.kn[j];
+                if (ky == 0) continue;  // empty prefix (pruning off): every child is empty
+                const u16 *ids = b.ids[j];
+                const bool score = s.a_num * (u64)ky + nn_term >= thr;
+                const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
+                if (score && gl == 0) prefix_orig(c, p, L, b.po[gi]);
+                __syncwarp(0xffu << (gi * kGroup));
+                for (int wb = lo >> 6; wb <= (hi >> 6); wb += kGroup) {
+                    const int wi = wb + gl;
+                    if (wi > (hi >> 6)) break;
+                    const u64 r = range_word(wi, lo, hi);
+                    u64 m = 0;
+                    if (!score) {
+                        for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
+                        m &= r;
+                        alive += (u64)__popcll(m);
+                        words += (u64)ky;
+                        ops += 2ull * ky;
+                        continue;
+                    }
+                    u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
+                    u64 fpl[kPlanesN] = {0, 0, 0, 0};
+                    for (int q = 0; q < ky; ++q) {
+                        const u64 x = c.CT[(size_t)ids[q] * c.GW + wi];
+                        m |= x;
+                        planes_add(tpl, x, pt);
+                    }
+                    m &= r;
+                    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)ids[kListT + q] * c.GW + wi], pn);
+                    alive += (u64)__popcll(m);
+                    words += (u64)(ky + kn);
+                    ops += (u64)ky * (2 + 4 * pt) + (u64)kn * 4 * pn;
+                    while (m) {
+                        const int bt = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        const int tp = planes_get(tpl, bt, pt);
+                        const int fp = planes_get(fpl, bt, pn);
+                        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+                        ++scored;
+                        ops += 14;
+                        if (s1 < best.s || s1 < thr) continue;
+                        const Key k = leaf_key(s1, b.po[gi], L, c.orig[wi * 64 + bt]);
+                        if (key_better(k, best)) best = k;
+                    }
+                }
+                __syncwarp(0xffu << (gi * kGroup));
+            }
+            __syncwarp();
+            // dense prefixes: the whole warp, leaves scored from row popcounts
+            while (dense) {
+                const int j = __ffs(dense) - 1;
+                dense &= dense - 1;
+                const Prefix p = b.p[j];
+                const int lo = prefix_gene(p, L - 1) + 1;
+                if (hi < lo) continue;
+                const int ky = b.ky[j];
+                unsigned by, bn;
+                dense_setup(c, s, p, L, b, by, bn, lane);
+                if (lane == 0) {
+                    visited += (u64)(hi - lo + 1);
+                    prefix_orig(c, p, L, b.po[0]);
+                    ++dense_n;
+                }
+                __syncwarp();
+                const bool score = s.a_num * (u64)ky + nn_term >= thr;
+                const int nzw = __popc(by) + __popc(bn);
                 for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
                     const int wi = wb + lane;
                     if (wi > (hi >> 6)) break;
-                    words += (u64)ky;
-                    u64 m = sibling_word(c, ws, ky, wi, lo, hi);
+                    u64 m = dense_sibling_word(c, b, by, wi) & range_word(wi, lo, hi);
                     alive += (u64)__popcll(m);
+                    words += (u64)ky;
+                    ops += 2ull * ky;
+                    if (!score) continue;
                     while (m) {
-                        const int b = __ffsll((long long)m) - 1;
+                        const int bt = __ffsll((long long)m) - 1;
                         m &= m - 1;
-                        const int g = wi * 64 + b;
+                        const int g = wi * 64 + bt;
                         const u64 *trow = c.T + (size_t)g * c.WTp;
                         const u64 *nrow = c.N + (size_t)g * c.WNp;
                         int tp = 0, fp = 0;
                         for (unsigned bits = by; bits; bits &= bits - 1) {
                             const int w = __ffs(bits) - 1;
-                            tp += __popcll(ws.ys[w] & trow[w]);
+                            tp += __popcll(b.ys[w] & trow[w]);
                         }
                         for (unsigned bits = bn; bits; bits &= bits - 1) {
                             const int w = __ffs(bits) - 1;
-                            fp += __popcll(ws.ns[w] & nrow[w]);
+                            fp += __popcll(b.ns[w] & nrow[w]);
                         }
                         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-                        if (s1 < best.s) continue;
-                        Key k;
-                        k.s = s1;
-                        k.t0 = k.t1 = k.t2 = 0;
-                        const int o = c.orig[g];
-                        int pos = 0;
-                        bool placed = false;
-                        for (int q = 0; q < L; ++q) {
-                            const int v = ws.po[q];
-                            if (!placed && o < v) {
-                                key_put(k, pos++, o);
-                                placed = true;
-                            }
-                            key_put(k, pos++, v);
-                        }
-                        if (!placed) key_put(k, pos, o);
+                        ++scored;
+                        ops += 8ull * nzw + 6;
+                        if (s1 < best.s || s1 < thr) continue;
+                        const Key k = leaf_key(s1, b.po[0], L, c.orig[g]);
                         if (key_better(k, best)) best = k;
                     }
                 }
+                __syncwarp();
             }
-            alive = warp_sum_u64(alive);
-            pruned += (u64)(hi - lo + 1) - alive;
-            __syncwarp();
+            // publish the warp's best score so that other warps can skip hopeless prefixes
+            const u64 wbest = warp_max_u64(best.s);
+            if (lane == 0 && wbest > thr) atomicMax(s.best_hint, wbest);
         }
-        if (lane == 0) {
-            count_level(s, round, h, visited, pruned);
-            atomicAdd(s.work, words);
-            atomicAdd(s.work + 1, prefixes);
-        }
+    }
+    visited = warp_sum_u64(visited);
+    alive = warp_sum_u64(alive);
+    words = warp_sum_u64(words);
+    prefixes = warp_sum_u64(prefixes);
+    scored = warp_sum_u64(scored);
+    ops = warp_sum_u64(ops);
+    if (!done && lane == 0) {
+        count_level(s, round, h, visited, visited - alive);
+        atomicAdd(s.work + kWorkColWords, words);
+        atomicAdd(s.work + kWorkPrefixes, prefixes);
+        atomicAdd(s.work + kWorkScored, scored);
+        atomicAdd(s.work + kWorkAluOps, ops);
+        atomicAdd(s.work + kWorkDense, dense_n);
     }
     block_commit_best(best, s.slots);
 }
@@ -440,6 +670,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int ro
     if (warp != 0) return;
     best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
     best = warp_max_key(best);
+    if (lane == 0) *s.best_hint = 0;
     if (best.s == 0) {
         if (lane == 0) s.state[1] = 1;
         return;
@@ -487,20 +718,21 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int ro
 // ---------------------------------------------------------------------------
 // Launchers
 
-void launch_transpose(const Cohort &c, u64 *CT, cudaStream_t st)
+void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st)
 {
-    const long long total = (long long)c.Nt * c.GW;
+    const long long total = (long long)samples * c.GW;
     if (total == 0) return;
     const int threads = 256;
     const long long blocks = (total + threads - 1) / threads;
-    k_transpose<<<(unsigned)blocks, threads, 0, st>>>(c, CT);
+    k_transpose<<<(unsigned)blocks, threads, 0, st>>>(c.G, rows, row_stride, samples, c.GW, cols);
 }
 
 void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st)
 {
     cudaMemsetAsync(s.cnt, 0, sizeof(u64) * 2 * (size_t)s.h * (size_t)max_rounds, st);
     cudaMemsetAsync(s.slots, 0, sizeof(Key) * (size_t)s.nslots, st);
-    cudaMemsetAsync(s.work, 0, sizeof(u64) * 2, st);
+    cudaMemsetAsync(s.work, 0, sizeof(u64) * kWorkCount, st);
+    cudaMemsetAsync(s.best_hint, 0, sizeof(u64), st);
     k_solve_init<<<1, 64, 0, st>>>(c, s);
 }
 

@@ -49,19 +49,20 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffT = 0;
 constexpr size_t kOffN = kOffT + align256(sizeof(u64) * kNaMaxG * kNaWTp);
 constexpr size_t kOffCT = kOffN + align256(sizeof(u64) * kNaMaxG * kNaWNp);
-constexpr size_t kOffOrig = kOffCT + align256(sizeof(u64) * kNaMaxNt * kNaGW);
+constexpr size_t kOffCN = kOffCT + align256(sizeof(u64) * kNaMaxNt * kNaGW);
+constexpr size_t kOffOrig = kOffCN + align256(sizeof(u64) * kNaMaxNn * kNaGW);
 constexpr size_t kOffInv = kOffOrig + align256(sizeof(u16) * kNaMaxG);
 constexpr size_t kOffU = kOffInv + align256(sizeof(u32) * kNaMaxG);
 constexpr size_t kOffState = kOffU + align256(sizeof(u64) * kNaWTp);
 constexpr size_t kOffWork = kOffState + align256(sizeof(int) * 4);
-constexpr size_t kOffCounts = kOffWork + align256(sizeof(u64) * 2);
-constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * kMaxH);
+constexpr size_t kOffCounts = kOffWork + align256(sizeof(u64) * (kWorkCount + 1));
+constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * 2 * kCountStride);
 constexpr size_t kOffCnt = kOffRes + align256(sizeof(int) * kNaRounds * (kNaMaxH + 2));
 constexpr size_t kOffSlots = kOffCnt + align256(sizeof(u64) * 2 * kNaRounds * kNaMaxH);
 constexpr size_t kOffF1 = kOffSlots + align256(sizeof(Key) * kNaMaxSlots);
 constexpr size_t kOffF2 = kOffF1 + align256(sizeof(Prefix) * kNaMaxG);
 constexpr size_t kOffF3 = kOffF2 + align256(sizeof(Prefix) * kNaFrontierCap);
-constexpr size_t kScratchBytes = kOffF3 + align256(sizeof(Prefix) * kNaFrontierCap);  // about 21 MB
+constexpr size_t kScratchBytes = kOffF3 + align256(sizeof(Prefix) * kNaFrontierCap);  // about 22 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -220,9 +221,10 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     u64 *T = (u64 *)(base + kOffT);
     u64 *N = (u64 *)(base + kOffN);
     u64 *CT = (u64 *)(base + kOffCT);
+    u64 *CN = (u64 *)(base + kOffCN);
     u16 *orig = (u16 *)(base + kOffOrig);
     u32 *inv = (u32 *)(base + kOffInv);
-    c.T = T; c.N = N; c.CT = CT; c.orig = orig; c.inv = inv;
+    c.T = T; c.N = N; c.CT = CT; c.CN = CN; c.orig = orig; c.inv = inv;
 
     Solve s;
     s.h = h;
@@ -235,10 +237,12 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.cnt = (u64 *)(base + kOffCnt);
     s.slots = (Key *)(base + kOffSlots);
     s.work = (u64 *)(base + kOffWork);
+    s.best_hint = s.work + kWorkCount;
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
     u32 *counts = (u32 *)(base + kOffCounts);
+    s.fetch = counts + kCountStride;
     Prefix *F[kMaxH] = {};
     u32 cap[kMaxH] = {};
     F[1] = (Prefix *)(base + kOffF1);
@@ -253,7 +257,8 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     NA_CUDA(cudaMemsetAsync(s.state, 0, sizeof(int) * 4, st));
     k_na_sort_keys<<<1, 1024, 0, st>>>((const u64 *)d_bitmaps, G, c.Wt, c.Wn, keys);
     k_na_pack<<<(G + 255) / 256, 256, 0, st>>>((const u64 *)d_bitmaps, c, keys, T, N, orig, inv, s.state);
-    launch_transpose(c, CT, st);
+    launch_transpose(c, T, c.WTp, Nt, CT, st);
+    launch_transpose(c, N, c.WNp, Nn, CN, st);
     NA_CUDA(cudaGetLastError());
     int hs[4] = {0, 0, 0, 0};
     NA_CUDA(cudaMemcpyAsync(hs, s.state, sizeof hs, cudaMemcpyDeviceToHost, st));
@@ -266,7 +271,7 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     bool done = Nt == 0;
     while (!done && rounds < Nt + 1) {
         const int r = rounds;
-        NA_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kMaxH, st));
+        NA_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * 2 * kCountStride, st));
         launch_level1(c, s, r, F[1], counts + 1, cap[1], st);
         for (int l = 2; l <= h - 1; ++l) {
             launch_expand(c, s, r, l, F[l - 1], counts + (l - 1), F[l], counts + l, cap[l], grid, st);

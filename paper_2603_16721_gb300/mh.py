@@ -51,7 +51,8 @@ class mh_result(ctypes.Structure):
                 ("pruned", ctypes.POINTER(ctypes.c_uint64)), ("solve_ms", ctypes.c_double),
                 ("leaf_ms", ctypes.c_double), ("leaf_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("leaf_words", ctypes.c_uint64),
-                ("leaf_prefixes", ctypes.c_uint64)]
+                ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
+                ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64)]
 
 
 _lib = None
@@ -121,6 +122,9 @@ class Result:
     kernel_launches: int
     leaf_words: int
     leaf_prefixes: int
+    leaf_scored: int = 0
+    leaf_alu_ops: int = 0
+    leaf_dense: int = 0
 
     @property
     def k(self) -> int:
@@ -145,7 +149,8 @@ def _to_result(p) -> Result:
                  pruned=arr(r.pruned, rounds * h, np.uint64).reshape(rounds, h),
                  solve_ms=float(r.solve_ms), leaf_ms=float(r.leaf_ms), leaf_launches=int(r.leaf_launches),
                  kernel_launches=int(r.kernel_launches), leaf_words=int(r.leaf_words),
-                 leaf_prefixes=int(r.leaf_prefixes))
+                 leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
+                 leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense))
     load().mh_result_free(p)
     return out
 
