@@ -227,7 +227,7 @@ def run_ours(args):
     H = mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn)
     mh.mh_set_stream(H, stream.cuda_stream)
     for _ in range(args.warmup):
-        mh.mh_solve_ex(H, H_HITS, ALPHA)
+        mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -242,7 +242,7 @@ def run_ours(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r = mh.mh_solve_ex(H, H_HITS, ALPHA, time_kernels=True)
+        r = mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds, time_kernels=True)
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -253,6 +253,12 @@ def run_ours(args):
     total_ms = sum(step_ms)
     total_ms_max, = aggregate_max([total_ms], world)
     value = world * args.steps / (total_ms_max / 1e3)
+
+    if args.kernels_only:  # profiling run: the timed solves only
+        H.close()
+        if rank == 0:
+            print(json.dumps({"kernels_only": True, "ms_per_step": total_ms / args.steps}))
+        return 0
 
     # end to end through the C ABI with host buffers: create (H2D), solve, read back
     e2e_ms = []
@@ -316,6 +322,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--max-rounds", type=int, default=0, help="stop each solve after R rounds (profiling)")
+    ap.add_argument("--kernels-only", action="store_true", help="time the solves only (profiling runs)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -22,9 +22,11 @@
 // with many samples take a row path: popcounts over the non-zero words only.
 //
 // Work distribution.  A warp takes 32 prefixes at a time from a per-depth atomic
-// counter (the analogue of the paper's chunked lambda dispatch, §III-E); each lane
-// first lists the samples of one prefix, then four groups of eight lanes sweep the
-// sparse prefixes' child ranges, and the whole warp takes the dense ones.
+// counter (the analogue of the paper's chunked lambda dispatch, §III-E).  Each
+// lane first lists the samples of one prefix; then the (prefix, column word)
+// items of the batch's sparse prefixes are spread over the 32 lanes, so
+// neighbouring lanes read neighbouring column words; dense prefixes are taken by
+// the whole warp, one at a time.
 #include "mh_internal.h"
 
 namespace mh {
@@ -33,8 +35,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBatch = 32;       // prefixes taken per warp
-constexpr int kGroup = 8;        // lanes per prefix on the sparse path
-constexpr int kGroups = 32 / kGroup;
 constexpr int kListT = 20;       // tumor samples listed per sparse prefix
 constexpr int kListN = 12;       // normal samples listed per sparse prefix
 constexpr int kPlanesT = 5;      // bit planes for counts <= 20
@@ -199,87 +199,106 @@ __device__ __forceinline__ int planes_get(const u64 (&p)[P], int b, int used)
 
 __device__ __forceinline__ int bit_length(int v) { return 32 - __clz(v); }
 
-// Per-warp scratch: one batch of prefixes and their sample lists.
-struct BatchScratch {
+// Per-warp scratch: one batch of prefixes, their sample lists and child ranges.
+struct Batch {
     Prefix p[kBatch];
-    u16 ky[kBatch], kn[kBatch];
+    int lo[kBatch], hi[kBatch];     // child range (0-based, inclusive); lo > hi when empty
+    int off[kBatch + 1];            // exclusive prefix sum of the sparse prefixes' column words
+    u16 ky[kBatch], kn[kBatch];     // samples of y_{l-1} (uncovered tumors) and n_{l-1}
     u16 ids[kBatch][kListT + kListN];
-    int po[kGroups][kMaxH];  // ascending original indices of each group's current prefix
-    u64 ys[kMaxWords];       // dense path: y_{l-1} and n_{l-1} words
+    u16 po[kBatch][kMaxH - 1];      // ascending original indices of the prefix genes (leaf)
+    u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words
     u64 ns[kMaxWords];
 };
 
-// Lane j of the warp lists the samples of prefix base+j: its tumor intersection
-// with U and its normal intersection, as sample indices when few, else only counts.
-template <bool kNormals>
-__device__ __forceinline__ void batch_load(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 count,
-                                           int L, BatchScratch &b, int lane)
+__device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT || kn > kListN; }
+
+// Lane j of the warp prepares prefix base+j: its child range, the samples of its
+// tumor intersection with U and of its normal intersection (listed when few,
+// else only counted: a "dense" prefix), and for leaves its original indices.
+// Returns the total number of column words of the batch's sparse prefixes and
+// sets the bit mask of dense prefixes; adds the children of every prefix to visited.
+template <bool kLeaf>
+__device__ __forceinline__ int batch_prepare(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 count,
+                                             int L, int hi_bound, bool all_children, Batch &b, int lane,
+                                             unsigned &dense_mask, u64 &visited)
 {
     const u32 i = base + lane;
-    int ky = 0, kn = 0;
-    if (i < count) {
+    int ky = 0, kn = 0, lo = 1, hi = 0;
+    bool valid = i < count;
+    if (valid) {
         const Prefix p = Fin[i];
         b.p[lane] = p;
-        int g[kMaxH];
+        int g[kMaxH - 1];
 #pragma unroll
         for (int q = 0; q < kMaxH - 1; ++q) g[q] = q < L ? prefix_gene(p, q) : 0;
+        lo = g[0];
+#pragma unroll
+        for (int q = 1; q < kMaxH - 1; ++q)
+            if (q < L) lo = g[q];
+        lo += 1;
+        hi = hi_bound;
         for (int w = 0; w < c.Wt; ++w) {
             u64 y = s.U[w];
 #pragma unroll
             for (int q = 0; q < kMaxH - 1; ++q)
                 if (q < L) y &= c.T[(size_t)g[q] * c.WTp + w];
             const int n = __popcll(y);
-            if (ky + n <= kListT) {
+            if (n && ky + n <= kListT) {
                 int k = ky;
-                while (y) {
-                    const int bt = __ffsll((long long)y) - 1;
+                do {
+                    b.ids[lane][k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
                     y &= y - 1;
-                    b.ids[lane][k++] = (u16)(w * 64 + bt);
-                }
+                } while (y);
             }
             ky += n;
         }
-        for (int w = 0; kNormals && w < c.Wn; ++w) {
-            u64 y = ~0ull;
+        if (kLeaf) {
+            for (int w = 0; w < c.Wn; ++w) {
+                u64 y = ~0ull;
 #pragma unroll
-            for (int q = 0; q < kMaxH - 1; ++q)
-                if (q < L) y &= c.N[(size_t)g[q] * c.WNp + w];
-            const int n = __popcll(y);
-            if (kn + n <= kListN) {
-                int k = kn;
-                while (y) {
-                    const int bt = __ffsll((long long)y) - 1;
-                    y &= y - 1;
-                    b.ids[lane][kListT + k++] = (u16)(w * 64 + bt);
+                for (int q = 0; q < kMaxH - 1; ++q)
+                    if (q < L) y &= c.N[(size_t)g[q] * c.WNp + w];
+                const int n = __popcll(y);
+                if (n && kn + n <= kListN) {
+                    int k = kn;
+                    do {
+                        b.ids[lane][kListT + k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+                        y &= y - 1;
+                    } while (y);
                 }
+                kn += n;
             }
-            kn += n;
+            // ascending original indices of the prefix genes (L <= 8)
+            for (int q = 0; q < L; ++q) {
+                const int v = c.orig[g[q < kMaxH - 1 ? q : 0]];
+                int j = q - 1;
+                while (j >= 0 && b.po[lane][j] > v) {
+                    b.po[lane][j + 1] = b.po[lane][j];
+                    --j;
+                }
+                b.po[lane][j + 1] = (u16)v;
+            }
         }
+        if (hi >= lo) visited += (u64)(hi - lo + 1);
     }
+    b.lo[lane] = lo;
+    b.hi[lane] = hi;
     b.ky[lane] = (u16)(ky < 0xffff ? ky : 0xffff);
     b.kn[lane] = (u16)(kn < 0xffff ? kn : 0xffff);
+    const bool dense = valid && hi >= lo && is_dense(ky, kn);
+    dense_mask = __ballot_sync(kFull, dense);
+    const int nw = (valid && hi >= lo && !dense && (ky > 0 || all_children)) ? (hi >> 6) - (lo >> 6) + 1 : 0;
+    const int incl = warp_incl_scan(nw, lane);
+    b.off[lane] = incl - nw;
+    if (lane == 31) b.off[kBatch] = incl;
     __syncwarp();
-}
-
-__device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT || kn > kListN; }
-
-// Ascending original indices of a prefix's genes (L <= 8), written by one lane.
-__device__ __forceinline__ void prefix_orig(const Cohort &c, const Prefix &p, int L, int *po)
-{
-    for (int i = 0; i < L; ++i) {
-        const int v = c.orig[prefix_gene(p, i)];
-        int j = i - 1;
-        while (j >= 0 && po[j] > v) {
-            po[j + 1] = po[j];
-            --j;
-        }
-        po[j + 1] = v;
-    }
+    return __shfl_sync(kFull, incl, 31);
 }
 
 // Dense path: lane w forms word w of y_{l-1} / n_{l-1} into the warp scratch.
-__device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, const Prefix &p, int L,
-                                            BatchScratch &b, unsigned &by, unsigned &bn, int lane)
+__device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, const Prefix &p, int L, Batch &b,
+                                            unsigned &by, unsigned &bn, int lane)
 {
     u64 y = 0, n = 0;
     if (lane < c.Wt) {
@@ -298,7 +317,7 @@ __device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, con
 }
 
 // OR of the sample-major columns of y_{l-1} at word wi (dense path: samples from the y words).
-__device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const BatchScratch &b, unsigned by, int wi)
+__device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const Batch &b, unsigned by, int wi)
 {
     u64 m = 0;
     for (unsigned bits = by; bits; bits &= bits - 1) {
@@ -336,6 +355,36 @@ __device__ __forceinline__ void group_append(u64 a, int wi, const Prefix &p, int
         if (pos < cap) Fout[pos] = prefix_with(p, L, wi * 64 + bt);
         ++pos;
     }
+}
+
+// Scores the non-empty leaves m of sparse prefix j at column word wi: TP / FP from
+// bit-sliced sums of the prefix's sample columns.  Returns the number scored.
+__device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Batch &b, int j, int wi, u64 m,
+                                       int L, u64 thr, Key &best)
+{
+    const int ky = b.ky[j], kn = b.kn[j];
+    const u16 *ids = b.ids[j];
+    const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
+    u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
+    u64 fpl[kPlanesN] = {0, 0, 0, 0};
+    for (int q = 0; q < ky; ++q) planes_add(tpl, c.CT[(size_t)ids[q] * c.GW + wi], pt);
+    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)ids[kListT + q] * c.GW + wi], pn);
+    int po[kMaxH - 1];
+#pragma unroll
+    for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[j][q] : 0;
+    int n = 0;
+    while (m) {
+        const int bt = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const int tp = planes_get(tpl, bt, pt);
+        const int fp = planes_get(fpl, bt, pn);
+        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+        ++n;
+        if (s1 < best.s || s1 < thr) continue;
+        const Key k = leaf_key(s1, po, L, c.orig[wi * 64 + bt]);
+        if (key_better(k, best)) best = k;
+    }
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -415,18 +464,17 @@ __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int roun
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
 // every depth-(level-1) prefix go to the depth-level frontier.
-__global__ void __launch_bounds__(kThreads) k_expand(Cohort c, Solve s, int round, int level, const Prefix *Fin,
-                                                     const u32 *nin, Prefix *Fout, u32 *nout, u32 cap)
+__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int round, int level, const Prefix *Fin,
+                                                        const u32 *nin, Prefix *Fout, u32 *nout, u32 cap)
 {
-    __shared__ BatchScratch scratch[kWarpsPerBlock];
+    __shared__ Batch scratch[kWarpsPerBlock];
     if (s.state[1]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BatchScratch &b = scratch[warp];
+    Batch &b = scratch[warp];
     const u32 count = *nin;
     const int L = level - 1;
-    const int hi = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
-    const int gi = lane / kGroup, gl = lane % kGroup;
-    const unsigned gmask = 0xffu << (gi * kGroup);
+    const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
+    const bool all_children = s.prune != 0;
     u32 *fetch = s.fetch + level;
     u64 visited = 0, alive = 0;
     for (;;) {
@@ -434,49 +482,45 @@ __global__ void __launch_bounds__(kThreads) k_expand(Cohort c, Solve s, int roun
         if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
         base = __shfl_sync(kFull, base, 0);
         if (base >= count) break;
-        const int nb = count - base < (u32)kBatch ? (int)(count - base) : kBatch;
-        batch_load<false>(c, s, Fin, base, count, L, b, lane);
-        unsigned dense = __ballot_sync(kFull, lane < nb && is_dense(b.ky[lane], b.kn[lane]));
-        // sparse prefixes: one group of 8 lanes each
-        for (int j = gi; j < nb; j += kGroups) {
-            if ((dense >> j) & 1u) continue;
-            const Prefix p = b.p[j];
-            const int lo = prefix_gene(p, L - 1) + 1;
-            if (hi < lo) continue;
-            if (gl == 0) visited += (u64)(hi - lo + 1);
-            const int ky = b.ky[j];
-            const u16 *ids = b.ids[j];
-            for (int wb = lo >> 6; wb <= (hi >> 6); wb += kGroup) {
-                const int wi = wb + gl;
-                u64 m = 0, a = 0;
-                if (wi <= (hi >> 6)) {
-                    for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
-                    const u64 r = range_word(wi, lo, hi);
-                    m &= r;
-                    a = s.prune ? r : m;
-                }
+        unsigned dense;
+        const int total = batch_prepare<false>(c, s, Fin, base, count, L, hi_bound, all_children, b, lane, dense,
+                                               visited);
+        // sparse prefixes: (prefix, column word) items spread over the lanes
+        int j = 0;
+        for (int tb = 0; tb < total; tb += 32) {
+            const int t = tb + lane;
+            u64 a = 0;
+            int wi = 0;
+            if (t < total) {
+                while (t >= b.off[j + 1]) ++j;
+                const int lo = b.lo[j], hi = b.hi[j];
+                wi = (lo >> 6) + (t - b.off[j]);
+                const int ky = b.ky[j];
+                const u16 *ids = b.ids[j];
+                u64 m = 0;
+                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
+                const u64 r = range_word(wi, lo, hi);
+                m &= r;
                 alive += (u64)__popcll(m);
-                group_append(a, wi, p, L, Fout, nout, cap, gmask, kGroup, gl);
+                a = all_children ? r : m;
             }
+            group_append(a, wi, b.p[j], L, Fout, nout, cap, kFull, 32, lane);
         }
-        __syncwarp();
         // dense prefixes: the whole warp
         while (dense) {
-            const int j = __ffs(dense) - 1;
+            const int jd = __ffs(dense) - 1;
             dense &= dense - 1;
-            const Prefix p = b.p[j];
-            const int lo = prefix_gene(p, L - 1) + 1;
-            if (hi < lo) continue;
+            const Prefix p = b.p[jd];
+            const int lo = b.lo[jd], hi = b.hi[jd];
             unsigned by, bn;
             dense_setup(c, s, p, L, b, by, bn, lane);
-            if (lane == 0) visited += (u64)(hi - lo + 1);
             for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
                 const int wi = wb + lane;
                 u64 m = 0, a = 0;
                 if (wi <= (hi >> 6)) {
                     const u64 r = range_word(wi, lo, hi);
                     m = dense_sibling_word(c, b, by, wi) & r;
-                    a = s.prune ? r : m;
+                    a = all_children ? r : m;
                 }
                 alive += (u64)__popcll(m);
                 group_append(a, wi, p, L, Fout, nout, cap, kFull, 32, lane);
@@ -494,19 +538,17 @@ __global__ void __launch_bounds__(kThreads) k_expand(Cohort c, Solve s, int roun
 // goes to the block's slot.  A prefix whose bound a_num * |y| + a_den * Nn is
 // below the best score already found anywhere cannot hold the round's winner,
 // so its leaves are tested (and counted) but not scored.
-__global__ void __launch_bounds__(kThreads) k_leaf(Cohort c, Solve s, int round, const Prefix *Fin, const u32 *nin)
+__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int round, const Prefix *Fin, const u32 *nin)
 {
-    __shared__ BatchScratch scratch[kWarpsPerBlock];
+    __shared__ Batch scratch[kWarpsPerBlock];
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    BatchScratch &b = scratch[warp];
+    Batch &b = scratch[warp];
     const bool done = s.state[1] != 0;
-    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, ops = 0, dense_n = 0;
+    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const int h = s.h, L = h - 1;
     if (!done) {
         const u32 count = *nin;
-        const int hi = c.G - 1;
-        const int gi = lane / kGroup, gl = lane % kGroup;
         u32 *fetch = s.fetch + h;
         const u64 nn_term = s.a_den * (u64)c.Nn + 1;
         for (;;) {
@@ -514,93 +556,51 @@ __global__ void __launch_bounds__(kThreads) k_leaf(Cohort c, Solve s, int round,
             if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
             base = __shfl_sync(kFull, base, 0);
             if (base >= count) break;
-            const int nb = count - base < (u32)kBatch ? (int)(count - base) : kBatch;
-            batch_load<true>(c, s, Fin, base, count, L, b, lane);
-            unsigned dense = __ballot_sync(kFull, lane < nb && is_dense(b.ky[lane], b.kn[lane]));
-            // the warp's threshold: best score seen by any block (only candidates >= it can win)
+            unsigned dense;
+            const int total = batch_prepare<true>(c, s, Fin, base, count, L, c.G - 1, false, b, lane, dense,
+                                                  visited);
+            prefixes += (u64)(base + lane < count);
+            // only candidates at least as good as the best score found anywhere can win
             u64 thr = 0;
             if (lane == 0) thr = *(volatile u64 *)s.best_hint;
             thr = warp_max_u64(thr > best.s ? thr : best.s);
-            prefixes += (u64)(lane < nb);
-            for (int j = gi; j < nb; j += kGroups) {
-                if ((dense >> j) & 1u) continue;
-                const Prefix p = b.p[j];
-                const int lo = prefix_gene(p, L - 1) + 1;
-                if (hi < lo) continue;
-                if (gl == 0) visited += (u64)(hi - lo + 1);
-                const int ky = b.ky[j], kn = b.kn[j];
-                if (ky == 0) continue;  // empty prefix (pruning off): every child is empty
+            int j = 0;
+            for (int t = lane; t < total; t += 32) {
+                while (t >= b.off[j + 1]) ++j;
+                const int lo = b.lo[j], hi = b.hi[j];
+                const int wi = (lo >> 6) + (t - b.off[j]);
+                const int ky = b.ky[j];
                 const u16 *ids = b.ids[j];
-                const bool score = s.a_num * (u64)ky + nn_term >= thr;
-                const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
-                if (score && gl == 0) prefix_orig(c, p, L, b.po[gi]);
-                __syncwarp(0xffu << (gi * kGroup));
-                for (int wb = lo >> 6; wb <= (hi >> 6); wb += kGroup) {
-                    const int wi = wb + gl;
-                    if (wi > (hi >> 6)) break;
-                    const u64 r = range_word(wi, lo, hi);
-                    u64 m = 0;
-                    if (!score) {
-                        for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
-                        m &= r;
-                        alive += (u64)__popcll(m);
-                        words += (u64)ky;
-                        ops += 2ull * ky;
-                        continue;
-                    }
-                    u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
-                    u64 fpl[kPlanesN] = {0, 0, 0, 0};
-                    for (int q = 0; q < ky; ++q) {
-                        const u64 x = c.CT[(size_t)ids[q] * c.GW + wi];
-                        m |= x;
-                        planes_add(tpl, x, pt);
-                    }
-                    m &= r;
-                    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)ids[kListT + q] * c.GW + wi], pn);
-                    alive += (u64)__popcll(m);
-                    words += (u64)(ky + kn);
-                    ops += (u64)ky * (2 + 4 * pt) + (u64)kn * 4 * pn;
-                    while (m) {
-                        const int bt = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        const int tp = planes_get(tpl, bt, pt);
-                        const int fp = planes_get(fpl, bt, pn);
-                        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-                        ++scored;
-                        ops += 14;
-                        if (s1 < best.s || s1 < thr) continue;
-                        const Key k = leaf_key(s1, b.po[gi], L, c.orig[wi * 64 + bt]);
-                        if (key_better(k, best)) best = k;
-                    }
+                u64 m = 0;
+                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
+                m &= range_word(wi, lo, hi);
+                alive += (u64)__popcll(m);
+                words += (u64)ky;
+                if (m && s.a_num * (u64)ky + nn_term >= thr) {
+                    scored += (u64)score_word(c, s, b, j, wi, m, L, thr, best);
+                    words += (u64)(ky + b.kn[j]);
                 }
-                __syncwarp(0xffu << (gi * kGroup));
             }
-            __syncwarp();
             // dense prefixes: the whole warp, leaves scored from row popcounts
             while (dense) {
-                const int j = __ffs(dense) - 1;
+                const int jd = __ffs(dense) - 1;
                 dense &= dense - 1;
-                const Prefix p = b.p[j];
-                const int lo = prefix_gene(p, L - 1) + 1;
-                if (hi < lo) continue;
-                const int ky = b.ky[j];
+                const Prefix p = b.p[jd];
+                const int lo = b.lo[jd], hi = b.hi[jd];
+                const int ky = b.ky[jd];
                 unsigned by, bn;
                 dense_setup(c, s, p, L, b, by, bn, lane);
-                if (lane == 0) {
-                    visited += (u64)(hi - lo + 1);
-                    prefix_orig(c, p, L, b.po[0]);
-                    ++dense_n;
-                }
-                __syncwarp();
+                if (lane == 0) ++dense_n;
+                int po[kMaxH - 1];
+#pragma unroll
+                for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[jd][q] : 0;
                 const bool score = s.a_num * (u64)ky + nn_term >= thr;
-                const int nzw = __popc(by) + __popc(bn);
                 for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
                     const int wi = wb + lane;
                     if (wi > (hi >> 6)) break;
                     u64 m = dense_sibling_word(c, b, by, wi) & range_word(wi, lo, hi);
                     alive += (u64)__popcll(m);
                     words += (u64)ky;
-                    ops += 2ull * ky;
                     if (!score) continue;
                     while (m) {
                         const int bt = __ffsll((long long)m) - 1;
@@ -619,9 +619,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf(Cohort c, Solve s, int round,
                         }
                         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
                         ++scored;
-                        ops += 8ull * nzw + 6;
                         if (s1 < best.s || s1 < thr) continue;
-                        const Key k = leaf_key(s1, b.po[0], L, c.orig[g]);
+                        const Key k = leaf_key(s1, po, L, c.orig[g]);
                         if (key_better(k, best)) best = k;
                     }
                 }
@@ -637,18 +636,15 @@ __global__ void __launch_bounds__(kThreads) k_leaf(Cohort c, Solve s, int round,
     words = warp_sum_u64(words);
     prefixes = warp_sum_u64(prefixes);
     scored = warp_sum_u64(scored);
-    ops = warp_sum_u64(ops);
     if (!done && lane == 0) {
         count_level(s, round, h, visited, visited - alive);
         atomicAdd(s.work + kWorkColWords, words);
         atomicAdd(s.work + kWorkPrefixes, prefixes);
         atomicAdd(s.work + kWorkScored, scored);
-        atomicAdd(s.work + kWorkAluOps, ops);
         atomicAdd(s.work + kWorkDense, dense_n);
     }
     block_commit_best(best, s.slots);
 }
-
 // End of a round: reduce the per-block bests, record the winner with its TP / FP,
 // clear the tumors it covers (DelCols) and raise the done flag when nothing was
 // found or every tumor is covered.  One block.
