@@ -213,19 +213,28 @@ struct Batch {
 
 __device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT || kn > kListN; }
 
+// Prefixes a warp takes per fetch: enough batches for every warp of the grid
+// when the frontier is small, up to kBatch when it is large.
+__device__ __forceinline__ u32 batch_size(u32 count)
+{
+    const u32 warps = gridDim.x * kWarpsPerBlock;
+    const u32 nb = (count + warps - 1) / warps;
+    return nb < 1 ? 1 : (nb > (u32)kBatch ? (u32)kBatch : nb);
+}
+
 // Lane j of the warp prepares prefix base+j: its child range, the samples of its
 // tumor intersection with U and of its normal intersection (listed when few,
 // else only counted: a "dense" prefix), and for leaves its original indices.
 // Returns the total number of column words of the batch's sparse prefixes and
 // sets the bit mask of dense prefixes; adds the children of every prefix to visited.
 template <bool kLeaf>
-__device__ __forceinline__ int batch_prepare(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 count,
+__device__ __forceinline__ int batch_prepare(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 end,
                                              int L, int hi_bound, bool all_children, Batch &b, int lane,
                                              unsigned &dense_mask, u64 &visited)
 {
     const u32 i = base + lane;
     int ky = 0, kn = 0, lo = 1, hi = 0;
-    bool valid = i < count;
+    bool valid = i < end;
     if (valid) {
         const Prefix p = Fin[i];
         b.p[lane] = p;
@@ -476,14 +485,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
     const bool all_children = s.prune != 0;
     u32 *fetch = s.fetch + level;
+    const u32 nb = batch_size(count);
     u64 visited = 0, alive = 0;
     for (;;) {
         u32 base = 0;
-        if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
+        if (lane == 0) base = atomicAdd(fetch, nb);
         base = __shfl_sync(kFull, base, 0);
         if (base >= count) break;
+        const u32 end = count - base < nb ? count : base + nb;
         unsigned dense;
-        const int total = batch_prepare<false>(c, s, Fin, base, count, L, hi_bound, all_children, b, lane, dense,
+        const int total = batch_prepare<false>(c, s, Fin, base, end, L, hi_bound, all_children, b, lane, dense,
                                                visited);
         // sparse prefixes: (prefix, column word) items spread over the lanes
         int j = 0;
@@ -550,16 +561,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
     if (!done) {
         const u32 count = *nin;
         u32 *fetch = s.fetch + h;
+        const u32 nb = batch_size(count);
         const u64 nn_term = s.a_den * (u64)c.Nn + 1;
         for (;;) {
             u32 base = 0;
-            if (lane == 0) base = atomicAdd(fetch, (u32)kBatch);
+            if (lane == 0) base = atomicAdd(fetch, nb);
             base = __shfl_sync(kFull, base, 0);
             if (base >= count) break;
+            const u32 end = count - base < nb ? count : base + nb;
             unsigned dense;
-            const int total = batch_prepare<true>(c, s, Fin, base, count, L, c.G - 1, false, b, lane, dense,
+            const int total = batch_prepare<true>(c, s, Fin, base, end, L, c.G - 1, false, b, lane, dense,
                                                   visited);
-            prefixes += (u64)(base + lane < count);
+            prefixes += (u64)(base + lane < end);
             // only candidates at least as good as the best score found anywhere can win
             u64 thr = 0;
             if (lane == 0) thr = *(volatile u64 *)s.best_hint;
@@ -647,65 +660,107 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
 }
 // End of a round: reduce the per-block bests, record the winner with its TP / FP,
 // clear the tumors it covers (DelCols) and raise the done flag when nothing was
-// found or every tumor is covered.  One block.
+// found or every tumor is covered.  The other blocks' bests are then re-scored
+// against the new U; the largest re-scored value belongs to a combination that is
+// still a candidate in the next round, so it is a lower bound on that round's
+// best and lets the next search skip scoring that cannot reach it.  One block.
 __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int round)
 {
     __shared__ Key wbest[kWarpsPerBlock];
+    __shared__ u64 whint[kWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
+    __shared__ int finished;
     if (s.state[1]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = s.h;
     Key best = key_empty();
     for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
         const Key k = s.slots[i];
         if (key_better(k, best)) best = k;
-        s.slots[i] = key_empty();
     }
     best = warp_max_key(best);
     if (lane == 0) wbest[warp] = best;
     __syncthreads();
-    if (warp != 0) return;
-    best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
-    best = warp_max_key(best);
-    if (lane == 0) *s.best_hint = 0;
-    if (best.s == 0) {
-        if (lane == 0) s.state[1] = 1;
-        return;
+    if (warp == 0) {
+        best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
+        best = warp_max_key(best);
+        if (best.s == 0) {
+            if (lane == 0) {
+                s.state[1] = 1;
+                finished = 1;
+            }
+        } else {
+            if (lane < h) {
+                const int o = key_get(best, lane);
+                os[lane] = o;
+                gs[lane] = (int)c.inv[o];
+            }
+            __syncwarp();
+            u64 y = 0, n = 0;
+            if (lane < c.Wt) {
+                y = s.U[lane];
+                for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+            }
+            if (lane < c.Wn) {
+                n = ~0ull;
+                for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
+            }
+            int tp = __popcll(y), fp = __popcll(n);
+            for (int off = 16; off; off >>= 1) {
+                tp += __shfl_xor_sync(kFull, tp, off);
+                fp += __shfl_xor_sync(kFull, fp, off);
+            }
+            u64 u = 0;
+            if (lane < c.Wt) {
+                u = s.U[lane] & ~y;
+                s.U[lane] = u;
+            }
+            const unsigned left = __ballot_sync(kFull, u != 0);
+            if (lane == 0) {
+                const int k = s.state[0];
+                int *r = s.res + (size_t)k * (h + 2);
+                for (int i = 0; i < h; ++i) r[i] = os[i];
+                r[h] = tp;
+                r[h + 1] = fp;
+                s.state[0] = k + 1;
+                if (!left) s.state[1] = 1;
+                finished = !left;
+            }
+        }
     }
-    const int h = s.h;
-    if (lane < h) {
-        const int o = key_get(best, lane);
-        os[lane] = o;
-        gs[lane] = (int)c.inv[o];
+    __syncthreads();
+    // re-score the other candidates against the new U (threadfence: U was written above)
+    __threadfence_block();
+    u64 hint = 0;
+    for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
+        const Key k = s.slots[i];
+        s.slots[i] = key_empty();
+        if (k.s == 0 || finished) continue;
+        int g[kMaxH];
+        for (int q = 0; q < h; ++q) g[q < kMaxH ? q : 0] = (int)c.inv[key_get(k, q)];
+        int tp = 0;
+        for (int w = 0; w < c.Wt; ++w) {
+            u64 y = s.U[w];
+            for (int q = 0; q < h; ++q) y &= c.T[(size_t)g[q < kMaxH ? q : 0] * c.WTp + w];
+            tp += __popcll(y);
+        }
+        if (tp == 0) continue;
+        int fp = 0;
+        for (int w = 0; w < c.Wn; ++w) {
+            u64 n = ~0ull;
+            for (int q = 0; q < h; ++q) n &= c.N[(size_t)g[q < kMaxH ? q : 0] * c.WNp + w];
+            fp += __popcll(n);
+        }
+        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+        hint = s1 > hint ? s1 : hint;
     }
-    __syncwarp();
-    u64 y = 0, n = 0;
-    if (lane < c.Wt) {
-        y = s.U[lane];
-        for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
-    }
-    if (lane < c.Wn) {
-        n = ~0ull;
-        for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
-    }
-    int tp = __popcll(y), fp = __popcll(n);
-    for (int off = 16; off; off >>= 1) {
-        tp += __shfl_xor_sync(kFull, tp, off);
-        fp += __shfl_xor_sync(kFull, fp, off);
-    }
-    u64 u = 0;
-    if (lane < c.Wt) {
-        u = s.U[lane] & ~y;
-        s.U[lane] = u;
-    }
-    const unsigned left = __ballot_sync(kFull, u != 0);
-    if (lane == 0) {
-        const int k = s.state[0];
-        int *r = s.res + (size_t)k * (h + 2);
-        for (int i = 0; i < h; ++i) r[i] = os[i];
-        r[h] = tp;
-        r[h + 1] = fp;
-        s.state[0] = k + 1;
-        if (!left) s.state[1] = 1;
+    hint = warp_max_u64(hint);
+    if (lane == 0) whint[warp] = hint;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 m = 0;
+        for (int i = 0; i < kWarpsPerBlock; ++i) m = whint[i] > m ? whint[i] : m;
+        *s.best_hint = m;
     }
 }
 
