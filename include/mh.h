@@ -146,7 +146,7 @@ MH_API const char *mh_last_error(void);
  * code running while another component owns all device memory through its own
  * pool, plug-ins handed fixed buffers by a host framework, or latency-critical
  * streams that must not see allocator traffic -- every piece of scratch lives
- * in one file-scope __device__ array of about 22 MB that every GPU loading this
+ * in one file-scope __device__ array of about 30 MB that every GPU loading this
  * library keeps until the process exits.  It returns the same selections as
  * mh_solve(h, alpha) with MH_PRUNE_PAPER.
  *   d_bitmaps : DEVICE pointer to packed rows (layout above), caller-owned, read only.
@@ -156,7 +156,7 @@ MH_API const char *mh_last_error(void);
  *   k_out     : HOST pointer receiving the number of selections; rounds_out (HOST, may be NULL)
  *               receives the number of greedy rounds searched.
  *   stream    : cudaStream_t (NULL = legacy default stream); the call is synchronous.
- * Limits: G <= 8192, Nt <= 1024, Nn <= 1024, 1 <= h <= 4, and at most 2^19
+ * Limits: G <= 8192, Nt <= 1024, Nn <= 1024, 1 <= h <= 4, and at most 2^17
  * prefixes per intermediate depth of the search; larger inputs return MH_EINVAL,
  * a larger frontier MH_ENOMEM, each with a message naming the limit.  The first
  * call on a device looks up the array's device address (once per device); make

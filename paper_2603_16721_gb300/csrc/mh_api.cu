@@ -86,7 +86,7 @@ struct mh_handle {
     int *dState = nullptr, *dRes = nullptr;
     Key *dSlots = nullptr;
     u32 *dCounts = nullptr;               // frontier sizes, one per depth, then work-distribution counters
-    Prefix *dF[kMaxH] = {};               // frontier of depth l at index l
+    Rec *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
     int *hState = nullptr;                // pinned: state + frontier counts
     int64_t frontier_bytes = 0;
@@ -203,11 +203,11 @@ int ensure_frontier(mh_handle *H, int l, u64 n)
     if (n <= H->cap[l]) return MH_OK;
     u64 want = std::max<u64>(n + n / 4, 1u << 16);
     if (want > 0xffffffffull) want = 0xffffffffull;
-    const int64_t old_bytes = (int64_t)H->cap[l] * (int64_t)sizeof(Prefix);
-    const int64_t new_bytes = (int64_t)want * (int64_t)sizeof(Prefix);
+    const int64_t old_bytes = (int64_t)H->cap[l] * (int64_t)sizeof(Rec);
+    const int64_t new_bytes = (int64_t)want * (int64_t)sizeof(Rec);
     if ((size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget() || n > 0xffffffffull)
         return fail(MH_ENOMEM, "depth-%d frontier needs %llu entries (%.1f GB), above the frontier budget", l,
-                    (unsigned long long)n, (double)n * sizeof(Prefix) / 1e9);
+                    (unsigned long long)n, (double)n * sizeof(Rec) / 1e9);
     MH_CUDA(cudaStreamSynchronize(H->stream));
     cudaFree(H->dF[l]);
     H->dF[l] = nullptr;

@@ -48,6 +48,19 @@ struct Prefix {
     u64 w0, w1;
 };
 
+// A node of the search frontier: the prefix and the samples of its
+// intersections, listed when few (ky <= kListT and kn <= kListN: "sparse"),
+// otherwise only counted ("dense": consumers rebuild them from the rows).
+constexpr int kListT = 20;  // tumor samples listed per sparse node
+constexpr int kListN = 12;  // normal samples listed per sparse node
+struct __align__(16) Rec {
+    Prefix p;
+    u16 ky, kn;                  // |y| (uncovered tumors) and |n| (normals), saturated at 0xffff
+    u16 ids[kListT + kListN];    // tumor sample indices, then normal sample indices
+    u32 pad[3];
+};
+static_assert(sizeof(Rec) == 96, "frontier records are 96 bytes");
+
 // Per-solve device state.
 struct Solve {
     int h;
@@ -77,10 +90,10 @@ enum {
 // Launchers (mh_kernels.cu).
 void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
 void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st);
-void launch_level1(const Cohort &c, const Solve &s, int round, Prefix *F1, u32 *n1, u32 cap1, cudaStream_t st);
-void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Prefix *Fin, const u32 *nin,
-                   Prefix *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st);
-void launch_leaf(const Cohort &c, const Solve &s, int round, const Prefix *Fin, const u32 *nin, int grid,
+void launch_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st);
+void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, const u32 *nin,
+                   Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st);
+void launch_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, const u32 *nin, int grid,
                  cudaStream_t st);
 void launch_finalize(const Cohort &c, const Solve &s, int round, cudaStream_t st);
 int level1_grid(const Cohort &c);

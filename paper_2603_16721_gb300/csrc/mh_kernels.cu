@@ -35,8 +35,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBatch = 32;       // prefixes taken per warp
-constexpr int kListT = 20;       // tumor samples listed per sparse prefix
-constexpr int kListN = 12;       // normal samples listed per sparse prefix
 constexpr int kPlanesT = 5;      // bit planes for counts <= 20
 constexpr int kPlanesN = 4;      // bit planes for counts <= 12
 
@@ -199,19 +197,9 @@ __device__ __forceinline__ int planes_get(const u64 (&p)[P], int b, int used)
 
 __device__ __forceinline__ int bit_length(int v) { return 32 - __clz(v); }
 
-// Per-warp scratch: one batch of prefixes, their sample lists and child ranges.
-struct Batch {
-    Prefix p[kBatch];
-    int lo[kBatch], hi[kBatch];     // child range (0-based, inclusive); lo > hi when empty
-    int off[kBatch + 1];            // exclusive prefix sum of the sparse prefixes' column words
-    u16 ky[kBatch], kn[kBatch];     // samples of y_{l-1} (uncovered tumors) and n_{l-1}
-    u16 ids[kBatch][kListT + kListN];
-    u16 po[kBatch][kMaxH - 1];      // ascending original indices of the prefix genes (leaf)
-    u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words
-    u64 ns[kMaxWords];
-};
-
 __device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT || kn > kListN; }
+
+__device__ __forceinline__ u16 sat16(int v) { return (u16)(v < 0xffff ? v : 0xffff); }
 
 // Prefixes a warp takes per fetch: enough batches for every warp of the grid
 // when the frontier is small, up to kBatch when it is large.
@@ -222,82 +210,48 @@ __device__ __forceinline__ u32 batch_size(u32 count)
     return nb < 1 ? 1 : (nb > (u32)kBatch ? (u32)kBatch : nb);
 }
 
-// Lane j of the warp prepares prefix base+j: its child range, the samples of its
-// tumor intersection with U and of its normal intersection (listed when few,
-// else only counted: a "dense" prefix), and for leaves its original indices.
-// Returns the total number of column words of the batch's sparse prefixes and
-// sets the bit mask of dense prefixes; adds the children of every prefix to visited.
-template <bool kLeaf>
-__device__ __forceinline__ int batch_prepare(const Cohort &c, const Solve &s, const Prefix *Fin, u32 base, u32 end,
-                                             int L, int hi_bound, bool all_children, Batch &b, int lane,
-                                             unsigned &dense_mask, u64 &visited)
+__device__ __forceinline__ void copy_rec(Rec *dst, const Rec *src)
+{
+    const uint4 *a = reinterpret_cast<const uint4 *>(src);
+    uint4 *b = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(Rec) / 16); ++i) b[i] = a[i];
+}
+
+// Per-warp scratch: one batch of frontier records and their child ranges.
+struct Batch {
+    Rec r[kBatch];
+    int lo[kBatch], hi[kBatch];     // child range (0-based, inclusive); lo > hi when empty
+    int off[kBatch + 1];            // exclusive prefix sum of the sparse records' column words
+    u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words
+    u64 ns[kMaxWords];
+};
+
+// Lane j takes record base+j (if < end) into the warp scratch with its child
+// range [last gene + 1, hi_bound]; counts its children as visited.  Returns the
+// number of column words of the batch's sparse records (those with samples, or
+// all of them with `all_children`) and the bit mask of dense records.
+__device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 base, u32 end, int L, int hi_bound,
+                                             bool all_children, Batch &b, int lane, unsigned &dense_mask,
+                                             u64 &visited)
 {
     const u32 i = base + lane;
-    int ky = 0, kn = 0, lo = 1, hi = 0;
-    bool valid = i < end;
+    const bool valid = i < end;
+    int lo = 1, hi = 0, ky = 0, kn = 0;
     if (valid) {
-        const Prefix p = Fin[i];
-        b.p[lane] = p;
-        int g[kMaxH - 1];
-#pragma unroll
-        for (int q = 0; q < kMaxH - 1; ++q) g[q] = q < L ? prefix_gene(p, q) : 0;
-        lo = g[0];
-#pragma unroll
-        for (int q = 1; q < kMaxH - 1; ++q)
-            if (q < L) lo = g[q];
-        lo += 1;
+        copy_rec(&b.r[lane], &Fin[i]);
+        lo = prefix_gene(b.r[lane].p, L - 1) + 1;
         hi = hi_bound;
-        for (int w = 0; w < c.Wt; ++w) {
-            u64 y = s.U[w];
-#pragma unroll
-            for (int q = 0; q < kMaxH - 1; ++q)
-                if (q < L) y &= c.T[(size_t)g[q] * c.WTp + w];
-            const int n = __popcll(y);
-            if (n && ky + n <= kListT) {
-                int k = ky;
-                do {
-                    b.ids[lane][k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
-                    y &= y - 1;
-                } while (y);
-            }
-            ky += n;
-        }
-        if (kLeaf) {
-            for (int w = 0; w < c.Wn; ++w) {
-                u64 y = ~0ull;
-#pragma unroll
-                for (int q = 0; q < kMaxH - 1; ++q)
-                    if (q < L) y &= c.N[(size_t)g[q] * c.WNp + w];
-                const int n = __popcll(y);
-                if (n && kn + n <= kListN) {
-                    int k = kn;
-                    do {
-                        b.ids[lane][kListT + k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
-                        y &= y - 1;
-                    } while (y);
-                }
-                kn += n;
-            }
-            // ascending original indices of the prefix genes (L <= 8)
-            for (int q = 0; q < L; ++q) {
-                const int v = c.orig[g[q < kMaxH - 1 ? q : 0]];
-                int j = q - 1;
-                while (j >= 0 && b.po[lane][j] > v) {
-                    b.po[lane][j + 1] = b.po[lane][j];
-                    --j;
-                }
-                b.po[lane][j + 1] = (u16)v;
-            }
-        }
+        ky = b.r[lane].ky;
+        kn = b.r[lane].kn;
         if (hi >= lo) visited += (u64)(hi - lo + 1);
     }
     b.lo[lane] = lo;
     b.hi[lane] = hi;
-    b.ky[lane] = (u16)(ky < 0xffff ? ky : 0xffff);
-    b.kn[lane] = (u16)(kn < 0xffff ? kn : 0xffff);
-    const bool dense = valid && hi >= lo && is_dense(ky, kn);
+    const bool live = valid && hi >= lo;
+    const bool dense = live && is_dense(ky, kn);
     dense_mask = __ballot_sync(kFull, dense);
-    const int nw = (valid && hi >= lo && !dense && (ky > 0 || all_children)) ? (hi >> 6) - (lo >> 6) + 1 : 0;
+    const int nw = (live && !dense && (ky > 0 || all_children)) ? (hi >> 6) - (lo >> 6) + 1 : 0;
     const int incl = warp_incl_scan(nw, lane);
     b.off[lane] = incl - nw;
     if (lane == 31) b.off[kBatch] = incl;
@@ -341,46 +295,92 @@ __device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const Batch &
     return m;
 }
 
-// Appends the set bits of `a` (children g = wi*64+bit of prefix p at position L) to
-// Fout with one atomic per group of `width` lanes (all lanes of the group call it).
-__device__ __forceinline__ void group_append(u64 a, int wi, const Prefix &p, int L, Prefix *Fout, u32 *nout,
-                                             u32 cap, unsigned mask, int width, int gl)
+// Reserves n consecutive frontier slots for each lane with one atomic per warp.
+__device__ __forceinline__ u32 warp_reserve(int n, u32 *nout, int lane)
 {
-    const int cnt = __popcll(a);
-    int incl = cnt;
-    for (int off = 1; off < width; off <<= 1) {
-        const int o = __shfl_up_sync(mask, incl, off, width);
-        if (gl >= off) incl += o;
-    }
-    const int total = __shfl_sync(mask, incl, width - 1, width);
-    if (total == 0) return;
+    const int incl = warp_incl_scan(n, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
     u32 base = 0;
-    if (gl == 0) base = atomicAdd(nout, (u32)total);
-    base = __shfl_sync(mask, base, 0, width);
-    u32 pos = base + (u32)(incl - cnt);
-    while (a) {
-        const int bt = __ffsll((long long)a) - 1;
-        a &= a - 1;
-        if (pos < cap) Fout[pos] = prefix_with(p, L, wi * 64 + bt);
-        ++pos;
+    if (total && lane == 0) base = atomicAdd(nout, (u32)total);
+    base = __shfl_sync(kFull, base, 0);
+    return base + (u32)(incl - n);
+}
+
+// Child record of a sparse parent: its samples are the parent's samples whose
+// column word wi has bit bt set.
+__device__ __forceinline__ void child_from_lists(const Cohort &c, const Rec &parent, int L, int wi, int bt,
+                                                 Rec &out)
+{
+    out.p = prefix_with(parent.p, L, wi * 64 + bt);
+    int ky = 0, kn = 0;
+    for (int q = 0; q < parent.ky; ++q) {
+        const int sm = parent.ids[q];
+        if ((c.CT[(size_t)sm * c.GW + wi] >> bt) & 1ull) out.ids[ky++] = (u16)sm;
+    }
+    for (int q = 0; q < parent.kn; ++q) {
+        const int sm = parent.ids[kListT + q];
+        if ((c.CN[(size_t)sm * c.GW + wi] >> bt) & 1ull) out.ids[kListT + kn++] = (u16)sm;
+    }
+    out.ky = (u16)ky;
+    out.kn = (u16)kn;
+}
+
+// Child record of a dense parent (its y / n words in the warp scratch): samples
+// from the rows of the child gene g, listed if few.
+__device__ __forceinline__ void child_from_rows(const Cohort &c, const Batch &b, unsigned by, unsigned bn,
+                                                const Prefix &parent, int L, int g, Rec &out)
+{
+    out.p = prefix_with(parent, L, g);
+    const u64 *trow = c.T + (size_t)g * c.WTp;
+    const u64 *nrow = c.N + (size_t)g * c.WNp;
+    int ky = 0, kn = 0;
+    for (unsigned bits = by; bits; bits &= bits - 1) ky += __popcll(b.ys[__ffs(bits) - 1] & trow[__ffs(bits) - 1]);
+    for (unsigned bits = bn; bits; bits &= bits - 1) kn += __popcll(b.ns[__ffs(bits) - 1] & nrow[__ffs(bits) - 1]);
+    if (!is_dense(ky, kn)) {
+        int k = 0;
+        for (unsigned bits = by; bits; bits &= bits - 1) {
+            const int w = __ffs(bits) - 1;
+            for (u64 y = b.ys[w] & trow[w]; y; y &= y - 1) out.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        }
+        k = kListT;
+        for (unsigned bits = bn; bits; bits &= bits - 1) {
+            const int w = __ffs(bits) - 1;
+            for (u64 y = b.ns[w] & nrow[w]; y; y &= y - 1) out.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        }
+    }
+    out.ky = sat16(ky);
+    out.kn = sat16(kn);
+}
+
+// Ascending original indices of the L genes of a prefix.
+__device__ __forceinline__ void prefix_orig(const Cohort &c, const Prefix &p, int L, int (&po)[kMaxH - 1])
+{
+#pragma unroll
+    for (int i = 0; i < kMaxH - 1; ++i) po[i] = 0;
+    for (int i = 0; i < L; ++i) {
+        const int v = c.orig[prefix_gene(p, i)];
+        int j = i - 1;
+        while (j >= 0 && po[j < 0 ? 0 : j] > v) {
+            po[j + 1] = po[j];
+            --j;
+        }
+        po[j + 1] = v;
     }
 }
 
-// Scores the non-empty leaves m of sparse prefix j at column word wi: TP / FP from
-// bit-sliced sums of the prefix's sample columns.  Returns the number scored.
-__device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Batch &b, int j, int wi, u64 m,
-                                       int L, u64 thr, Key &best)
+// Scores the non-empty leaves m of sparse record r at column word wi: TP / FP
+// from bit-sliced sums of the record's sample columns.  Returns the number scored.
+__device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Rec &r, int wi, u64 m, int L, u64 thr,
+                                       Key &best)
 {
-    const int ky = b.ky[j], kn = b.kn[j];
-    const u16 *ids = b.ids[j];
+    const int ky = r.ky, kn = r.kn;
     const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
     u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
     u64 fpl[kPlanesN] = {0, 0, 0, 0};
-    for (int q = 0; q < ky; ++q) planes_add(tpl, c.CT[(size_t)ids[q] * c.GW + wi], pt);
-    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)ids[kListT + q] * c.GW + wi], pn);
+    for (int q = 0; q < ky; ++q) planes_add(tpl, c.CT[(size_t)r.ids[q] * c.GW + wi], pt);
+    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)r.ids[kListT + q] * c.GW + wi], pn);
     int po[kMaxH - 1];
-#pragma unroll
-    for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[j][q] : 0;
+    bool have_po = false;
     int n = 0;
     while (m) {
         const int bt = __ffsll((long long)m) - 1;
@@ -390,6 +390,10 @@ __device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Ba
         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
         ++n;
         if (s1 < best.s || s1 < thr) continue;
+        if (!have_po) {
+            prefix_orig(c, r.p, L, po);
+            have_po = true;
+        }
         const Key k = leaf_key(s1, po, L, c.orig[wi * 64 + bt]);
         if (key_better(k, best)) best = k;
     }
@@ -423,23 +427,56 @@ __global__ void k_solve_init(Cohort c, Solve s)
     if (w < 4) s.state[w] = 0;
 }
 
+// Re-scores the previous round's per-block bests against the current U (one warp
+// per key, lane w on word w) and clears them.  A key still covering an uncovered
+// tumor is a candidate of this round, so the largest value is a lower bound on
+// this round's best: the leaf kernel need not score what cannot reach it.
+__device__ void rescore_slots(const Cohort &c, const Solve &s)
+{
+    const int lane = threadIdx.x & 31;
+    const int h = s.h;
+    u64 hint = 0;
+    for (int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); i < s.nslots; i += gridDim.x * kWarpsPerBlock) {
+        const Key k = s.slots[i];
+        if (k.s == 0) continue;
+        u64 y = 0, n = 0;
+        if (lane < c.Wt) y = s.U[lane];
+        if (lane < c.Wn) n = ~0ull;
+        for (int q = 0; q < h; ++q) {
+            const int g = (int)c.inv[key_get(k, q)];
+            if (lane < c.Wt) y &= c.T[(size_t)g * c.WTp + lane];
+            if (lane < c.Wn) n &= c.N[(size_t)g * c.WNp + lane];
+        }
+        int tp = __popcll(y), fp = __popcll(n);
+        for (int off = 16; off; off >>= 1) {
+            tp += __shfl_xor_sync(kFull, tp, off);
+            fp += __shfl_xor_sync(kFull, fp, off);
+        }
+        if (lane == 0) s.slots[i] = key_empty();
+        if (tp == 0) continue;
+        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+        hint = s1 > hint ? s1 : hint;
+    }
+    if (lane == 0 && hint) atomicMax(s.best_hint, hint);
+}
+
 // Depth 1: y_1(g) = U & x_g for g in [0, G-h] (0-based).  For h = 1 these are
 // the leaves and are scored here; otherwise the non-empty ones (all of them with
-// pruning off) become the depth-1 frontier.
-__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int round, Prefix *F1, u32 *n1, u32 cap1)
+// pruning off) become depth-1 records.
+__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int round, Rec *F1, u32 *n1, u32 cap1)
 {
     if (s.state[1]) return;
     const int lane = threadIdx.x & 31;
+    if (s.h > 1) rescore_slots(c, s);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int last = c.G - s.h;  // 0-based inclusive bound of depth 1
     const bool in = g <= last;
-    bool nonempty = false;
-    int tp = 0;
+    int ky = 0;
     if (in) {
         const u64 *row = c.T + (size_t)g * c.WTp;
-        for (int w = 0; w < c.Wt; ++w) tp += __popcll(row[w] & s.U[w]);
-        nonempty = tp > 0;
+        for (int w = 0; w < c.Wt; ++w) ky += __popcll(row[w] & s.U[w]);
     }
+    const bool nonempty = ky > 0;
     const unsigned bin = __ballot_sync(kFull, in), bne = __ballot_sync(kFull, nonempty);
     if (lane == 0) count_level(s, round, 1, (u64)__popc(bin), (u64)__popc(bin & ~bne));
     if (s.h == 1) {
@@ -448,33 +485,40 @@ __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int roun
             int fp = 0;
             const u64 *nrow = c.N + (size_t)g * c.WNp;
             for (int w = 0; w < c.Wn; ++w) fp += __popcll(nrow[w]);
-            best.s = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+            best.s = s.a_num * (u64)ky + s.a_den * (u64)(c.Nn - fp) + 1;
             key_put(best, 0, c.orig[g]);
         }
         block_commit_best(best, s.slots);
         return;
     }
     const bool keep = s.prune ? in : nonempty;
-    const unsigned bk = __ballot_sync(kFull, keep);
-    if (!bk) return;
-    u32 base = 0;
-    if (lane == 0) base = atomicAdd(n1, (u32)__popc(bk));
-    base = __shfl_sync(kFull, base, 0);
-    if (keep) {
-        const u32 pos = base + __popc(bk & ((1u << lane) - 1u));
-        if (pos < cap1) {
-            Prefix p;
-            p.w0 = (u64)g;
-            p.w1 = 0;
-            F1[pos] = p;
-        }
+    const u32 pos = warp_reserve(keep ? 1 : 0, n1, lane);
+    if (!keep || pos >= cap1) return;
+    Rec r;
+    r.p.w0 = (u64)g;
+    r.p.w1 = 0;
+    r.pad[0] = r.pad[1] = r.pad[2] = 0;
+    const u64 *trow = c.T + (size_t)g * c.WTp;
+    const u64 *nrow = c.N + (size_t)g * c.WNp;
+    int kn = 0;
+    for (int w = 0; w < c.Wn; ++w) kn += __popcll(nrow[w]);
+    if (!is_dense(ky, kn)) {
+        int k = 0;
+        for (int w = 0; w < c.Wt; ++w)
+            for (u64 y = trow[w] & s.U[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        k = kListT;
+        for (int w = 0; w < c.Wn; ++w)
+            for (u64 y = nrow[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
     }
+    r.ky = sat16(ky);
+    r.kn = sat16(kn);
+    copy_rec(&F1[pos], &r);
 }
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
-// every depth-(level-1) prefix go to the depth-level frontier.
-__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int round, int level, const Prefix *Fin,
-                                                        const u32 *nin, Prefix *Fout, u32 *nout, u32 cap)
+// every depth-(level-1) record become depth-level records.
+__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int round, int level, const Rec *Fin,
+                                                        const u32 *nin, Rec *Fout, u32 *nout, u32 cap)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (s.state[1]) return;
@@ -494,9 +538,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
         if (base >= count) break;
         const u32 end = count - base < nb ? count : base + nb;
         unsigned dense;
-        const int total = batch_prepare<false>(c, s, Fin, base, end, L, hi_bound, all_children, b, lane, dense,
-                                               visited);
-        // sparse prefixes: (prefix, column word) items spread over the lanes
+        const int total = batch_prepare(Fin, base, end, L, hi_bound, all_children, b, lane, dense, visited);
+        // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32) {
             const int t = tb + lane;
@@ -506,22 +549,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
                 while (t >= b.off[j + 1]) ++j;
                 const int lo = b.lo[j], hi = b.hi[j];
                 wi = (lo >> 6) + (t - b.off[j]);
-                const int ky = b.ky[j];
-                const u16 *ids = b.ids[j];
+                const Rec &r = b.r[j];
                 u64 m = 0;
-                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
-                const u64 r = range_word(wi, lo, hi);
-                m &= r;
+                for (int q = 0; q < r.ky; ++q) m |= c.CT[(size_t)r.ids[q] * c.GW + wi];
+                const u64 rw = range_word(wi, lo, hi);
+                m &= rw;
                 alive += (u64)__popcll(m);
-                a = all_children ? r : m;
+                a = all_children ? rw : m;
             }
-            group_append(a, wi, b.p[j], L, Fout, nout, cap, kFull, 32, lane);
+            u32 pos = warp_reserve(__popcll(a), nout, lane);
+            while (a) {
+                const int bt = __ffsll((long long)a) - 1;
+                a &= a - 1;
+                if (pos < cap) {
+                    Rec child;
+                    child.pad[0] = child.pad[1] = child.pad[2] = 0;
+                    child_from_lists(c, b.r[j], L, wi, bt, child);
+                    copy_rec(&Fout[pos], &child);
+                }
+                ++pos;
+            }
         }
-        // dense prefixes: the whole warp
+        // dense records: the whole warp
         while (dense) {
             const int jd = __ffs(dense) - 1;
             dense &= dense - 1;
-            const Prefix p = b.p[jd];
+            const Prefix p = b.r[jd].p;
             const int lo = b.lo[jd], hi = b.hi[jd];
             unsigned by, bn;
             dense_setup(c, s, p, L, b, by, bn, lane);
@@ -529,12 +582,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
                 const int wi = wb + lane;
                 u64 m = 0, a = 0;
                 if (wi <= (hi >> 6)) {
-                    const u64 r = range_word(wi, lo, hi);
-                    m = dense_sibling_word(c, b, by, wi) & r;
-                    a = all_children ? r : m;
+                    const u64 rw = range_word(wi, lo, hi);
+                    m = dense_sibling_word(c, b, by, wi) & rw;
+                    a = all_children ? rw : m;
                 }
                 alive += (u64)__popcll(m);
-                group_append(a, wi, p, L, Fout, nout, cap, kFull, 32, lane);
+                u32 pos = warp_reserve(__popcll(a), nout, lane);
+                while (a) {
+                    const int bt = __ffsll((long long)a) - 1;
+                    a &= a - 1;
+                    if (pos < cap) {
+                        Rec child;
+                        child.pad[0] = child.pad[1] = child.pad[2] = 0;
+                        child_from_rows(c, b, by, bn, p, L, wi * 64 + bt, child);
+                        copy_rec(&Fout[pos], &child);
+                    }
+                    ++pos;
+                }
             }
             __syncwarp();
         }
@@ -546,10 +610,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
 
 // Depth h (leaves): every non-empty leaf is a candidate with score
 // S = a_num * TP + a_den * (Nn - FP); the best (score desc, original tuple asc)
-// goes to the block's slot.  A prefix whose bound a_num * |y| + a_den * Nn is
-// below the best score already found anywhere cannot hold the round's winner,
-// so its leaves are tested (and counted) but not scored.
-__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int round, const Prefix *Fin, const u32 *nin)
+// goes to the block's slot.  A record whose bound a_num * |y| + a_den * Nn is
+// below the best score known to exist cannot hold the round's winner, so its
+// leaves are tested (and counted) but not scored.
+__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int round, const Rec *Fin, const u32 *nin)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     Key best = key_empty();
@@ -570,10 +634,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
             if (base >= count) break;
             const u32 end = count - base < nb ? count : base + nb;
             unsigned dense;
-            const int total = batch_prepare<true>(c, s, Fin, base, end, L, c.G - 1, false, b, lane, dense,
-                                                  visited);
+            const int total = batch_prepare(Fin, base, end, L, c.G - 1, false, b, lane, dense, visited);
             prefixes += (u64)(base + lane < end);
-            // only candidates at least as good as the best score found anywhere can win
+            // only candidates at least as good as the best score known to exist can win
             u64 thr = 0;
             if (lane == 0) thr = *(volatile u64 *)s.best_hint;
             thr = warp_max_u64(thr > best.s ? thr : best.s);
@@ -582,31 +645,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
                 while (t >= b.off[j + 1]) ++j;
                 const int lo = b.lo[j], hi = b.hi[j];
                 const int wi = (lo >> 6) + (t - b.off[j]);
-                const int ky = b.ky[j];
-                const u16 *ids = b.ids[j];
+                const Rec &r = b.r[j];
+                const int ky = r.ky;
                 u64 m = 0;
-                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)ids[q] * c.GW + wi];
+                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)r.ids[q] * c.GW + wi];
                 m &= range_word(wi, lo, hi);
                 alive += (u64)__popcll(m);
                 words += (u64)ky;
                 if (m && s.a_num * (u64)ky + nn_term >= thr) {
-                    scored += (u64)score_word(c, s, b, j, wi, m, L, thr, best);
-                    words += (u64)(ky + b.kn[j]);
+                    scored += (u64)score_word(c, s, r, wi, m, L, thr, best);
+                    words += (u64)(ky + r.kn);
                 }
             }
-            // dense prefixes: the whole warp, leaves scored from row popcounts
+            // dense records: the whole warp, leaves scored from row popcounts
             while (dense) {
                 const int jd = __ffs(dense) - 1;
                 dense &= dense - 1;
-                const Prefix p = b.p[jd];
+                const Prefix p = b.r[jd].p;
                 const int lo = b.lo[jd], hi = b.hi[jd];
-                const int ky = b.ky[jd];
+                const int ky = b.r[jd].ky;
                 unsigned by, bn;
                 dense_setup(c, s, p, L, b, by, bn, lane);
                 if (lane == 0) ++dense_n;
                 int po[kMaxH - 1];
-#pragma unroll
-                for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[jd][q] : 0;
+                prefix_orig(c, p, L, po);
                 const bool score = s.a_num * (u64)ky + nn_term >= thr;
                 for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
                     const int wi = wb + lane;
@@ -639,7 +701,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
                 }
                 __syncwarp();
             }
-            // publish the warp's best score so that other warps can skip hopeless prefixes
+            // publish the warp's best score so that other warps can skip hopeless records
             const u64 wbest = warp_max_u64(best.s);
             if (lane == 0 && wbest > thr) atomicMax(s.best_hint, wbest);
         }
@@ -658,18 +720,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
     }
     block_commit_best(best, s.slots);
 }
+
 // End of a round: reduce the per-block bests, record the winner with its TP / FP,
 // clear the tumors it covers (DelCols) and raise the done flag when nothing was
-// found or every tumor is covered.  The other blocks' bests are then re-scored
-// against the new U; the largest re-scored value belongs to a combination that is
-// still a candidate in the next round, so it is a lower bound on that round's
-// best and lets the next search skip scoring that cannot reach it.  One block.
+// found or every tumor is covered.  The per-block bests stay in place for the
+// next round's depth-1 kernel, which re-scores and clears them (h = 1 clears
+// them here).  One block.
 __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int round)
 {
     __shared__ Key wbest[kWarpsPerBlock];
-    __shared__ u64 whint[kWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
-    __shared__ int finished;
     if (s.state[1]) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = s.h;
@@ -677,90 +737,53 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int ro
     for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
         const Key k = s.slots[i];
         if (key_better(k, best)) best = k;
+        if (h == 1) s.slots[i] = key_empty();
     }
     best = warp_max_key(best);
     if (lane == 0) wbest[warp] = best;
     __syncthreads();
-    if (warp == 0) {
-        best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
-        best = warp_max_key(best);
-        if (best.s == 0) {
-            if (lane == 0) {
-                s.state[1] = 1;
-                finished = 1;
-            }
-        } else {
-            if (lane < h) {
-                const int o = key_get(best, lane);
-                os[lane] = o;
-                gs[lane] = (int)c.inv[o];
-            }
-            __syncwarp();
-            u64 y = 0, n = 0;
-            if (lane < c.Wt) {
-                y = s.U[lane];
-                for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
-            }
-            if (lane < c.Wn) {
-                n = ~0ull;
-                for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
-            }
-            int tp = __popcll(y), fp = __popcll(n);
-            for (int off = 16; off; off >>= 1) {
-                tp += __shfl_xor_sync(kFull, tp, off);
-                fp += __shfl_xor_sync(kFull, fp, off);
-            }
-            u64 u = 0;
-            if (lane < c.Wt) {
-                u = s.U[lane] & ~y;
-                s.U[lane] = u;
-            }
-            const unsigned left = __ballot_sync(kFull, u != 0);
-            if (lane == 0) {
-                const int k = s.state[0];
-                int *r = s.res + (size_t)k * (h + 2);
-                for (int i = 0; i < h; ++i) r[i] = os[i];
-                r[h] = tp;
-                r[h + 1] = fp;
-                s.state[0] = k + 1;
-                if (!left) s.state[1] = 1;
-                finished = !left;
-            }
-        }
+    if (warp != 0) return;
+    best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
+    best = warp_max_key(best);
+    if (lane == 0) *s.best_hint = 0;
+    if (best.s == 0) {
+        if (lane == 0) s.state[1] = 1;
+        return;
     }
-    __syncthreads();
-    // re-score the other candidates against the new U (threadfence: U was written above)
-    __threadfence_block();
-    u64 hint = 0;
-    for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
-        const Key k = s.slots[i];
-        s.slots[i] = key_empty();
-        if (k.s == 0 || finished) continue;
-        int g[kMaxH];
-        for (int q = 0; q < h; ++q) g[q < kMaxH ? q : 0] = (int)c.inv[key_get(k, q)];
-        int tp = 0;
-        for (int w = 0; w < c.Wt; ++w) {
-            u64 y = s.U[w];
-            for (int q = 0; q < h; ++q) y &= c.T[(size_t)g[q < kMaxH ? q : 0] * c.WTp + w];
-            tp += __popcll(y);
-        }
-        if (tp == 0) continue;
-        int fp = 0;
-        for (int w = 0; w < c.Wn; ++w) {
-            u64 n = ~0ull;
-            for (int q = 0; q < h; ++q) n &= c.N[(size_t)g[q < kMaxH ? q : 0] * c.WNp + w];
-            fp += __popcll(n);
-        }
-        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-        hint = s1 > hint ? s1 : hint;
+    if (lane < h) {
+        const int o = key_get(best, lane);
+        os[lane] = o;
+        gs[lane] = (int)c.inv[o];
     }
-    hint = warp_max_u64(hint);
-    if (lane == 0) whint[warp] = hint;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        u64 m = 0;
-        for (int i = 0; i < kWarpsPerBlock; ++i) m = whint[i] > m ? whint[i] : m;
-        *s.best_hint = m;
+    __syncwarp();
+    u64 y = 0, n = 0;
+    if (lane < c.Wt) {
+        y = s.U[lane];
+        for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+    }
+    if (lane < c.Wn) {
+        n = ~0ull;
+        for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
+    }
+    int tp = __popcll(y), fp = __popcll(n);
+    for (int off = 16; off; off >>= 1) {
+        tp += __shfl_xor_sync(kFull, tp, off);
+        fp += __shfl_xor_sync(kFull, fp, off);
+    }
+    u64 u = 0;
+    if (lane < c.Wt) {
+        u = s.U[lane] & ~y;
+        s.U[lane] = u;
+    }
+    const unsigned left = __ballot_sync(kFull, u != 0);
+    if (lane == 0) {
+        const int k = s.state[0];
+        int *r = s.res + (size_t)k * (h + 2);
+        for (int i = 0; i < h; ++i) r[i] = os[i];
+        r[h] = tp;
+        r[h + 1] = fp;
+        s.state[0] = k + 1;
+        if (!left) s.state[1] = 1;
     }
 }
 
@@ -789,18 +812,18 @@ void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStre
 
 int level1_grid(const Cohort &c) { return (c.G + kThreads - 1) / kThreads; }
 
-void launch_level1(const Cohort &c, const Solve &s, int round, Prefix *F1, u32 *n1, u32 cap1, cudaStream_t st)
+void launch_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st)
 {
     k_level1<<<level1_grid(c), kThreads, 0, st>>>(c, s, round, F1, n1, cap1);
 }
 
-void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Prefix *Fin, const u32 *nin,
-                   Prefix *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st)
+void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, const u32 *nin,
+                   Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st)
 {
     k_expand<<<grid, kThreads, 0, st>>>(c, s, round, level, Fin, nin, Fout, nout, cap);
 }
 
-void launch_leaf(const Cohort &c, const Solve &s, int round, const Prefix *Fin, const u32 *nin, int grid,
+void launch_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, const u32 *nin, int grid,
                  cudaStream_t st)
 {
     k_leaf<<<grid, kThreads, 0, st>>>(c, s, round, Fin, nin);

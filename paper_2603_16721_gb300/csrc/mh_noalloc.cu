@@ -34,7 +34,7 @@ constexpr int kNaMaxG = 8192;
 constexpr int kNaMaxNt = 1024;
 constexpr int kNaMaxNn = 1024;
 constexpr int kNaMaxH = 4;
-constexpr u32 kNaFrontierCap = 1u << 19;  // entries per intermediate depth
+constexpr u32 kNaFrontierCap = 1u << 17;  // entries per intermediate depth
 constexpr int kNaMaxSlots = 4096;
 constexpr int kNaMaxDevices = 64;
 
@@ -60,9 +60,9 @@ constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * 2 * kCountStride)
 constexpr size_t kOffCnt = kOffRes + align256(sizeof(int) * kNaRounds * (kNaMaxH + 2));
 constexpr size_t kOffSlots = kOffCnt + align256(sizeof(u64) * 2 * kNaRounds * kNaMaxH);
 constexpr size_t kOffF1 = kOffSlots + align256(sizeof(Key) * kNaMaxSlots);
-constexpr size_t kOffF2 = kOffF1 + align256(sizeof(Prefix) * kNaMaxG);
-constexpr size_t kOffF3 = kOffF2 + align256(sizeof(Prefix) * kNaFrontierCap);
-constexpr size_t kScratchBytes = kOffF3 + align256(sizeof(Prefix) * kNaFrontierCap);  // about 22 MB
+constexpr size_t kOffF2 = kOffF1 + align256(sizeof(Rec) * kNaMaxG);
+constexpr size_t kOffF3 = kOffF2 + align256(sizeof(Rec) * kNaFrontierCap);
+constexpr size_t kScratchBytes = kOffF3 + align256(sizeof(Rec) * kNaFrontierCap);  // about 30 MB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -243,13 +243,13 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
     u32 *counts = (u32 *)(base + kOffCounts);
     s.fetch = counts + kCountStride;
-    Prefix *F[kMaxH] = {};
+    Rec *F[kMaxH] = {};
     u32 cap[kMaxH] = {};
-    F[1] = (Prefix *)(base + kOffF1);
+    F[1] = (Rec *)(base + kOffF1);
     cap[1] = kNaMaxG;
-    F[2] = (Prefix *)(base + kOffF2);
+    F[2] = (Rec *)(base + kOffF2);
     cap[2] = kNaFrontierCap;
-    F[3] = (Prefix *)(base + kOffF3);
+    F[3] = (Rec *)(base + kOffF3);
     cap[3] = kNaFrontierCap;
 
     // store: sort keys (into the depth-2 frontier area, free at this point), pack, transpose

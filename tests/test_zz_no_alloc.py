@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 def _cohorts():
     small = synth.generate(synth.c2_law(900, 190, 70, seed=21, h=2))
-    return [(synth.generate(synth.c2()), 3), (small, 2), (small, 3)]
+    return [(synth.generate(synth.c2_law(2000, 300, 200, seed=1, h=3)), 3), (small, 2), (small, 3)]
 
 
 def test_noalloc_matches_solve_on_consecutive_calls():
