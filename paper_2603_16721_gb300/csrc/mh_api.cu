@@ -84,7 +84,7 @@ struct mh_handle {
     int ws_h = 0, ws_rounds = 0, ws_slots = 0;
     u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr;
     int *dState = nullptr, *dRes = nullptr;
-    Key *dSlots = nullptr;
+    Key *dSlots = nullptr, *dCand = nullptr;
     u32 *dCounts = nullptr;               // frontier sizes, one per depth, then work-distribution counters
     Rec *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
@@ -95,7 +95,7 @@ struct mh_handle {
     {
         cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dCN); cudaFree(dOrig); cudaFree(dInv);
         cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
-        cudaFree(dSlots); cudaFree(dCounts);
+        cudaFree(dSlots); cudaFree(dCand); cudaFree(dCounts);
         for (int l = 0; l < kMaxH; ++l) cudaFree(dF[l]);
         if (hState) cudaFreeHost(hState);
     }
@@ -230,10 +230,11 @@ int ensure_workspace(mh_handle *H, int h)
     int rc;
     if (!H->dU) {
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dState, 4, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)2 * kCountStride, &H->device_bytes))) return rc;
-        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (4 + kCountStride)));
+        if ((rc = dalloc(&H->dCounts, (size_t)kCountStride, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes))) return rc;
+        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountStride)));
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
         cudaFree(H->dCnt);
@@ -365,81 +366,107 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     s.cnt = H->dCnt;
     s.slots = H->dSlots;
     s.nslots = H->ws_slots;
+    s.cand = H->dCand;
     s.work = H->dWork;
     s.best_hint = H->dWork + kWorkCount;
-    s.fetch = H->dCounts + kCountStride;
     int max_rounds = H->Nt + 1;
     if (opts->max_rounds > 0) max_rounds = std::min(max_rounds, (int)opts->max_rounds);
 
     EventPair total;
     MH_CUDA(cudaEventCreate(&total.a));
     MH_CUDA(cudaEventCreate(&total.b));
-    std::vector<EventPair> leaf_ev;
+    struct LeafEvents {
+        EventPair ev;
+        bool valid;
+    };
+    std::vector<LeafEvents> leaf_ev;
+    auto destroy_events = [&]() {
+        cudaEventDestroy(total.a);
+        cudaEventDestroy(total.b);
+        for (auto &e : leaf_ev) {
+            cudaEventDestroy(e.ev.a);
+            cudaEventDestroy(e.ev.b);
+        }
+    };
     int64_t launches = 0, leaf_launches = 0;
     const int grid = leaf_grid(H);
+    u32 *counts = H->dCounts;
 
     MH_CUDA(cudaEventRecord(total.a, st));
-    launch_solve_init(c, s, H->ws_rounds, st);
+    launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, st);
     ++launches;
-    int rounds = 0;
+    // Rounds are enqueued in growing batches without waiting: every kernel reads
+    // the round index and the done / overflow flags on the device.  After a batch
+    // the host reads the state; an overflowed frontier is grown and its round rerun.
+    int batch = 4, rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
-    while (!done && rounds < max_rounds) {
-        const int r = rounds;
-        MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * 2 * kCountStride, st));
-        launch_level1(c, s, r, H->dF[1], H->dCounts + 1, H->cap[1], st);
-        ++launches;
-        for (int l = 2; l <= h - 1; ++l) {
-            for (;;) {
-                launch_expand(c, s, r, l, H->dF[l - 1], H->dCounts + (l - 1), H->dF[l], H->dCounts + l,
+    while (!done) {
+        const size_t first_ev = leaf_ev.size();
+        const int n = std::min(batch, max_rounds - rounds_done);
+        for (int b = 0; b < n; ++b) {
+            launch_level1(c, s, H->dF[1], counts + 1, H->cap[1], st);
+            ++launches;
+            for (int l = 2; l <= h - 1; ++l) {
+                launch_expand(c, s, l, H->dF[l - 1], counts + (l - 1), H->cap[l - 1], H->dF[l], counts + l,
                               H->cap[l], grid, st);
                 ++launches;
-                MH_CUDA(cudaGetLastError());
-                MH_CUDA(cudaMemcpyAsync(H->hState, H->dCounts, sizeof(u32) * kMaxH, cudaMemcpyDeviceToHost, st));
-                MH_CUDA(cudaStreamSynchronize(st));
-                const u64 need = (u64)((u32 *)H->hState)[l];
-                if (need <= H->cap[l]) break;
-                // frontier too small: grow it, forget this depth's counters and redo the depth
-                if ((rc = ensure_frontier(H, l, need))) {
-                    cudaEventDestroy(total.a);
-                    cudaEventDestroy(total.b);
-                    for (auto &e : leaf_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+            }
+            if (h >= 2) {
+                LeafEvents e{};
+                if (opts->time_kernels) {
+                    MH_CUDA(cudaEventCreate(&e.ev.a));
+                    MH_CUDA(cudaEventCreate(&e.ev.b));
+                    MH_CUDA(cudaEventRecord(e.ev.a, st));
+                }
+                launch_leaf(c, s, H->dF[h - 1], counts + (h - 1), H->cap[h - 1], grid, st);
+                ++launches;
+                ++leaf_launches;
+                if (opts->time_kernels) {
+                    MH_CUDA(cudaEventRecord(e.ev.b, st));
+                    e.valid = true;
+                    leaf_ev.push_back(e);
+                }
+            }
+            launch_finalize(c, s, counts, st);
+            ++launches;
+        }
+        MH_CUDA(cudaGetLastError());
+        MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
+        MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountStride, cudaMemcpyDeviceToHost,
+                                st));
+        MH_CUDA(cudaStreamSynchronize(st));
+        const int *hs = H->hState;
+        const u32 *hc = (const u32 *)(H->hState + kStateWords);
+        rounds_done = hs[4];
+        if (hs[3]) {
+            // a frontier of round rounds_done did not fit: grow it, forget the round's
+            // partial counters and frontier sizes, and run the round again
+            for (size_t e = first_ev; e < leaf_ev.size(); ++e) leaf_ev[e].valid = false;
+            for (int l = 1; l < h; ++l) {
+                if (hc[l] > H->cap[l] && (rc = ensure_frontier(H, l, hc[l]))) {
+                    destroy_events();
                     return rc;
                 }
-                MH_CUDA(cudaMemsetAsync(H->dCounts + l, 0, sizeof(u32), st));
-                MH_CUDA(cudaMemsetAsync(s.fetch + l, 0, sizeof(u32), st));
-                MH_CUDA(cudaMemsetAsync(H->dCnt + ((size_t)r * h + (l - 1)) * 2, 0, 2 * sizeof(u64), st));
             }
+            MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
+            MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st));
+            MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
+            continue;
         }
-        if (h >= 2) {
-            EventPair ev;
-            if (opts->time_kernels) {
-                MH_CUDA(cudaEventCreate(&ev.a));
-                MH_CUDA(cudaEventCreate(&ev.b));
-                MH_CUDA(cudaEventRecord(ev.a, st));
-            }
-            launch_leaf(c, s, r, H->dF[h - 1], H->dCounts + (h - 1), grid, st);
-            ++launches;
-            ++leaf_launches;
-            if (opts->time_kernels) {
-                MH_CUDA(cudaEventRecord(ev.b, st));
-                leaf_ev.push_back(ev);
-            }
-        }
-        launch_finalize(c, s, r, st);
-        ++launches;
-        MH_CUDA(cudaGetLastError());
-        MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
-        MH_CUDA(cudaStreamSynchronize(st));
-        ++rounds;
-        done = H->hState[1] != 0;
+        done = hs[1] != 0 || rounds_done >= max_rounds;
+        batch = std::min(batch * 2, 64);
     }
     MH_CUDA(cudaEventRecord(total.b, st));
-    MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
     MH_CUDA(cudaStreamSynchronize(st));
     const int k = H->hState[0];
+    const int rounds = H->hState[4];
 
     mh_result *R = (mh_result *)calloc(1, sizeof(mh_result));
-    if (!R) return fail(MH_ENOMEM, "host allocation of the result failed");
+    if (!R) {
+        destroy_events();
+        return fail(MH_ENOMEM, "host allocation of the result failed");
+    }
     R->h = h;
     R->k = k;
     R->rounds = rounds;
@@ -450,6 +477,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     R->pruned = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
     if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned) {
         mh_result_free(R);
+        destroy_events();
         return fail(MH_ENOMEM, "host allocation of the result failed");
     }
     std::vector<int> res((size_t)std::max(1, k) * (h + 2));
@@ -459,10 +487,12 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && rounds)
         e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         mh_result_free(R);
+        destroy_events();
         return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
     }
     for (int i = 0; i < k; ++i) {
@@ -477,18 +507,19 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     float ms = 0.f;
     cudaEventElapsedTime(&ms, total.a, total.b);
     R->solve_ms = ms;
+    // leaf time of the rounds that ran (launches after the last round return at once)
     double leaf_ms = 0.0;
+    int64_t timed = 0;
     for (auto &ev : leaf_ev) {
+        if (!ev.valid || timed >= rounds) continue;
         float x = 0.f;
-        cudaEventElapsedTime(&x, ev.a, ev.b);
+        cudaEventElapsedTime(&x, ev.ev.a, ev.ev.b);
         leaf_ms += x;
-        cudaEventDestroy(ev.a);
-        cudaEventDestroy(ev.b);
+        ++timed;
     }
-    cudaEventDestroy(total.a);
-    cudaEventDestroy(total.b);
+    destroy_events();
     R->leaf_ms = leaf_ms;
-    R->leaf_launches = leaf_launches;
+    R->leaf_launches = opts->time_kernels ? timed : leaf_launches;
     R->kernel_launches = launches;
     R->leaf_words = work[kWorkColWords];
     R->leaf_prefixes = work[kWorkPrefixes];

@@ -67,15 +67,18 @@ struct Solve {
     int prune;          // 0 = paper (cut empty intersections), 1 = off
     u64 a_num, a_den;
     u64 *U;             // WTp words: uncovered tumors
-    int *state;         // [0] = k selected, [1] = done flag, [2] = error flag
+    int *state;         // kStateWords ints: k selected, done, error, overflow, round, round limit
     int *res;           // per round: h original indices, TP, FP
     u64 *cnt;           // per round, per level: visited, pruned
     Key *slots;         // per-block best candidates of the current round
     int nslots;
     u64 *work;          // leaf-kernel work counters, see kWork*
-    u32 *fetch;         // per-depth work-distribution counters, zeroed every round
-    u64 *best_hint;     // best score (s field) found so far in the round, for skipping hopeless scoring
+    Key *cand;          // kCandidates best keys of the previous round (for the next threshold)
+    u64 *best_hint;     // best score (s field) known to exist in the round, for skipping hopeless scoring
 };
+
+constexpr int kCandidates = 32;
+constexpr int kStateWords = 8;
 
 // Leaf-kernel work counters (Solve::work).
 enum {
@@ -89,13 +92,16 @@ enum {
 
 // Launchers (mh_kernels.cu).
 void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
-void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st);
-void launch_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st);
-void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, const u32 *nin,
+// Rounds run on the device: every kernel reads the round index and the done /
+// overflow flags from Solve::state, so the host can enqueue many rounds ahead.
+void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts,
+                       cudaStream_t st);
+void launch_level1(const Cohort &c, const Solve &s, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st);
+void launch_expand(const Cohort &c, const Solve &s, int level, const Rec *Fin, const u32 *nin, u32 cap_in,
                    Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st);
-void launch_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, const u32 *nin, int grid,
+void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin, u32 cap_in, int grid,
                  cudaStream_t st);
-void launch_finalize(const Cohort &c, const Solve &s, int round, cudaStream_t st);
+void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
 int level1_grid(const Cohort &c);
 
 // Message returned by mh_last_error() on the calling thread.

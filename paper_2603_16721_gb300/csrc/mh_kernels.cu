@@ -201,13 +201,19 @@ __device__ __forceinline__ bool is_dense(int ky, int kn) { return ky > kListT ||
 
 __device__ __forceinline__ u16 sat16(int v) { return (u16)(v < 0xffff ? v : 0xffff); }
 
-// Prefixes a warp takes per fetch: enough batches for every warp of the grid
-// when the frontier is small, up to kBatch when it is large.
-__device__ __forceinline__ u32 batch_size(u32 count)
+// Round state (Solve::state): a kernel of a round does nothing once the solve is
+// done or a frontier of the round has overflowed.
+enum { kStK = 0, kStDone = 1, kStError = 2, kStOverflow = 3, kStRound = 4, kStMaxRounds = 5 };
+
+__device__ __forceinline__ bool halted(const Solve &s) { return s.state[kStDone] | s.state[kStOverflow]; }
+
+// A consumer whose input frontier did not fit raises the overflow flag; the host
+// grows the frontier and runs the round again.
+__device__ __forceinline__ bool input_overflowed(const Solve &s, u32 count, u32 cap)
 {
-    const u32 warps = gridDim.x * kWarpsPerBlock;
-    const u32 nb = (count + warps - 1) / warps;
-    return nb < 1 ? 1 : (nb > (u32)kBatch ? (u32)kBatch : nb);
+    if (count <= cap) return false;
+    if (threadIdx.x == 0) s.state[kStOverflow] = 1;
+    return true;
 }
 
 __device__ __forceinline__ void copy_rec(Rec *dst, const Rec *src)
@@ -227,16 +233,16 @@ struct Batch {
     u64 ns[kMaxWords];
 };
 
-// Lane j takes record base+j (if < end) into the warp scratch with its child
-// range [last gene + 1, hi_bound]; counts its children as visited.  Returns the
-// number of column words of the batch's sparse records (those with samples, or
-// all of them with `all_children`) and the bit mask of dense records.
-__device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 base, u32 end, int L, int hi_bound,
+// Lane j takes record first + j*stride (if < count) into the warp scratch with
+// its child range [last gene + 1, hi_bound]; counts its children as visited.
+// Returns the number of column words of the batch's sparse records (those with
+// samples, or all of them with `all_children`) and the bit mask of dense records.
+__device__ __forceinline__ int batch_prepare(const Rec *Fin, u64 first, u64 stride, u32 count, int L, int hi_bound,
                                              bool all_children, Batch &b, int lane, unsigned &dense_mask,
                                              u64 &visited)
 {
-    const u32 i = base + lane;
-    const bool valid = i < end;
+    const u64 i = first + (u64)lane * stride;
+    const bool valid = i < count;
     int lo = 1, hi = 0, ky = 0, kn = 0;
     if (valid) {
         copy_rec(&b.r[lane], &Fin[i]);
@@ -417,18 +423,18 @@ __global__ void k_transpose(int G, const u64 *rows, int row_stride, int samples,
     cols[t] = word;
 }
 
-__global__ void k_solve_init(Cohort c, Solve s)
+__global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
 {
     const int w = threadIdx.x;
     if (w < c.WTp) {
         const int rem = c.Nt - 64 * w;
         s.U[w] = rem >= 64 ? ~0ull : (rem <= 0 ? 0ull : ((1ull << rem) - 1ull));
     }
-    if (w < 4) s.state[w] = 0;
+    if (w < kStateWords) s.state[w] = w == kStMaxRounds ? max_rounds : 0;
 }
 
-// Re-scores the previous round's per-block bests against the current U (one warp
-// per key, lane w on word w) and clears them.  A key still covering an uncovered
+// Re-scores the previous round's best candidates against the current U (one warp
+// per key, lane w on word w).  A key still covering an uncovered
 // tumor is a candidate of this round, so the largest value is a lower bound on
 // this round's best: the leaf kernel need not score what cannot reach it.
 __device__ void rescore_slots(const Cohort &c, const Solve &s)
@@ -436,8 +442,8 @@ __device__ void rescore_slots(const Cohort &c, const Solve &s)
     const int lane = threadIdx.x & 31;
     const int h = s.h;
     u64 hint = 0;
-    for (int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); i < s.nslots; i += gridDim.x * kWarpsPerBlock) {
-        const Key k = s.slots[i];
+    for (int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); i < kCandidates; i += gridDim.x * kWarpsPerBlock) {
+        const Key k = s.cand[i];
         if (k.s == 0) continue;
         u64 y = 0, n = 0;
         if (lane < c.Wt) y = s.U[lane];
@@ -452,7 +458,6 @@ __device__ void rescore_slots(const Cohort &c, const Solve &s)
             tp += __shfl_xor_sync(kFull, tp, off);
             fp += __shfl_xor_sync(kFull, fp, off);
         }
-        if (lane == 0) s.slots[i] = key_empty();
         if (tp == 0) continue;
         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
         hint = s1 > hint ? s1 : hint;
@@ -463,9 +468,10 @@ __device__ void rescore_slots(const Cohort &c, const Solve &s)
 // Depth 1: y_1(g) = U & x_g for g in [0, G-h] (0-based).  For h = 1 these are
 // the leaves and are scored here; otherwise the non-empty ones (all of them with
 // pruning off) become depth-1 records.
-__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int round, Rec *F1, u32 *n1, u32 cap1)
+__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Rec *F1, u32 *n1, u32 cap1)
 {
-    if (s.state[1]) return;
+    if (halted(s)) return;
+    const int round = s.state[kStRound];
     const int lane = threadIdx.x & 31;
     if (s.h > 1) rescore_slots(c, s);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -517,28 +523,25 @@ __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, int roun
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
 // every depth-(level-1) record become depth-level records.
-__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int round, int level, const Rec *Fin,
-                                                        const u32 *nin, Rec *Fout, u32 *nout, u32 cap)
+__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, const Rec *Fin,
+                                                        const u32 *nin, u32 cap_in, Rec *Fout, u32 *nout, u32 cap)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
-    if (s.state[1]) return;
+    if (halted(s)) return;
+    const u32 count = *nin;
+    if (input_overflowed(s, count, cap_in)) return;
+    const int round = s.state[kStRound];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Batch &b = scratch[warp];
-    const u32 count = *nin;
     const int L = level - 1;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
     const bool all_children = s.prune != 0;
-    u32 *fetch = s.fetch + level;
-    const u32 nb = batch_size(count);
+    const u64 nw = (u64)gridDim.x * kWarpsPerBlock, gw = (u64)blockIdx.x * kWarpsPerBlock + warp;
     u64 visited = 0, alive = 0;
-    for (;;) {
-        u32 base = 0;
-        if (lane == 0) base = atomicAdd(fetch, nb);
-        base = __shfl_sync(kFull, base, 0);
-        if (base >= count) break;
-        const u32 end = count - base < nb ? count : base + nb;
+    for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
-        const int total = batch_prepare(Fin, base, end, L, hi_bound, all_children, b, lane, dense, visited);
+        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, hi_bound, all_children, b, lane, dense,
+                                        visited);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32) {
@@ -613,29 +616,25 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int r
 // goes to the block's slot.  A record whose bound a_num * |y| + a_den * Nn is
 // below the best score known to exist cannot hold the round's winner, so its
 // leaves are tested (and counted) but not scored.
-__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int round, const Rec *Fin, const u32 *nin)
+__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Batch &b = scratch[warp];
-    const bool done = s.state[1] != 0;
+    if (halted(s) || input_overflowed(s, *nin, cap_in)) return;
+    const bool done = false;
+    const int round = s.state[kStRound];
     u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const int h = s.h, L = h - 1;
     if (!done) {
         const u32 count = *nin;
-        u32 *fetch = s.fetch + h;
-        const u32 nb = batch_size(count);
         const u64 nn_term = s.a_den * (u64)c.Nn + 1;
-        for (;;) {
-            u32 base = 0;
-            if (lane == 0) base = atomicAdd(fetch, nb);
-            base = __shfl_sync(kFull, base, 0);
-            if (base >= count) break;
-            const u32 end = count - base < nb ? count : base + nb;
+        const u64 nw = (u64)gridDim.x * kWarpsPerBlock, gw = (u64)blockIdx.x * kWarpsPerBlock + warp;
+        for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
             unsigned dense;
-            const int total = batch_prepare(Fin, base, end, L, c.G - 1, false, b, lane, dense, visited);
-            prefixes += (u64)(base + lane < end);
+            const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited);
+            prefixes += (u64)(gw + (kb + lane) * nw < count);
             // only candidates at least as good as the best score known to exist can win
             u64 thr = 0;
             if (lane == 0) thr = *(volatile u64 *)s.best_hint;
@@ -722,32 +721,45 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, int rou
 }
 
 // End of a round: reduce the per-block bests, record the winner with its TP / FP,
-// clear the tumors it covers (DelCols) and raise the done flag when nothing was
-// found or every tumor is covered.  The per-block bests stay in place for the
-// next round's depth-1 kernel, which re-scores and clears them (h = 1 clears
-// them here).  One block.
-__global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int round)
+// clear the tumors it covers (DelCols), keep the best other candidates for the
+// next round's threshold, reset the frontier sizes and advance the round; raise
+// the done flag when nothing was found, every tumor is covered or the round limit
+// is reached.  One block.
+__global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *counts)
 {
     __shared__ Key wbest[kWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
-    if (s.state[1]) return;
+    if (halted(s)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = s.h;
     Key best = key_empty();
     for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
         const Key k = s.slots[i];
         if (key_better(k, best)) best = k;
-        if (h == 1) s.slots[i] = key_empty();
+        s.slots[i] = key_empty();
     }
-    best = warp_max_key(best);
-    if (lane == 0) wbest[warp] = best;
+    // the best kCandidates / kWarpsPerBlock of each warp's lane bests become next
+    // round's candidates; the block's best is the winner
+    Key mine = best;
+    for (int r = 0; r < kCandidates / kWarpsPerBlock; ++r) {
+        const Key m = warp_max_key(mine);
+        if (lane == 0) s.cand[warp * (kCandidates / kWarpsPerBlock) + r] = m;
+        if (m.s != 0 && mine.s == m.s && mine.t0 == m.t0 && mine.t1 == m.t1 && mine.t2 == m.t2) mine = key_empty();
+        if (r == 0 && lane == 0) wbest[warp] = m;
+    }
+    if (threadIdx.x < kCountStride) counts[threadIdx.x] = 0;
     __syncthreads();
     if (warp != 0) return;
     best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
     best = warp_max_key(best);
-    if (lane == 0) *s.best_hint = 0;
+    const int round = s.state[kStRound];
+    const bool last_round = round + 1 >= s.state[kStMaxRounds];
+    if (lane == 0) {
+        *s.best_hint = 0;
+        s.state[kStRound] = round + 1;
+    }
     if (best.s == 0) {
-        if (lane == 0) s.state[1] = 1;
+        if (lane == 0) s.state[kStDone] = 1;
         return;
     }
     if (lane < h) {
@@ -777,13 +789,13 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, int ro
     }
     const unsigned left = __ballot_sync(kFull, u != 0);
     if (lane == 0) {
-        const int k = s.state[0];
+        const int k = s.state[kStK];
         int *r = s.res + (size_t)k * (h + 2);
         for (int i = 0; i < h; ++i) r[i] = os[i];
         r[h] = tp;
         r[h + 1] = fp;
-        s.state[0] = k + 1;
-        if (!left) s.state[1] = 1;
+        s.state[kStK] = k + 1;
+        if (!left || last_round) s.state[kStDone] = 1;
     }
 }
 
@@ -801,37 +813,40 @@ void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samp
     k_transpose<<<(unsigned)blocks, threads, 0, st>>>(c.G, rows, row_stride, samples, c.GW, cols);
 }
 
-void launch_solve_init(const Cohort &c, const Solve &s, int max_rounds, cudaStream_t st)
+void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts,
+                       cudaStream_t st)
 {
-    cudaMemsetAsync(s.cnt, 0, sizeof(u64) * 2 * (size_t)s.h * (size_t)max_rounds, st);
+    cudaMemsetAsync(s.cnt, 0, sizeof(u64) * 2 * (size_t)s.h * (size_t)counter_rounds, st);
     cudaMemsetAsync(s.slots, 0, sizeof(Key) * (size_t)s.nslots, st);
+    cudaMemsetAsync(s.cand, 0, sizeof(Key) * (size_t)kCandidates, st);
     cudaMemsetAsync(s.work, 0, sizeof(u64) * kWorkCount, st);
     cudaMemsetAsync(s.best_hint, 0, sizeof(u64), st);
-    k_solve_init<<<1, 64, 0, st>>>(c, s);
+    cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st);
+    k_solve_init<<<1, 64, 0, st>>>(c, s, max_rounds);
 }
 
 int level1_grid(const Cohort &c) { return (c.G + kThreads - 1) / kThreads; }
 
-void launch_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st)
+void launch_level1(const Cohort &c, const Solve &s, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st)
 {
-    k_level1<<<level1_grid(c), kThreads, 0, st>>>(c, s, round, F1, n1, cap1);
+    k_level1<<<level1_grid(c), kThreads, 0, st>>>(c, s, F1, n1, cap1);
 }
 
-void launch_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, const u32 *nin,
+void launch_expand(const Cohort &c, const Solve &s, int level, const Rec *Fin, const u32 *nin, u32 cap_in,
                    Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st)
 {
-    k_expand<<<grid, kThreads, 0, st>>>(c, s, round, level, Fin, nin, Fout, nout, cap);
+    k_expand<<<grid, kThreads, 0, st>>>(c, s, level, Fin, nin, cap_in, Fout, nout, cap);
 }
 
-void launch_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, const u32 *nin, int grid,
+void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin, u32 cap_in, int grid,
                  cudaStream_t st)
 {
-    k_leaf<<<grid, kThreads, 0, st>>>(c, s, round, Fin, nin);
+    k_leaf<<<grid, kThreads, 0, st>>>(c, s, Fin, nin, cap_in);
 }
 
-void launch_finalize(const Cohort &c, const Solve &s, int round, cudaStream_t st)
+void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st)
 {
-    k_finalize<<<1, kThreads, 0, st>>>(c, s, round);
+    k_finalize<<<1, kThreads, 0, st>>>(c, s, counts);
 }
 
 }  // namespace mh

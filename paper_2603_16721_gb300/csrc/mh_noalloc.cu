@@ -54,12 +54,13 @@ constexpr size_t kOffOrig = kOffCN + align256(sizeof(u64) * kNaMaxNn * kNaGW);
 constexpr size_t kOffInv = kOffOrig + align256(sizeof(u16) * kNaMaxG);
 constexpr size_t kOffU = kOffInv + align256(sizeof(u32) * kNaMaxG);
 constexpr size_t kOffState = kOffU + align256(sizeof(u64) * kNaWTp);
-constexpr size_t kOffWork = kOffState + align256(sizeof(int) * 4);
+constexpr size_t kOffWork = kOffState + align256(sizeof(int) * kStateWords);
 constexpr size_t kOffCounts = kOffWork + align256(sizeof(u64) * (kWorkCount + 1));
 constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * 2 * kCountStride);
 constexpr size_t kOffCnt = kOffRes + align256(sizeof(int) * kNaRounds * (kNaMaxH + 2));
 constexpr size_t kOffSlots = kOffCnt + align256(sizeof(u64) * 2 * kNaRounds * kNaMaxH);
-constexpr size_t kOffF1 = kOffSlots + align256(sizeof(Key) * kNaMaxSlots);
+constexpr size_t kOffCand = kOffSlots + align256(sizeof(Key) * kNaMaxSlots);
+constexpr size_t kOffF1 = kOffCand + align256(sizeof(Key) * kCandidates);
 constexpr size_t kOffF2 = kOffF1 + align256(sizeof(Rec) * kNaMaxG);
 constexpr size_t kOffF3 = kOffF2 + align256(sizeof(Rec) * kNaFrontierCap);
 constexpr size_t kScratchBytes = kOffF3 + align256(sizeof(Rec) * kNaFrontierCap);  // about 30 MB
@@ -238,11 +239,11 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.slots = (Key *)(base + kOffSlots);
     s.work = (u64 *)(base + kOffWork);
     s.best_hint = s.work + kWorkCount;
+    s.cand = (Key *)(base + kOffCand);
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
     u32 *counts = (u32 *)(base + kOffCounts);
-    s.fetch = counts + kCountStride;
     Rec *F[kMaxH] = {};
     u32 cap[kMaxH] = {};
     F[1] = (Rec *)(base + kOffF1);
@@ -254,48 +255,54 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
 
     // store: sort keys (into the depth-2 frontier area, free at this point), pack, transpose
     u32 *keys = (u32 *)F[2];
-    NA_CUDA(cudaMemsetAsync(s.state, 0, sizeof(int) * 4, st));
+    NA_CUDA(cudaMemsetAsync(s.state, 0, sizeof(int) * kStateWords, st));
     k_na_sort_keys<<<1, 1024, 0, st>>>((const u64 *)d_bitmaps, G, c.Wt, c.Wn, keys);
     k_na_pack<<<(G + 255) / 256, 256, 0, st>>>((const u64 *)d_bitmaps, c, keys, T, N, orig, inv, s.state);
     launch_transpose(c, T, c.WTp, Nt, CT, st);
     launch_transpose(c, N, c.WNp, Nn, CN, st);
     NA_CUDA(cudaGetLastError());
-    int hs[4] = {0, 0, 0, 0};
+    int hs[kStateWords] = {};
     NA_CUDA(cudaMemcpyAsync(hs, s.state, sizeof hs, cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
     if (hs[2]) return na_fail(MH_EINVAL, "mh_solve_noalloc: padding bits past Nt or Nn are set");
 
-    launch_solve_init(c, s, kNaRounds, st);
+    launch_solve_init(c, s, kNaRounds, Nt + 1, counts, st);
     const int grid = leaf_blocks;
-    int rounds = 0;
+    // rounds run on the device; the host enqueues them in growing batches
+    int batch = 4, rounds = 0;
     bool done = Nt == 0;
-    while (!done && rounds < Nt + 1) {
-        const int r = rounds;
-        NA_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * 2 * kCountStride, st));
-        launch_level1(c, s, r, F[1], counts + 1, cap[1], st);
-        for (int l = 2; l <= h - 1; ++l) {
-            launch_expand(c, s, r, l, F[l - 1], counts + (l - 1), F[l], counts + l, cap[l], grid, st);
-            u32 n = 0;
-            NA_CUDA(cudaMemcpyAsync(&n, counts + l, sizeof n, cudaMemcpyDeviceToHost, st));
-            NA_CUDA(cudaStreamSynchronize(st));
-            if (n > cap[l])
-                return na_fail(MH_ENOMEM,
-                               "mh_solve_noalloc: depth-%d frontier needs %u entries, the fixed scratch holds %u", l,
-                               n, cap[l]);
+    int st8[kStateWords];
+    while (!done) {
+        const int n = batch < Nt + 1 - rounds ? batch : Nt + 1 - rounds;
+        for (int b = 0; b < n; ++b) {
+            launch_level1(c, s, F[1], counts + 1, cap[1], st);
+            for (int l = 2; l <= h - 1; ++l)
+                launch_expand(c, s, l, F[l - 1], counts + (l - 1), cap[l - 1], F[l], counts + l, cap[l], grid, st);
+            if (h >= 2) launch_leaf(c, s, F[h - 1], counts + (h - 1), cap[h - 1], grid, st);
+            launch_finalize(c, s, counts, st);
         }
-        if (h >= 2) launch_leaf(c, s, r, F[h - 1], counts + (h - 1), grid, st);
-        launch_finalize(c, s, r, st);
         NA_CUDA(cudaGetLastError());
-        NA_CUDA(cudaMemcpyAsync(hs, s.state, sizeof hs, cudaMemcpyDeviceToHost, st));
+        u32 hc[kCountStride];
+        NA_CUDA(cudaMemcpyAsync(st8, s.state, sizeof st8, cudaMemcpyDeviceToHost, st));
+        NA_CUDA(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
         NA_CUDA(cudaStreamSynchronize(st));
-        ++rounds;
-        done = hs[1] != 0;
+        rounds = st8[4];
+        if (st8[3]) {
+            for (int l = 1; l < h; ++l)
+                if (hc[l] > cap[l])
+                    return na_fail(MH_ENOMEM,
+                                   "mh_solve_noalloc: depth-%d frontier needs %u entries, the fixed scratch holds %u",
+                                   l, hc[l], cap[l]);
+            return na_fail(MH_ENOMEM, "mh_solve_noalloc: a frontier exceeds the fixed scratch");
+        }
+        done = st8[1] != 0 || rounds >= Nt + 1;
+        batch = batch * 2 < 64 ? batch * 2 : 64;
     }
     k_na_unpack<<<4, 256, 0, st>>>(s.res, s.state, h, capacity, d_genes, d_tp, d_fp);
     NA_CUDA(cudaGetLastError());
-    NA_CUDA(cudaMemcpyAsync(hs, s.state, sizeof hs, cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaMemcpyAsync(st8, s.state, sizeof st8, cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
-    *k_out = hs[0];
+    *k_out = st8[0];
     if (rounds_out) *rounds_out = rounds;
     return MH_OK;
 }
