@@ -301,6 +301,40 @@ __device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const Batch &
     return m;
 }
 
+// Sibling masks of the items t0, t0+32, ... (kIlp of them) of a batch: the
+// column loads of all of them are issued together.  j is the lane's running
+// record index (items are visited in increasing order).
+constexpr int kIlp = 4;
+__device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, int t0, int total, int &j,
+                                              int (&jj)[kIlp], int (&wi)[kIlp], int (&ky)[kIlp], u64 (&m)[kIlp],
+                                              u64 (&rw)[kIlp])
+{
+    int kmax = 0;
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        const int t = t0 + 32 * u;
+        ky[u] = 0;
+        wi[u] = 0;
+        rw[u] = 0;
+        m[u] = 0;
+        if (t < total) {
+            while (t >= b.off[j + 1]) ++j;
+            wi[u] = (b.lo[j] >> 6) + (t - b.off[j]);
+            ky[u] = b.r[j].ky;
+            rw[u] = range_word(wi[u], b.lo[j], b.hi[j]);
+        }
+        jj[u] = j;
+        kmax = ky[u] > kmax ? ky[u] : kmax;
+    }
+    for (int q = 0; q < kmax; ++q) {
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u)
+            if (q < ky[u]) m[u] |= c.CT[(size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) m[u] &= rw[u];
+}
+
 // Reserves n consecutive frontier slots for each lane with one atomic per warp.
 __device__ __forceinline__ u32 warp_reserve(int n, u32 *nout, int lane)
 {
@@ -544,33 +578,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int l
                                         visited);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
-        for (int tb = 0; tb < total; tb += 32) {
-            const int t = tb + lane;
-            u64 a = 0;
-            int wi = 0;
-            if (t < total) {
-                while (t >= b.off[j + 1]) ++j;
-                const int lo = b.lo[j], hi = b.hi[j];
-                wi = (lo >> 6) + (t - b.off[j]);
-                const Rec &r = b.r[j];
-                u64 m = 0;
-                for (int q = 0; q < r.ky; ++q) m |= c.CT[(size_t)r.ids[q] * c.GW + wi];
-                const u64 rw = range_word(wi, lo, hi);
-                m &= rw;
-                alive += (u64)__popcll(m);
-                a = all_children ? rw : m;
+        for (int tb = 0; tb < total; tb += 32 * kIlp) {
+            int jj[kIlp], wi[kIlp], ky[kIlp];
+            u64 m[kIlp], rw[kIlp];
+            sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
+            int nchild = 0;
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u) {
+                alive += (u64)__popcll(m[u]);
+                if (all_children) m[u] = rw[u];
+                nchild += __popcll(m[u]);
             }
-            u32 pos = warp_reserve(__popcll(a), nout, lane);
-            while (a) {
-                const int bt = __ffsll((long long)a) - 1;
-                a &= a - 1;
-                if (pos < cap) {
-                    Rec child;
-                    child.pad[0] = child.pad[1] = child.pad[2] = 0;
-                    child_from_lists(c, b.r[j], L, wi, bt, child);
-                    copy_rec(&Fout[pos], &child);
+            u32 pos = warp_reserve(nchild, nout, lane);
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u) {
+                for (u64 a = m[u]; a; a &= a - 1) {
+                    if (pos < cap) {
+                        Rec child;
+                        child.pad[0] = child.pad[1] = child.pad[2] = 0;
+                        child_from_lists(c, b.r[jj[u]], L, wi[u], __ffsll((long long)a) - 1, child);
+                        copy_rec(&Fout[pos], &child);
+                    }
+                    ++pos;
                 }
-                ++pos;
             }
         }
         // dense records: the whole warp
@@ -616,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int l
 // goes to the block's slot.  A record whose bound a_num * |y| + a_den * Nn is
 // below the best score known to exist cannot hold the round's winner, so its
 // leaves are tested (and counted) but not scored.
-__global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
+__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     Key best = key_empty();
@@ -640,20 +670,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_leaf(Cohort c, Solve s, const R
             if (lane == 0) thr = *(volatile u64 *)s.best_hint;
             thr = warp_max_u64(thr > best.s ? thr : best.s);
             int j = 0;
-            for (int t = lane; t < total; t += 32) {
-                while (t >= b.off[j + 1]) ++j;
-                const int lo = b.lo[j], hi = b.hi[j];
-                const int wi = (lo >> 6) + (t - b.off[j]);
-                const Rec &r = b.r[j];
-                const int ky = r.ky;
-                u64 m = 0;
-                for (int q = 0; q < ky; ++q) m |= c.CT[(size_t)r.ids[q] * c.GW + wi];
-                m &= range_word(wi, lo, hi);
-                alive += (u64)__popcll(m);
-                words += (u64)ky;
-                if (m && s.a_num * (u64)ky + nn_term >= thr) {
-                    scored += (u64)score_word(c, s, r, wi, m, L, thr, best);
-                    words += (u64)(ky + r.kn);
+            for (int tb = 0; tb < total; tb += 32 * kIlp) {
+                int jj[kIlp], wi[kIlp], ky[kIlp];
+                u64 m[kIlp], rw[kIlp];
+                sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
+#pragma unroll
+                for (int u = 0; u < kIlp; ++u) {
+                    alive += (u64)__popcll(m[u]);
+                    words += (u64)ky[u];
+                    if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
+                        const Rec &r = b.r[jj[u]];
+                        scored += (u64)score_word(c, s, r, wi[u], m[u], L, thr, best);
+                        words += (u64)(ky[u] + r.kn);
+                    }
                 }
             }
             // dense records: the whole warp, leaves scored from row popcounts
