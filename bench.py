@@ -290,6 +290,8 @@ def run_ours(args):
             "config": {"workload": "c2: h=3, G=5000, Nt=500, Nn=300, seed 1, alpha=1/10",
                        "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MiB write)",
                        "rounds_per_solve": r0.rounds, "selected": r0.k},
+            "breakdown_ms_per_solve": {k: round(sum(getattr(r, k) for r in results) / len(results), 3)
+                                       for k in ("level1_ms", "expand_ms", "leaf_ms", "finalize_ms")},
             "extra": {"p50_ms": statistics.median(step_ms), "p99_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
                       "combos_scored_per_s": scored * value / world, "leaves_tested_per_s": vis_leaves * value / world,
                       "prefixes_pruned_per_s": pruned_prefixes * value / world,

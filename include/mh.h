@@ -73,7 +73,7 @@ typedef struct {
     mh_rational alpha;    /* weight of true positives */
     int32_t prune;        /* MH_PRUNE_PAPER (default 0) or MH_PRUNE_OFF */
     int32_t max_rounds;   /* stop after this many greedy rounds; <= 0 means no limit */
-    int32_t time_kernels; /* non-zero: time every leaf-kernel launch with CUDA events */
+    int32_t time_kernels; /* non-zero: time every kernel launch with CUDA events */
 } mh_solve_opts;
 
 /* Result of a solve, allocated by the library; release with mh_result_free.
@@ -99,6 +99,9 @@ typedef struct {
     uint64_t leaf_scored;    /* leaves whose TP / FP the leaf kernel evaluated exactly */
     uint64_t leaf_alu_ops;   /* 32-bit integer operations of the leaf kernel's tests and scores */
     uint64_t leaf_dense;     /* prefixes the leaf kernel took on its row (dense) path */
+    double level1_ms;        /* with time_kernels: summed durations of the depth-1, */
+    double expand_ms;        /* frontier-expansion and */
+    double finalize_ms;      /* end-of-round kernels (CUDA events) */
 } mh_result;
 
 /* Create a handle for one cohort from packed rows in HOST memory.

@@ -375,18 +375,17 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     EventPair total;
     MH_CUDA(cudaEventCreate(&total.a));
     MH_CUDA(cudaEventCreate(&total.b));
-    struct LeafEvents {
-        EventPair ev;
+    // with time_kernels, events around each kernel of a round: level1 | expand | leaf | finalize
+    struct RoundEvents {
+        cudaEvent_t ev[5];
         bool valid;
     };
-    std::vector<LeafEvents> leaf_ev;
+    std::vector<RoundEvents> round_ev;
     auto destroy_events = [&]() {
         cudaEventDestroy(total.a);
         cudaEventDestroy(total.b);
-        for (auto &e : leaf_ev) {
-            cudaEventDestroy(e.ev.a);
-            cudaEventDestroy(e.ev.b);
-        }
+        for (auto &e : round_ev)
+            for (int i = 0; i < 5; ++i) cudaEventDestroy(e.ev[i]);
     };
     int64_t launches = 0, leaf_launches = 0;
     const int grid = leaf_grid(H);
@@ -401,34 +400,36 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     int batch = 4, rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
     while (!done) {
-        const size_t first_ev = leaf_ev.size();
+        const size_t first_ev = round_ev.size();
         const int n = std::min(batch, max_rounds - rounds_done);
         for (int b = 0; b < n; ++b) {
+            RoundEvents e{};
+            if (opts->time_kernels) {
+                for (int i = 0; i < 5; ++i) MH_CUDA(cudaEventCreate(&e.ev[i]));
+                e.valid = true;
+                MH_CUDA(cudaEventRecord(e.ev[0], st));
+            }
             launch_level1(c, s, H->dF[1], counts + 1, H->cap[1], st);
             ++launches;
+            if (opts->time_kernels) MH_CUDA(cudaEventRecord(e.ev[1], st));
             for (int l = 2; l <= h - 1; ++l) {
                 launch_expand(c, s, l, H->dF[l - 1], counts + (l - 1), H->cap[l - 1], H->dF[l], counts + l,
                               H->cap[l], grid, st);
                 ++launches;
             }
+            if (opts->time_kernels) MH_CUDA(cudaEventRecord(e.ev[2], st));
             if (h >= 2) {
-                LeafEvents e{};
-                if (opts->time_kernels) {
-                    MH_CUDA(cudaEventCreate(&e.ev.a));
-                    MH_CUDA(cudaEventCreate(&e.ev.b));
-                    MH_CUDA(cudaEventRecord(e.ev.a, st));
-                }
                 launch_leaf(c, s, H->dF[h - 1], counts + (h - 1), H->cap[h - 1], grid, st);
                 ++launches;
                 ++leaf_launches;
-                if (opts->time_kernels) {
-                    MH_CUDA(cudaEventRecord(e.ev.b, st));
-                    e.valid = true;
-                    leaf_ev.push_back(e);
-                }
             }
+            if (opts->time_kernels) MH_CUDA(cudaEventRecord(e.ev[3], st));
             launch_finalize(c, s, counts, st);
             ++launches;
+            if (opts->time_kernels) {
+                MH_CUDA(cudaEventRecord(e.ev[4], st));
+                round_ev.push_back(e);
+            }
         }
         MH_CUDA(cudaGetLastError());
         MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
@@ -441,7 +442,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         if (hs[3]) {
             // a frontier of round rounds_done did not fit: grow it, forget the round's
             // partial counters and frontier sizes, and run the round again
-            for (size_t e = first_ev; e < leaf_ev.size(); ++e) leaf_ev[e].valid = false;
+            for (size_t e = first_ev; e < round_ev.size(); ++e) round_ev[e].valid = false;
             for (int l = 1; l < h; ++l) {
                 if (hc[l] > H->cap[l] && (rc = ensure_frontier(H, l, hc[l]))) {
                     destroy_events();
@@ -507,19 +508,24 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     float ms = 0.f;
     cudaEventElapsedTime(&ms, total.a, total.b);
     R->solve_ms = ms;
-    // leaf time of the rounds that ran (launches after the last round return at once)
-    double leaf_ms = 0.0;
+    // kernel times of the rounds that ran (launches after the last round return at once)
+    double kms[4] = {0, 0, 0, 0};
     int64_t timed = 0;
-    for (auto &ev : leaf_ev) {
+    for (auto &ev : round_ev) {
         if (!ev.valid || timed >= rounds) continue;
-        float x = 0.f;
-        cudaEventElapsedTime(&x, ev.ev.a, ev.ev.b);
-        leaf_ms += x;
+        for (int i = 0; i < 4; ++i) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ev.ev[i], ev.ev[i + 1]);
+            kms[i] += x;
+        }
         ++timed;
     }
     destroy_events();
-    R->leaf_ms = leaf_ms;
-    R->leaf_launches = opts->time_kernels ? timed : leaf_launches;
+    R->leaf_ms = kms[2];
+    R->level1_ms = kms[0];
+    R->expand_ms = kms[1];
+    R->finalize_ms = kms[3];
+    R->leaf_launches = opts->time_kernels ? (h >= 2 ? timed : 0) : leaf_launches;
     R->kernel_launches = launches;
     R->leaf_words = work[kWorkColWords];
     R->leaf_prefixes = work[kWorkPrefixes];

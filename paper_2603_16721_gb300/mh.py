@@ -52,7 +52,8 @@ class mh_result(ctypes.Structure):
                 ("leaf_ms", ctypes.c_double), ("leaf_launches", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("leaf_words", ctypes.c_uint64),
                 ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
-                ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64)]
+                ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64),
+                ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -125,6 +126,9 @@ class Result:
     leaf_scored: int = 0
     leaf_alu_ops: int = 0
     leaf_dense: int = 0
+    level1_ms: float = 0.0
+    expand_ms: float = 0.0
+    finalize_ms: float = 0.0
 
     @property
     def k(self) -> int:
@@ -150,7 +154,8 @@ def _to_result(p) -> Result:
                  solve_ms=float(r.solve_ms), leaf_ms=float(r.leaf_ms), leaf_launches=int(r.leaf_launches),
                  kernel_launches=int(r.kernel_launches), leaf_words=int(r.leaf_words),
                  leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
-                 leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense))
+                 leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense),
+                 level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms))
     load().mh_result_free(p)
     return out
 
