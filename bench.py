@@ -292,6 +292,7 @@ def run_ours(args):
                        "rounds_per_solve": r0.rounds, "selected": r0.k},
             "breakdown_ms_per_solve": {k: round(sum(getattr(r, k) for r in results) / len(results), 3)
                                        for k in ("level1_ms", "expand_ms", "leaf_ms", "finalize_ms")},
+            "mode": "persistent" if r0.mode == mh.MH_MODE_PERSISTENT else "launches",
             "extra": {"p50_ms": statistics.median(step_ms), "p99_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
                       "combos_scored_per_s": scored * value / world, "leaves_tested_per_s": vis_leaves * value / world,
                       "prefixes_pruned_per_s": pruned_prefixes * value / world,

@@ -67,6 +67,14 @@ typedef struct {
 #define MH_PRUNE_PAPER 0
 #define MH_PRUNE_OFF 1
 
+/* Execution of a solve.
+ *   MH_MODE_PERSISTENT: one cooperative kernel runs every round, its phases
+ *                       separated by grid barriers (default; falls back to
+ *                       MH_MODE_LAUNCHES where cooperative launch is unavailable).
+ *   MH_MODE_LAUNCHES:   one kernel launch per phase of every round. */
+#define MH_MODE_PERSISTENT 0
+#define MH_MODE_LAUNCHES 1
+
 /* Options of a solve; zero-initialise and set what you need. */
 typedef struct {
     int32_t h;            /* hits per combination, 1..9 */
@@ -74,6 +82,7 @@ typedef struct {
     int32_t prune;        /* MH_PRUNE_PAPER (default 0) or MH_PRUNE_OFF */
     int32_t max_rounds;   /* stop after this many greedy rounds; <= 0 means no limit */
     int32_t time_kernels; /* non-zero: time every kernel launch with CUDA events */
+    int32_t mode;         /* MH_MODE_PERSISTENT (default 0) or MH_MODE_LAUNCHES */
 } mh_solve_opts;
 
 /* Result of a solve, allocated by the library; release with mh_result_free.
@@ -91,7 +100,7 @@ typedef struct {
     uint64_t *visited;   /* rounds*h */
     uint64_t *pruned;    /* rounds*h */
     double solve_ms;     /* wall time of the solve measured with CUDA events on the handle's stream */
-    double leaf_ms;      /* sum of leaf-kernel durations (CUDA events), if time_kernels */
+    double leaf_ms;      /* summed duration of the leaf phase (see level1_ms) */
     int64_t leaf_launches;   /* leaf-kernel launches in this solve */
     int64_t kernel_launches; /* all kernel launches of this solve */
     uint64_t leaf_words;     /* 64-bit sample-major column words read by the leaf kernel */
@@ -99,9 +108,10 @@ typedef struct {
     uint64_t leaf_scored;    /* leaves whose TP / FP the leaf kernel evaluated exactly */
     uint64_t leaf_alu_ops;   /* 32-bit integer operations of the leaf kernel's tests and scores */
     uint64_t leaf_dense;     /* prefixes the leaf kernel took on its row (dense) path */
-    double level1_ms;        /* with time_kernels: summed durations of the depth-1, */
-    double expand_ms;        /* frontier-expansion and */
-    double finalize_ms;      /* end-of-round kernels (CUDA events) */
+    double level1_ms;        /* summed durations of the depth-1, frontier-expansion and */
+    double expand_ms;        /* end-of-round phases: CUDA events around each kernel with */
+    double finalize_ms;      /* time_kernels (launch mode), the device clock (persistent mode) */
+    int32_t mode;            /* the mode that ran (MH_MODE_*) */
 } mh_result;
 
 /* Create a handle for one cohort from packed rows in HOST memory.

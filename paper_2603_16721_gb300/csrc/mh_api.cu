@@ -89,13 +89,15 @@ struct mh_handle {
     Rec *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
     int *hState = nullptr;                // pinned: state + frontier counts
+    GridSync *dSync = nullptr;            // barrier of the persistent solve
+    int coop = 0, pgrid = 0;              // cooperative launch supported; persistent grid size
     int64_t frontier_bytes = 0;
 
     ~mh_handle()
     {
         cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dCN); cudaFree(dOrig); cudaFree(dInv);
         cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
-        cudaFree(dSlots); cudaFree(dCand); cudaFree(dCounts);
+        cudaFree(dSlots); cudaFree(dCand); cudaFree(dCounts); cudaFree(dSync);
         for (int l = 0; l < kMaxH; ++l) cudaFree(dF[l]);
         if (hState) cudaFreeHost(hState);
     }
@@ -184,6 +186,7 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->coop, cudaDevAttrCooperativeLaunch, dev);
     if (e != cudaSuccess) {
         delete H;
         return fail(MH_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
@@ -226,7 +229,7 @@ int leaf_grid(const mh_handle *H) { return std::max(1, H->num_sms * 4); }
 int ensure_workspace(mh_handle *H, int h)
 {
     const int rounds = H->Nt + 2;
-    const int slots = std::max(level1_grid(H->c), leaf_grid(H));
+    const int slots = std::max(std::max(level1_grid(H->c), leaf_grid(H)), persistent_grid(H->num_sms));
     int rc;
     if (!H->dU) {
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
@@ -234,6 +237,8 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dCounts, (size_t)kCountStride, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dSync, 1, &H->device_bytes))) return rc;
+        H->pgrid = H->coop ? persistent_grid(H->num_sms) : 0;
         MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountStride)));
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
@@ -351,6 +356,8 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         return fail(MH_EINVAL, "alpha=%d/%d: need num >= 0 and den > 0", opts->alpha.num, opts->alpha.den);
     if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
         return fail(MH_EINVAL, "prune=%d is not a pruning mode", opts->prune);
+    if (opts->mode != MH_MODE_PERSISTENT && opts->mode != MH_MODE_LAUNCHES)
+        return fail(MH_EINVAL, "mode=%d is not an execution mode", opts->mode);
     int rc = ensure_workspace(H, h);
     if (rc) return rc;
     cudaStream_t st = H->stream;
@@ -394,11 +401,51 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     MH_CUDA(cudaEventRecord(total.a, st));
     launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, st);
     ++launches;
+    const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
+    int rounds_done = 0;
+    bool done = H->Nt == 0;  // every tumor covered from the start
+    if (persistent) {
+        // One cooperative launch runs every round; it returns early only when a
+        // frontier overflowed (grown here, then the round is run again).
+        while (!done) {
+            Frontiers f;
+            for (int l = 0; l < kMaxH; ++l) {
+                f.F[l] = H->dF[l];
+                f.cap[l] = H->cap[l];
+            }
+            MH_CUDA(cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st));
+            MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, H->pgrid, st));
+            ++launches;
+            MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
+            MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountStride,
+                                    cudaMemcpyDeviceToHost, st));
+            MH_CUDA(cudaStreamSynchronize(st));
+            const int *hs = H->hState;
+            const u32 *hc = (const u32 *)(H->hState + kStateWords);
+            rounds_done = hs[4];
+            if (hs[2]) {
+                destroy_events();
+                return fail(MH_ETIMEOUT, "a grid barrier of the persistent solve timed out in round %d", rounds_done);
+            }
+            if (hs[3]) {
+                for (int l = 1; l < h; ++l) {
+                    if (hc[l] > H->cap[l] && (rc = ensure_frontier(H, l, hc[l]))) {
+                        destroy_events();
+                        return rc;
+                    }
+                }
+                MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
+                MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st));
+                MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
+                continue;
+            }
+            done = true;
+        }
+    }
     // Rounds are enqueued in growing batches without waiting: every kernel reads
     // the round index and the done / overflow flags on the device.  After a batch
     // the host reads the state; an overflowed frontier is grown and its round rerun.
-    int batch = 4, rounds_done = 0;
-    bool done = H->Nt == 0;  // every tumor covered from the start
+    int batch = 4;
     while (!done) {
         const size_t first_ev = round_ev.size();
         const int n = std::min(batch, max_rounds - rounds_done);
@@ -521,11 +568,16 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         ++timed;
     }
     destroy_events();
+    if (persistent) {  // phase times measured inside the persistent kernel
+        for (int i = 0; i < 4; ++i) kms[i] = (double)work[kWorkPhaseNs + i] * 1e-6;
+        leaf_launches = h >= 2 ? rounds : 0;
+    }
     R->leaf_ms = kms[2];
     R->level1_ms = kms[0];
     R->expand_ms = kms[1];
     R->finalize_ms = kms[3];
-    R->leaf_launches = opts->time_kernels ? (h >= 2 ? timed : 0) : leaf_launches;
+    R->leaf_launches = opts->time_kernels && !persistent ? (h >= 2 ? timed : 0) : leaf_launches;
+    R->mode = persistent ? MH_MODE_PERSISTENT : MH_MODE_LAUNCHES;
     R->kernel_launches = launches;
     R->leaf_words = work[kWorkColWords];
     R->leaf_prefixes = work[kWorkPrefixes];

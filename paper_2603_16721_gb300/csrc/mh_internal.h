@@ -17,6 +17,8 @@ constexpr int kMaxWords = 32;      // per-block row words: Nt, Nn <= 2048
 constexpr int kMaxSamples = 2048;  // Nt <= 2048
 constexpr int kMaxGenes = 65535;   // gene indices are 16-bit in prefixes and keys
 constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxWarpsPerBlock = 32;
+constexpr int kErrTimeout = 4;     // same value as MH_ETIMEOUT
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kCountStride = 16;   // u32 slots per counter array (>= kMaxH + 1)
 
@@ -87,7 +89,19 @@ enum {
     kWorkScored = 2,     // leaves whose TP / FP were evaluated exactly
     kWorkAluOps = 3,     // 32-bit integer operations of those steps (see mh_kernels.cu)
     kWorkDense = 4,      // prefixes taken by the dense (row) path
-    kWorkCount = 8
+    kWorkPhaseNs = 5,    // persistent solve: ns spent in depth 1, depths 2..h-1, leaves, end of round (4 slots)
+    kWorkCount = 12
+};
+
+// Frontier buffers of the persistent solve (depth l at index l).
+struct Frontiers {
+    Rec *F[kMaxH];
+    u32 cap[kMaxH];
+};
+
+// Grid-wide barrier state of the persistent solve (zeroed before each launch).
+struct GridSync {
+    unsigned count, gen;
 };
 
 // Launchers (mh_kernels.cu).
@@ -102,6 +116,14 @@ void launch_expand(const Cohort &c, const Solve &s, int level, const Rec *Fin, c
 void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin, u32 cap_in, int grid,
                  cudaStream_t st);
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
+
+// Persistent solve: all rounds in one cooperative launch of `grid` blocks
+// (persistent_grid() = the co-resident maximum, 0 if it cannot be determined).
+// It returns when the solve is done, a frontier overflowed (state) or a grid
+// barrier timed out (state error = kErrTimeout).
+int persistent_grid(int num_sms);
+cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
+                                    u32 *counts, int grid, cudaStream_t st);
 int level1_grid(const Cohort &c);
 
 // Message returned by mh_last_error() on the calling thread.

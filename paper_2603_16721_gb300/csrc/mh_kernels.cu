@@ -224,6 +224,16 @@ __device__ __forceinline__ void copy_rec(Rec *dst, const Rec *src)
     for (int i = 0; i < (int)(sizeof(Rec) / 16); ++i) b[i] = a[i];
 }
 
+// Frontier record from global memory, read through L2 only (records are
+// rewritten every round; a persistent kernel must not see stale L1 lines).
+__device__ __forceinline__ void load_rec(Rec *dst, const Rec *src)
+{
+    const uint4 *a = reinterpret_cast<const uint4 *>(src);
+    uint4 *b = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(Rec) / 16); ++i) b[i] = __ldcg(a + i);
+}
+
 // Per-warp scratch: one batch of frontier records and their child ranges.
 struct Batch {
     Rec r[kBatch];
@@ -245,7 +255,7 @@ __device__ __forceinline__ int batch_prepare(const Rec *Fin, u64 first, u64 stri
     const bool valid = i < count;
     int lo = 1, hi = 0, ky = 0, kn = 0;
     if (valid) {
-        copy_rec(&b.r[lane], &Fin[i]);
+        load_rec(&b.r[lane], &Fin[i]);
         lo = prefix_gene(b.r[lane].p, L - 1) + 1;
         hi = hi_bound;
         ky = b.r[lane].ky;
@@ -271,7 +281,7 @@ __device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, con
 {
     u64 y = 0, n = 0;
     if (lane < c.Wt) {
-        y = s.U[lane];
+        y = __ldcg(&s.U[lane]);
         for (int i = 0; i < L; ++i) y &= c.T[(size_t)prefix_gene(p, i) * c.WTp + lane];
     }
     if (lane < c.Wn) {
@@ -441,46 +451,32 @@ __device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Re
 }
 
 // ---------------------------------------------------------------------------
-
-__global__ void k_transpose(int G, const u64 *rows, int row_stride, int samples, int GW, u64 *cols)
-{
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)samples * GW;
-    if (t >= total) return;
-    const int s = (int)(t / GW), wi = (int)(t % GW);
-    const int sw = s >> 6, sb = s & 63;
-    u64 word = 0;
-    for (int b = 0; b < 64; ++b) {
-        const int g = wi * 64 + b;
-        if (g < G) word |= ((rows[(size_t)g * row_stride + sw] >> sb) & 1ull) << b;
-    }
-    cols[t] = word;
-}
-
-__global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
-{
-    const int w = threadIdx.x;
-    if (w < c.WTp) {
-        const int rem = c.Nt - 64 * w;
-        s.U[w] = rem >= 64 ? ~0ull : (rem <= 0 ? 0ull : ((1ull << rem) - 1ull));
-    }
-    if (w < kStateWords) s.state[w] = w == kStMaxRounds ? max_rounds : 0;
-}
+// Phases of one greedy round.  Each is written for the whole grid of the kernel
+// that runs it (blockIdx / gridDim): the one-kernel-per-phase path wraps each in
+// its own kernel; the persistent solve kernel runs them back to back with a grid
+// barrier in between.  Data that changes during a solve (U, frontier records,
+// counters, slots) is read with L2-only loads so that a persistent kernel never
+// sees a stale L1 line written by another SM.
 
 // Re-scores the previous round's best candidates against the current U (one warp
-// per key, lane w on word w).  A key still covering an uncovered
-// tumor is a candidate of this round, so the largest value is a lower bound on
-// this round's best: the leaf kernel need not score what cannot reach it.
-__device__ void rescore_slots(const Cohort &c, const Solve &s)
+// per key, lane w on word w).  A key still covering an uncovered tumor is a
+// candidate of this round, so the largest value is a lower bound on this round's
+// best: the leaf phase need not score what cannot reach it.
+__device__ void rescore_candidates(const Cohort &c, const Solve &s)
 {
     const int lane = threadIdx.x & 31;
     const int h = s.h;
     u64 hint = 0;
-    for (int i = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); i < kCandidates; i += gridDim.x * kWarpsPerBlock) {
-        const Key k = s.cand[i];
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < kCandidates;
+         i += gridDim.x * (blockDim.x >> 5)) {
+        Key k;
+        k.s = __ldcg(&s.cand[i].s);
         if (k.s == 0) continue;
+        k.t0 = __ldcg(&s.cand[i].t0);
+        k.t1 = __ldcg(&s.cand[i].t1);
+        k.t2 = __ldcg(&s.cand[i].t2);
         u64 y = 0, n = 0;
-        if (lane < c.Wt) y = s.U[lane];
+        if (lane < c.Wt) y = __ldcg(&s.U[lane]);
         if (lane < c.Wn) n = ~0ull;
         for (int q = 0; q < h; ++q) {
             const int g = (int)c.inv[key_get(k, q)];
@@ -500,77 +496,76 @@ __device__ void rescore_slots(const Cohort &c, const Solve &s)
 }
 
 // Depth 1: y_1(g) = U & x_g for g in [0, G-h] (0-based).  For h = 1 these are
-// the leaves and are scored here; otherwise the non-empty ones (all of them with
-// pruning off) become depth-1 records.
-__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Rec *F1, u32 *n1, u32 cap1)
+// the leaves and are scored here (the block's best goes to its slot); otherwise
+// the non-empty ones (all of them with pruning off) become depth-1 records.
+// Every thread of the block must call it.
+__device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1)
 {
-    if (halted(s)) return;
-    const int round = s.state[kStRound];
     const int lane = threadIdx.x & 31;
-    if (s.h > 1) rescore_slots(c, s);
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int last = c.G - s.h;  // 0-based inclusive bound of depth 1
-    const bool in = g <= last;
-    int ky = 0;
-    if (in) {
-        const u64 *row = c.T + (size_t)g * c.WTp;
-        for (int w = 0; w < c.Wt; ++w) ky += __popcll(row[w] & s.U[w]);
-    }
-    const bool nonempty = ky > 0;
-    const unsigned bin = __ballot_sync(kFull, in), bne = __ballot_sync(kFull, nonempty);
-    if (lane == 0) count_level(s, round, 1, (u64)__popc(bin), (u64)__popc(bin & ~bne));
-    if (s.h == 1) {
-        Key best = key_empty();
-        if (nonempty) {
-            int fp = 0;
-            const u64 *nrow = c.N + (size_t)g * c.WNp;
-            for (int w = 0; w < c.Wn; ++w) fp += __popcll(nrow[w]);
-            best.s = s.a_num * (u64)ky + s.a_den * (u64)(c.Nn - fp) + 1;
-            key_put(best, 0, c.orig[g]);
+    const int h = s.h;
+    if (h > 1) rescore_candidates(c, s);
+    const int last = c.G - h;  // 0-based inclusive bound of depth 1
+    Key best = key_empty();
+    for (int base = blockIdx.x * blockDim.x; base < c.G; base += gridDim.x * blockDim.x) {
+        const int g = base + threadIdx.x;
+        const bool in = g <= last;
+        int ky = 0;
+        if (in) {
+            const u64 *row = c.T + (size_t)g * c.WTp;
+            for (int w = 0; w < c.Wt; ++w) ky += __popcll(row[w] & __ldcg(&s.U[w]));
         }
-        block_commit_best(best, s.slots);
-        return;
+        const bool nonempty = ky > 0;
+        const unsigned bin = __ballot_sync(kFull, in), bne = __ballot_sync(kFull, nonempty);
+        if (lane == 0) count_level(s, round, 1, (u64)__popc(bin), (u64)__popc(bin & ~bne));
+        if (h == 1) {
+            if (nonempty) {
+                int fp = 0;
+                const u64 *nrow = c.N + (size_t)g * c.WNp;
+                for (int w = 0; w < c.Wn; ++w) fp += __popcll(nrow[w]);
+                Key k = key_empty();
+                k.s = s.a_num * (u64)ky + s.a_den * (u64)(c.Nn - fp) + 1;
+                key_put(k, 0, c.orig[g]);
+                if (key_better(k, best)) best = k;
+            }
+            continue;
+        }
+        const bool keep = s.prune ? in : nonempty;
+        const u32 pos = warp_reserve(keep ? 1 : 0, n1, lane);
+        if (!keep || pos >= cap1) continue;
+        Rec r;
+        r.p.w0 = (u64)g;
+        r.p.w1 = 0;
+        r.pad[0] = r.pad[1] = r.pad[2] = 0;
+        const u64 *trow = c.T + (size_t)g * c.WTp;
+        const u64 *nrow = c.N + (size_t)g * c.WNp;
+        int kn = 0;
+        for (int w = 0; w < c.Wn; ++w) kn += __popcll(nrow[w]);
+        if (!is_dense(ky, kn)) {
+            int k = 0;
+            for (int w = 0; w < c.Wt; ++w)
+                for (u64 y = trow[w] & __ldcg(&s.U[w]); y; y &= y - 1)
+                    r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+            k = kListT;
+            for (int w = 0; w < c.Wn; ++w)
+                for (u64 y = nrow[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        }
+        r.ky = sat16(ky);
+        r.kn = sat16(kn);
+        copy_rec(&F1[pos], &r);
     }
-    const bool keep = s.prune ? in : nonempty;
-    const u32 pos = warp_reserve(keep ? 1 : 0, n1, lane);
-    if (!keep || pos >= cap1) return;
-    Rec r;
-    r.p.w0 = (u64)g;
-    r.p.w1 = 0;
-    r.pad[0] = r.pad[1] = r.pad[2] = 0;
-    const u64 *trow = c.T + (size_t)g * c.WTp;
-    const u64 *nrow = c.N + (size_t)g * c.WNp;
-    int kn = 0;
-    for (int w = 0; w < c.Wn; ++w) kn += __popcll(nrow[w]);
-    if (!is_dense(ky, kn)) {
-        int k = 0;
-        for (int w = 0; w < c.Wt; ++w)
-            for (u64 y = trow[w] & s.U[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
-        k = kListT;
-        for (int w = 0; w < c.Wn; ++w)
-            for (u64 y = nrow[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
-    }
-    r.ky = sat16(ky);
-    r.kn = sat16(kn);
-    copy_rec(&F1[pos], &r);
+    if (h == 1) block_commit_best(best, s.slots);
 }
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
 // every depth-(level-1) record become depth-level records.
-__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, const Rec *Fin,
-                                                        const u32 *nin, u32 cap_in, Rec *Fout, u32 *nout, u32 cap)
+__device__ void phase_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, u32 count,
+                             Rec *Fout, u32 *nout, u32 cap, Batch &b)
 {
-    __shared__ Batch scratch[kWarpsPerBlock];
-    if (halted(s)) return;
-    const u32 count = *nin;
-    if (input_overflowed(s, count, cap_in)) return;
-    const int round = s.state[kStRound];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Batch &b = scratch[warp];
     const int L = level - 1;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
     const bool all_children = s.prune != 0;
-    const u64 nw = (u64)gridDim.x * kWarpsPerBlock, gw = (u64)blockIdx.x * kWarpsPerBlock + warp;
+    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
@@ -645,186 +640,341 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int l
 // S = a_num * TP + a_den * (Nn - FP); the best (score desc, original tuple asc)
 // goes to the block's slot.  A record whose bound a_num * |y| + a_den * Nn is
 // below the best score known to exist cannot hold the round's winner, so its
-// leaves are tested (and counted) but not scored.
-__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
+// leaves are tested (and counted) but not scored.  Every thread of the block
+// must call it.
+__device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, u32 count, Batch &b)
 {
-    __shared__ Batch scratch[kWarpsPerBlock];
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Batch &b = scratch[warp];
-    if (halted(s) || input_overflowed(s, *nin, cap_in)) return;
-    const bool done = false;
-    const int round = s.state[kStRound];
     u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const int h = s.h, L = h - 1;
-    if (!done) {
-        const u32 count = *nin;
-        const u64 nn_term = s.a_den * (u64)c.Nn + 1;
-        const u64 nw = (u64)gridDim.x * kWarpsPerBlock, gw = (u64)blockIdx.x * kWarpsPerBlock + warp;
-        for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
-            unsigned dense;
-            const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited);
-            prefixes += (u64)(gw + (kb + lane) * nw < count);
-            // only candidates at least as good as the best score known to exist can win
-            u64 thr = 0;
-            if (lane == 0) thr = *(volatile u64 *)s.best_hint;
-            thr = warp_max_u64(thr > best.s ? thr : best.s);
-            int j = 0;
-            for (int tb = 0; tb < total; tb += 32 * kIlp) {
-                int jj[kIlp], wi[kIlp], ky[kIlp];
-                u64 m[kIlp], rw[kIlp];
-                sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
+    const u64 nn_term = s.a_den * (u64)c.Nn + 1;
+    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
+    for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
+        unsigned dense;
+        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited);
+        prefixes += (u64)(gw + (kb + lane) * nw < count);
+        // only candidates at least as good as the best score known to exist can win
+        u64 thr = 0;
+        if (lane == 0) thr = *(volatile u64 *)s.best_hint;
+        thr = warp_max_u64(thr > best.s ? thr : best.s);
+        int j = 0;
+        for (int tb = 0; tb < total; tb += 32 * kIlp) {
+            int jj[kIlp], wi[kIlp], ky[kIlp];
+            u64 m[kIlp], rw[kIlp];
+            sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
 #pragma unroll
-                for (int u = 0; u < kIlp; ++u) {
-                    alive += (u64)__popcll(m[u]);
-                    words += (u64)ky[u];
-                    if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
-                        const Rec &r = b.r[jj[u]];
-                        scored += (u64)score_word(c, s, r, wi[u], m[u], L, thr, best);
-                        words += (u64)(ky[u] + r.kn);
-                    }
+            for (int u = 0; u < kIlp; ++u) {
+                alive += (u64)__popcll(m[u]);
+                words += (u64)ky[u];
+                if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
+                    const Rec &r = b.r[jj[u]];
+                    scored += (u64)score_word(c, s, r, wi[u], m[u], L, thr, best);
+                    words += (u64)(ky[u] + r.kn);
                 }
             }
-            // dense records: the whole warp, leaves scored from row popcounts
-            while (dense) {
-                const int jd = __ffs(dense) - 1;
-                dense &= dense - 1;
-                const Prefix p = b.r[jd].p;
-                const int lo = b.lo[jd], hi = b.hi[jd];
-                const int ky = b.r[jd].ky;
-                unsigned by, bn;
-                dense_setup(c, s, p, L, b, by, bn, lane);
-                if (lane == 0) ++dense_n;
-                int po[kMaxH - 1];
-                prefix_orig(c, p, L, po);
-                const bool score = s.a_num * (u64)ky + nn_term >= thr;
-                for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
-                    const int wi = wb + lane;
-                    if (wi > (hi >> 6)) break;
-                    u64 m = dense_sibling_word(c, b, by, wi) & range_word(wi, lo, hi);
-                    alive += (u64)__popcll(m);
-                    words += (u64)ky;
-                    if (!score) continue;
-                    while (m) {
-                        const int bt = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        const int g = wi * 64 + bt;
-                        const u64 *trow = c.T + (size_t)g * c.WTp;
-                        const u64 *nrow = c.N + (size_t)g * c.WNp;
-                        int tp = 0, fp = 0;
-                        for (unsigned bits = by; bits; bits &= bits - 1) {
-                            const int w = __ffs(bits) - 1;
-                            tp += __popcll(b.ys[w] & trow[w]);
-                        }
-                        for (unsigned bits = bn; bits; bits &= bits - 1) {
-                            const int w = __ffs(bits) - 1;
-                            fp += __popcll(b.ns[w] & nrow[w]);
-                        }
-                        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-                        ++scored;
-                        if (s1 < best.s || s1 < thr) continue;
-                        const Key k = leaf_key(s1, po, L, c.orig[g]);
-                        if (key_better(k, best)) best = k;
-                    }
-                }
-                __syncwarp();
-            }
-            // publish the warp's best score so that other warps can skip hopeless records
-            const u64 wbest = warp_max_u64(best.s);
-            if (lane == 0 && wbest > thr) atomicMax(s.best_hint, wbest);
         }
+        // dense records: the whole warp, leaves scored from row popcounts
+        while (dense) {
+            const int jd = __ffs(dense) - 1;
+            dense &= dense - 1;
+            const Prefix p = b.r[jd].p;
+            const int lo = b.lo[jd], hi = b.hi[jd];
+            const int ky = b.r[jd].ky;
+            unsigned by, bn;
+            dense_setup(c, s, p, L, b, by, bn, lane);
+            if (lane == 0) ++dense_n;
+            int po[kMaxH - 1];
+            prefix_orig(c, p, L, po);
+            const bool score = s.a_num * (u64)ky + nn_term >= thr;
+            for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
+                const int wi = wb + lane;
+                if (wi > (hi >> 6)) break;
+                u64 m = dense_sibling_word(c, b, by, wi) & range_word(wi, lo, hi);
+                alive += (u64)__popcll(m);
+                words += (u64)ky;
+                if (!score) continue;
+                while (m) {
+                    const int bt = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const int g = wi * 64 + bt;
+                    const u64 *trow = c.T + (size_t)g * c.WTp;
+                    const u64 *nrow = c.N + (size_t)g * c.WNp;
+                    int tp = 0, fp = 0;
+                    for (unsigned bits = by; bits; bits &= bits - 1) {
+                        const int w = __ffs(bits) - 1;
+                        tp += __popcll(b.ys[w] & trow[w]);
+                    }
+                    for (unsigned bits = bn; bits; bits &= bits - 1) {
+                        const int w = __ffs(bits) - 1;
+                        fp += __popcll(b.ns[w] & nrow[w]);
+                    }
+                    const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+                    ++scored;
+                    if (s1 < best.s || s1 < thr) continue;
+                    const Key k = leaf_key(s1, po, L, c.orig[g]);
+                    if (key_better(k, best)) best = k;
+                }
+            }
+            __syncwarp();
+        }
+        // publish the warp's best score so that other warps can skip hopeless records
+        const u64 wbest = warp_max_u64(best.s);
+        if (lane == 0 && wbest > thr) atomicMax(s.best_hint, wbest);
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
     words = warp_sum_u64(words);
     prefixes = warp_sum_u64(prefixes);
     scored = warp_sum_u64(scored);
-    if (!done && lane == 0) {
+    if (lane == 0) {
         count_level(s, round, h, visited, visited - alive);
-        atomicAdd(s.work + kWorkColWords, words);
-        atomicAdd(s.work + kWorkPrefixes, prefixes);
-        atomicAdd(s.work + kWorkScored, scored);
-        atomicAdd(s.work + kWorkDense, dense_n);
+        if (words) atomicAdd(s.work + kWorkColWords, words);
+        if (prefixes) atomicAdd(s.work + kWorkPrefixes, prefixes);
+        if (scored) atomicAdd(s.work + kWorkScored, scored);
+        if (dense_n) atomicAdd(s.work + kWorkDense, dense_n);
     }
     block_commit_best(best, s.slots);
 }
 
-// End of a round: reduce the per-block bests, record the winner with its TP / FP,
-// clear the tumors it covers (DelCols), keep the best other candidates for the
-// next round's threshold, reset the frontier sizes and advance the round; raise
-// the done flag when nothing was found, every tumor is covered or the round limit
-// is reached.  One block.
-__global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *counts)
+// End of a round, by one block: reduce the per-block bests, record the winner
+// with its TP / FP, clear the tumors it covers (DelCols), keep the best other
+// candidates for the next round's threshold, reset the frontier sizes and advance
+// the round; raise the done flag when nothing was found, every tumor is covered or
+// the round limit is reached.  Every thread of the block must call it.
+__device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int nslots)
 {
-    __shared__ Key wbest[kWarpsPerBlock];
+    __shared__ Key wbest[kMaxWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
-    if (halted(s)) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     Key best = key_empty();
-    for (int i = threadIdx.x; i < s.nslots; i += blockDim.x) {
-        const Key k = s.slots[i];
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        Key k;
+        k.s = __ldcg(&s.slots[i].s);
+        k.t0 = __ldcg(&s.slots[i].t0);
+        k.t1 = __ldcg(&s.slots[i].t1);
+        k.t2 = __ldcg(&s.slots[i].t2);
         if (key_better(k, best)) best = k;
         s.slots[i] = key_empty();
     }
-    // the best kCandidates / kWarpsPerBlock of each warp's lane bests become next
-    // round's candidates; the block's best is the winner
+    // the best kCandidates of the warps' lane bests become next round's candidates
     Key mine = best;
-    for (int r = 0; r < kCandidates / kWarpsPerBlock; ++r) {
+    const int per_warp = (kCandidates + nwarps - 1) / nwarps;
+    for (int r = 0; r < per_warp; ++r) {
         const Key m = warp_max_key(mine);
-        if (lane == 0) s.cand[warp * (kCandidates / kWarpsPerBlock) + r] = m;
+        const int idx = warp * per_warp + r;
+        if (lane == 0 && idx < kCandidates) s.cand[idx] = m;
         if (m.s != 0 && mine.s == m.s && mine.t0 == m.t0 && mine.t1 == m.t1 && mine.t2 == m.t2) mine = key_empty();
         if (r == 0 && lane == 0) wbest[warp] = m;
     }
     if (threadIdx.x < kCountStride) counts[threadIdx.x] = 0;
     __syncthreads();
-    if (warp != 0) return;
-    best = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
-    best = warp_max_key(best);
-    const int round = s.state[kStRound];
-    const bool last_round = round + 1 >= s.state[kStMaxRounds];
-    if (lane == 0) {
-        *s.best_hint = 0;
-        s.state[kStRound] = round + 1;
+    if (warp == 0) {
+        best = lane < nwarps ? wbest[lane] : key_empty();
+        best = warp_max_key(best);
+        const int round = *(volatile int *)&s.state[kStRound];
+        const bool last_round = round + 1 >= *(volatile int *)&s.state[kStMaxRounds];
+        if (lane == 0) {
+            *(volatile u64 *)s.best_hint = 0;
+            s.state[kStRound] = round + 1;
+        }
+        if (best.s == 0) {
+            if (lane == 0) s.state[kStDone] = 1;
+        } else {
+            if (lane < h) {
+                const int o = key_get(best, lane);
+                os[lane] = o;
+                gs[lane] = (int)c.inv[o];
+            }
+            __syncwarp();
+            u64 y = 0, n = 0, u = 0;
+            if (lane < c.Wt) {
+                u = __ldcg(&s.U[lane]);
+                y = u;
+                for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+            }
+            if (lane < c.Wn) {
+                n = ~0ull;
+                for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
+            }
+            int tp = __popcll(y), fp = __popcll(n);
+            for (int off = 16; off; off >>= 1) {
+                tp += __shfl_xor_sync(kFull, tp, off);
+                fp += __shfl_xor_sync(kFull, fp, off);
+            }
+            if (lane < c.Wt) {
+                u &= ~y;
+                s.U[lane] = u;
+            }
+            const unsigned left = __ballot_sync(kFull, u != 0);
+            if (lane == 0) {
+                const int k = *(volatile int *)&s.state[kStK];
+                int *r = s.res + (size_t)k * (h + 2);
+                for (int i = 0; i < h; ++i) r[i] = os[i];
+                r[h] = tp;
+                r[h + 1] = fp;
+                s.state[kStK] = k + 1;
+                if (!left || last_round) s.state[kStDone] = 1;
+            }
+        }
     }
-    if (best.s == 0) {
-        if (lane == 0) s.state[kStDone] = 1;
-        return;
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// One kernel per phase.
+
+__global__ void k_transpose(int G, const u64 *rows, int row_stride, int samples, int GW, u64 *cols)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)samples * GW;
+    if (t >= total) return;
+    const int s = (int)(t / GW), wi = (int)(t % GW);
+    const int sw = s >> 6, sb = s & 63;
+    u64 word = 0;
+    for (int b = 0; b < 64; ++b) {
+        const int g = wi * 64 + b;
+        if (g < G) word |= ((rows[(size_t)g * row_stride + sw] >> sb) & 1ull) << b;
     }
-    if (lane < h) {
-        const int o = key_get(best, lane);
-        os[lane] = o;
-        gs[lane] = (int)c.inv[o];
+    cols[t] = word;
+}
+
+__global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
+{
+    const int w = threadIdx.x;
+    if (w < c.WTp) {
+        const int rem = c.Nt - 64 * w;
+        s.U[w] = rem >= 64 ? ~0ull : (rem <= 0 ? 0ull : ((1ull << rem) - 1ull));
     }
-    __syncwarp();
-    u64 y = 0, n = 0;
-    if (lane < c.Wt) {
-        y = s.U[lane];
-        for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+    if (w < kStateWords) s.state[w] = w == kStMaxRounds ? max_rounds : 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Rec *F1, u32 *n1, u32 cap1)
+{
+    if (halted(s)) return;
+    phase_level1(c, s, s.state[kStRound], F1, n1, cap1);
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, const Rec *Fin,
+                                                        const u32 *nin, u32 cap_in, Rec *Fout, u32 *nout, u32 cap)
+{
+    __shared__ Batch scratch[kWarpsPerBlock];
+    if (halted(s)) return;
+    const u32 count = *nin;
+    if (input_overflowed(s, count, cap_in)) return;
+    phase_expand(c, s, s.state[kStRound], level, Fin, count, Fout, nout, cap, scratch[threadIdx.x >> 5]);
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
+{
+    __shared__ Batch scratch[kWarpsPerBlock];
+    if (halted(s) || input_overflowed(s, *nin, cap_in)) return;
+    phase_leaf(c, s, s.state[kStRound], Fin, *nin, scratch[threadIdx.x >> 5]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *counts)
+{
+    if (halted(s)) return;
+    phase_finalize(c, s, counts, s.nslots);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent solve: every round of the greedy loop in one cooperative launch.
+
+// Grid barrier with a bounded wait: a block that waits longer than about two
+// seconds records MH_ETIMEOUT in the state and returns false instead of hanging.
+__device__ __forceinline__ bool grid_sync(GridSync *g, int *state)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned gen = *(volatile unsigned *)&g->gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&g->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&g->count, 0u);
+            __threadfence();
+            atomicAdd(&g->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*(volatile unsigned *)&g->gen == gen) {
+                __nanosleep(64);
+                if (++spins > (1ull << 25)) {
+                    atomicExch(&state[kStError], kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
     }
-    if (lane < c.Wn) {
-        n = ~0ull;
-        for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
-    }
-    int tp = __popcll(y), fp = __popcll(n);
-    for (int off = 16; off; off >>= 1) {
-        tp += __shfl_xor_sync(kFull, tp, off);
-        fp += __shfl_xor_sync(kFull, fp, off);
-    }
-    u64 u = 0;
-    if (lane < c.Wt) {
-        u = s.U[lane] & ~y;
-        s.U[lane] = u;
-    }
-    const unsigned left = __ballot_sync(kFull, u != 0);
-    if (lane == 0) {
-        const int k = s.state[kStK];
-        int *r = s.res + (size_t)k * (h + 2);
-        for (int i = 0; i < h; ++i) r[i] = os[i];
-        r[h] = tp;
-        r[h + 1] = fp;
-        s.state[kStK] = k + 1;
-        if (!left || last_round) s.state[kStDone] = 1;
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ u64 global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
+{
+    __shared__ Batch scratch[kWarpsPerBlock];
+    __shared__ int stop;
+    Batch &b = scratch[threadIdx.x >> 5];
+    const int h = s.h;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    u64 t = timer ? global_ns() : 0;
+    auto lap = [&](int phase) {
+        if (timer) {
+            const u64 now = global_ns();
+            atomicAdd(s.work + kWorkPhaseNs + phase, now - t);
+            t = now;
+        }
+    };
+    for (;;) {
+        if (threadIdx.x == 0)
+            stop = *(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStOverflow] |
+                   *(volatile int *)&s.state[kStError];
+        __syncthreads();
+        if (stop) break;
+        const int round = *(volatile int *)&s.state[kStRound];
+        phase_level1(c, s, round, f.F[1], counts + 1, f.cap[1]);
+        if (!grid_sync(gsync, s.state)) return;
+        lap(0);
+        bool overflow = false;
+        for (int l = 2; l <= h - 1 && !overflow; ++l) {
+            const u32 count = __ldcg(&counts[l - 1]);
+            if (count > f.cap[l - 1]) {
+                overflow = true;
+                break;
+            }
+            phase_expand(c, s, round, l, f.F[l - 1], count, f.F[l], counts + l, f.cap[l], b);
+            if (!grid_sync(gsync, s.state)) return;
+        }
+        if (!overflow && h >= 2) {
+            lap(1);
+            const u32 count = __ldcg(&counts[h - 1]);
+            if (count > f.cap[h - 1]) {
+                overflow = true;
+            } else {
+                phase_leaf(c, s, round, f.F[h - 1], count, b);
+                if (!grid_sync(gsync, s.state)) return;
+                lap(2);
+            }
+        }
+        if (overflow) {
+            // every block read the same counts after the same barrier: all leave together
+            if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+            return;
+        }
+        if (blockIdx.x == 0) phase_finalize(c, s, counts, gridDim.x);
+        if (!grid_sync(gsync, s.state)) return;
+        lap(3);
     }
 }
 
@@ -876,6 +1026,23 @@ void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st)
 {
     k_finalize<<<1, kThreads, 0, st>>>(c, s, counts);
+}
+
+int persistent_grid(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kThreads, 0) != cudaSuccess) return 0;
+    return per_sm * num_sms;
+}
+
+cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
+                                    u32 *counts, int grid, cudaStream_t st)
+{
+    Cohort cc = c;
+    Solve ss = s;
+    Frontiers ff = f;
+    void *args[] = {&cc, &ss, &ff, &gsync, &counts};
+    return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
 }  // namespace mh

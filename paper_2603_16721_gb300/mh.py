@@ -21,6 +21,7 @@ from . import _build
 
 MH_OK, MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT, MH_EAGAIN, MH_EREJECT = range(7)
 MH_PRUNE_PAPER, MH_PRUNE_OFF = 0, 1
+MH_MODE_PERSISTENT, MH_MODE_LAUNCHES = 0, 1
 _NAMES = {0: "MH_OK", 1: "MH_EINVAL", 2: "MH_ENOMEM", 3: "MH_ECUDA", 4: "MH_ETIMEOUT", 5: "MH_EAGAIN",
           6: "MH_EREJECT"}
 
@@ -41,7 +42,7 @@ class mh_rational(ctypes.Structure):
 
 class mh_solve_opts(ctypes.Structure):
     _fields_ = [("h", ctypes.c_int32), ("alpha", mh_rational), ("prune", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32), ("time_kernels", ctypes.c_int32)]
+                ("max_rounds", ctypes.c_int32), ("time_kernels", ctypes.c_int32), ("mode", ctypes.c_int32)]
 
 
 class mh_result(ctypes.Structure):
@@ -53,7 +54,8 @@ class mh_result(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("leaf_words", ctypes.c_uint64),
                 ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
                 ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64),
-                ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double)]
+                ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
+                ("mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -129,6 +131,7 @@ class Result:
     level1_ms: float = 0.0
     expand_ms: float = 0.0
     finalize_ms: float = 0.0
+    mode: int = 0
 
     @property
     def k(self) -> int:
@@ -155,7 +158,8 @@ def _to_result(p) -> Result:
                  kernel_launches=int(r.kernel_launches), leaf_words=int(r.leaf_words),
                  leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
                  leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense),
-                 level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms))
+                 level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms),
+                 mode=int(r.mode))
     load().mh_result_free(p)
     return out
 
@@ -214,8 +218,8 @@ def mh_solve(handle: Handle, h: int, alpha=(1, 10)) -> Result:
 
 
 def mh_solve_ex(handle: Handle, h: int, alpha=(1, 10), prune: int = MH_PRUNE_PAPER, max_rounds: int = 0,
-                time_kernels: bool = False) -> Result:
-    o = mh_solve_opts(h, mh_rational(*alpha), prune, max_rounds, int(bool(time_kernels)))
+                time_kernels: bool = False, mode: int = MH_MODE_PERSISTENT) -> Result:
+    o = mh_solve_opts(h, mh_rational(*alpha), prune, max_rounds, int(bool(time_kernels)), mode)
     p = ctypes.POINTER(mh_result)()
     _check(load().mh_solve_ex(handle.ptr, ctypes.byref(o), ctypes.byref(p)))
     return _to_result(p)

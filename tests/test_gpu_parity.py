@@ -46,10 +46,11 @@ def _same(gpu, ref, counters=True):
 def test_hand_cases(mh, case):
     bm = case.bitmaps()
     for prune in (mh.MH_PRUNE_PAPER, mh.MH_PRUNE_OFF):
-        got = _gpu(mh, bm, case.G, case.Nt, case.Nn, case.h, case.alpha, prune=prune)
-        assert got.records() == case.expect
-        ref = oracle.pdfs(bm, case.G, case.Nt, case.Nn, case.h, case.alpha, prune=prune == mh.MH_PRUNE_PAPER)
-        _same(got, ref)
+        for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
+            got = _gpu(mh, bm, case.G, case.Nt, case.Nn, case.h, case.alpha, prune=prune, mode=mode)
+            assert got.records() == case.expect
+            ref = oracle.pdfs(bm, case.G, case.Nt, case.Nn, case.h, case.alpha, prune=prune == mh.MH_PRUNE_PAPER)
+            _same(got, ref)
 
 
 @pytest.mark.parametrize("seed", range(60))
@@ -63,6 +64,7 @@ def test_random_small(mh, seed):
     alpha = [(1, 10), (1, 1), (3, 7), (0, 1), (7, 2)][seed % 5]
     ref = oracle.pdfs(bm, G, Nt, Nn, h, alpha)
     _same(_gpu(mh, bm, G, Nt, Nn, h, alpha), ref)
+    _same(_gpu(mh, bm, G, Nt, Nn, h, alpha, mode=mh.MH_MODE_LAUNCHES), ref)
     if G <= 40 and h <= 3:
         _same(_gpu(mh, bm, G, Nt, Nn, h, alpha, prune=mh.MH_PRUNE_OFF),
               oracle.pdfs(bm, G, Nt, Nn, h, alpha, prune=False))
@@ -111,9 +113,11 @@ def _golden(name, spec, h):
 def test_c2_full_solve_matches_oracle(mh):
     """The benchmark workload (h=3, G=5,000, Nt=500, Nn=300), whole greedy solve."""
     c, recs, vis, pru = _golden("c2_pdfs", synth.c2(), 3)
-    got = _gpu(mh, c.bitmaps, c.G, c.Nt, c.Nn, 3)
-    assert got.records() == recs
-    assert np.array_equal(got.visited, vis) and np.array_equal(got.pruned, pru)
+    for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
+        got = _gpu(mh, c.bitmaps, c.G, c.Nt, c.Nn, 3, mode=mode)
+        assert got.mode == mode
+        assert got.records() == recs
+        assert np.array_equal(got.visited, vis) and np.array_equal(got.pruned, pru)
 
 
 def test_c2_exhaustive_first_round_counts(mh):
