@@ -293,6 +293,9 @@ def run_ours(args):
             "breakdown_ms_per_solve": {k: round(sum(getattr(r, k) for r in results) / len(results), 3)
                                        for k in ("level1_ms", "expand_ms", "leaf_ms", "finalize_ms")},
             "mode": "persistent" if r0.mode == mh.MH_MODE_PERSISTENT else "launches",
+            "warp_balance": {k: {"mean_warp_cycles": round(r0.diag[i] / max(1, r0.diag[4 + i]), 1),
+                                 "longest_warp_cycles_per_round": round(r0.diag[2 + i] / max(1, r0.rounds), 1)}
+                             for i, k in enumerate(("expand", "leaf"))},
             "extra": {"p50_ms": statistics.median(step_ms), "p99_ms": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
                       "combos_scored_per_s": scored * value / world, "leaves_tested_per_s": vis_leaves * value / world,
                       "prefixes_pruned_per_s": pruned_prefixes * value / world,

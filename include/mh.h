@@ -112,6 +112,8 @@ typedef struct {
     double expand_ms;        /* end-of-round phases: CUDA events around each kernel with */
     double finalize_ms;      /* time_kernels (launch mode), the device clock (persistent mode) */
     int32_t mode;            /* the mode that ran (MH_MODE_*) */
+    uint64_t diag[8];        /* diagnostics, [expansion, leaf]: summed warp cycles, summed per-round
+                                longest warp cycles, warp count (indices 0-1, 2-3, 4-5) */
 } mh_result;
 
 /* Create a handle for one cohort from packed rows in HOST memory.

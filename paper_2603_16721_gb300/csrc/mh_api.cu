@@ -578,6 +578,11 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     R->finalize_ms = kms[3];
     R->leaf_launches = opts->time_kernels && !persistent ? (h >= 2 ? timed : 0) : leaf_launches;
     R->mode = persistent ? MH_MODE_PERSISTENT : MH_MODE_LAUNCHES;
+    for (int i = 0; i < 2; ++i) {
+        R->diag[i] = work[kWorkWarpSum + i];
+        R->diag[2 + i] = work[kWorkWarpMaxSum + i];
+        R->diag[4 + i] = work[kWorkWarpN + i];
+    }
     R->kernel_launches = launches;
     R->leaf_words = work[kWorkColWords];
     R->leaf_prefixes = work[kWorkPrefixes];

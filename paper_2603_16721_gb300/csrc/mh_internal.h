@@ -90,7 +90,11 @@ enum {
     kWorkAluOps = 3,     // 32-bit integer operations of those steps (see mh_kernels.cu)
     kWorkDense = 4,      // prefixes taken by the dense (row) path
     kWorkPhaseNs = 5,    // persistent solve: ns spent in depth 1, depths 2..h-1, leaves, end of round (4 slots)
-    kWorkCount = 12
+    kWorkWarpSum = 9,    // diagnostics, [expand, leaf]: summed warp cycles of the phase,
+    kWorkWarpMax = 11,   //   the longest warp of the current round,
+    kWorkWarpMaxSum = 13,//   the longest warps summed over rounds,
+    kWorkWarpN = 15,     //   warp count
+    kWorkCount = 20
 };
 
 // Frontier buffers of the persistent solve (depth l at index l).

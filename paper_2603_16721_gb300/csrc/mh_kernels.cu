@@ -558,9 +558,21 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
 // every depth-(level-1) record become depth-level records.
+// Per-warp cycle statistics of a phase (k = 0 expand, 1 leaf), for diagnostics.
+__device__ __forceinline__ void warp_cycles(const Solve &s, int k, long long t0, int lane)
+{
+    if (lane == 0) {
+        const u64 dt = (u64)(clock64() - t0);
+        atomicAdd(s.work + kWorkWarpSum + k, dt);
+        atomicMax(s.work + kWorkWarpMax + k, dt);
+        atomicAdd(s.work + kWorkWarpN + k, 1ull);
+    }
+}
+
 __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, u32 count,
                              Rec *Fout, u32 *nout, u32 cap, Batch &b)
 {
+    const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = level - 1;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
@@ -634,6 +646,7 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
     if (lane == 0) count_level(s, round, level, visited, visited - alive);
+    warp_cycles(s, 0, t0, lane);
 }
 
 // Depth h (leaves): every non-empty leaf is a candidate with score
@@ -644,6 +657,7 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
 // must call it.
 __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, u32 count, Batch &b)
 {
+    const long long t0 = clock64();
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
@@ -734,6 +748,7 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
         if (scored) atomicAdd(s.work + kWorkScored, scored);
         if (dense_n) atomicAdd(s.work + kWorkDense, dense_n);
     }
+    warp_cycles(s, 1, t0, lane);
     block_commit_best(best, s.slots);
 }
 
@@ -778,6 +793,10 @@ __device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int
         if (lane == 0) {
             *(volatile u64 *)s.best_hint = 0;
             s.state[kStRound] = round + 1;
+        }
+        if (lane < 2) {  // diagnostics: the round's longest warps
+            s.work[kWorkWarpMaxSum + lane] += __ldcg(&s.work[kWorkWarpMax + lane]);
+            s.work[kWorkWarpMax + lane] = 0;
         }
         if (best.s == 0) {
             if (lane == 0) s.state[kStDone] = 1;

@@ -55,7 +55,7 @@ class mh_result(ctypes.Structure):
                 ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
                 ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64),
                 ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
-                ("mode", ctypes.c_int32)]
+                ("mode", ctypes.c_int32), ("diag", ctypes.c_uint64 * 8)]
 
 
 _lib = None
@@ -132,6 +132,7 @@ class Result:
     expand_ms: float = 0.0
     finalize_ms: float = 0.0
     mode: int = 0
+    diag: tuple = ()
 
     @property
     def k(self) -> int:
@@ -159,7 +160,7 @@ def _to_result(p) -> Result:
                  leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
                  leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense),
                  level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms),
-                 mode=int(r.mode))
+                 mode=int(r.mode), diag=tuple(int(x) for x in r.diag))
     load().mh_result_free(p)
     return out
 
