@@ -295,22 +295,6 @@ __device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, con
     __syncwarp();
 }
 
-// OR of the sample-major columns of y_{l-1} at word wi (dense path: samples from the y words).
-__device__ __forceinline__ u64 dense_sibling_word(const Cohort &c, const Batch &b, unsigned by, int wi)
-{
-    u64 m = 0;
-    for (unsigned bits = by; bits; bits &= bits - 1) {
-        const int w = __ffs(bits) - 1;
-        u64 y = b.ys[w];
-        while (y) {
-            const int bt = __ffsll((long long)y) - 1;
-            y &= y - 1;
-            m |= c.CT[(size_t)(w * 64 + bt) * c.GW + wi];
-        }
-    }
-    return m;
-}
-
 // Sibling masks of the items t0, t0+32, ... (kIlp of them) of a batch: the
 // column loads of all of them are issued together.  j is the lane's running
 // record index (items are visited in increasing order).
@@ -610,7 +594,8 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
                 }
             }
         }
-        // dense records: the whole warp
+        // dense records: the whole warp, one child gene per lane, tested on the rows
+        // (y_{l-1} & x_g, the running intersection of Algorithm 2)
         while (dense) {
             const int jd = __ffs(dense) - 1;
             dense &= dense - 1;
@@ -618,26 +603,24 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
             const int lo = b.lo[jd], hi = b.hi[jd];
             unsigned by, bn;
             dense_setup(c, s, p, L, b, by, bn, lane);
-            for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
-                const int wi = wb + lane;
-                u64 m = 0, a = 0;
-                if (wi <= (hi >> 6)) {
-                    const u64 rw = range_word(wi, lo, hi);
-                    m = dense_sibling_word(c, b, by, wi) & rw;
-                    a = all_children ? rw : m;
-                }
-                alive += (u64)__popcll(m);
-                u32 pos = warp_reserve(__popcll(a), nout, lane);
-                while (a) {
-                    const int bt = __ffsll((long long)a) - 1;
-                    a &= a - 1;
-                    if (pos < cap) {
-                        Rec child;
-                        child.pad[0] = child.pad[1] = child.pad[2] = 0;
-                        child_from_rows(c, b, by, bn, p, L, wi * 64 + bt, child);
-                        copy_rec(&Fout[pos], &child);
+            for (int gb = lo; gb <= hi; gb += 32) {
+                const int g = gb + lane;
+                int kyc = 0;
+                if (g <= hi) {
+                    const u64 *trow = c.T + (size_t)g * c.WTp;
+                    for (unsigned bits = by; bits; bits &= bits - 1) {
+                        const int w = __ffs(bits) - 1;
+                        kyc += __popcll(b.ys[w] & trow[w]);
                     }
-                    ++pos;
+                }
+                alive += (u64)(kyc > 0);
+                const bool emit = g <= hi && (all_children || kyc > 0);
+                const u32 pos = warp_reserve(emit ? 1 : 0, nout, lane);
+                if (emit && pos < cap) {
+                    Rec child;
+                    child.pad[0] = child.pad[1] = child.pad[2] = 0;
+                    child_from_rows(c, b, by, bn, p, L, g, child);
+                    copy_rec(&Fout[pos], &child);
                 }
             }
             __syncwarp();
@@ -688,7 +671,8 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
                 }
             }
         }
-        // dense records: the whole warp, leaves scored from row popcounts
+        // dense records: the whole warp, one leaf gene per lane, tested and scored
+        // on the rows (popcounts over the prefix's non-zero words only)
         while (dense) {
             const int jd = __ffs(dense) - 1;
             dense &= dense - 1;
@@ -701,34 +685,31 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
             int po[kMaxH - 1];
             prefix_orig(c, p, L, po);
             const bool score = s.a_num * (u64)ky + nn_term >= thr;
-            for (int wb = lo >> 6; wb <= (hi >> 6); wb += 32) {
-                const int wi = wb + lane;
-                if (wi > (hi >> 6)) break;
-                u64 m = dense_sibling_word(c, b, by, wi) & range_word(wi, lo, hi);
-                alive += (u64)__popcll(m);
-                words += (u64)ky;
-                if (!score) continue;
-                while (m) {
-                    const int bt = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    const int g = wi * 64 + bt;
-                    const u64 *trow = c.T + (size_t)g * c.WTp;
-                    const u64 *nrow = c.N + (size_t)g * c.WNp;
-                    int tp = 0, fp = 0;
-                    for (unsigned bits = by; bits; bits &= bits - 1) {
-                        const int w = __ffs(bits) - 1;
-                        tp += __popcll(b.ys[w] & trow[w]);
-                    }
-                    for (unsigned bits = bn; bits; bits &= bits - 1) {
-                        const int w = __ffs(bits) - 1;
-                        fp += __popcll(b.ns[w] & nrow[w]);
-                    }
-                    const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-                    ++scored;
-                    if (s1 < best.s || s1 < thr) continue;
-                    const Key k = leaf_key(s1, po, L, c.orig[g]);
-                    if (key_better(k, best)) best = k;
+            const int nzy = __popc(by);
+            for (int gb = lo; gb <= hi; gb += 32) {
+                const int g = gb + lane;
+                if (g > hi) break;
+                const u64 *trow = c.T + (size_t)g * c.WTp;
+                int tp = 0;
+                for (unsigned bits = by; bits; bits &= bits - 1) {
+                    const int w = __ffs(bits) - 1;
+                    tp += __popcll(b.ys[w] & trow[w]);
                 }
+                words += (u64)nzy;
+                if (tp == 0) continue;
+                ++alive;
+                if (!score) continue;
+                const u64 *nrow = c.N + (size_t)g * c.WNp;
+                int fp = 0;
+                for (unsigned bits = bn; bits; bits &= bits - 1) {
+                    const int w = __ffs(bits) - 1;
+                    fp += __popcll(b.ns[w] & nrow[w]);
+                }
+                const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+                ++scored;
+                if (s1 < best.s || s1 < thr) continue;
+                const Key k = leaf_key(s1, po, L, c.orig[g]);
+                if (key_better(k, best)) best = k;
             }
             __syncwarp();
         }
