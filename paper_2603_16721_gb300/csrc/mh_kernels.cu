@@ -239,8 +239,9 @@ struct Batch {
     Rec r[kBatch];
     int lo[kBatch], hi[kBatch];     // child range (0-based, inclusive); lo > hi when empty
     int off[kBatch + 1];            // exclusive prefix sum of the sparse records' column words
-    u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words
-    u64 ns[kMaxWords];
+    u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words; expansion: staged
+    u64 ns[kMaxWords];              // child masks and their (record, word) of one item per lane
+    int cx[33];                     // expansion: exclusive prefix sum of the lanes' child counts
 };
 
 // Lane j takes record first + j*stride (if < count) into the warp scratch with
@@ -580,18 +581,41 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
                 if (all_children) m[u] = rw[u];
                 nchild += __popcll(m[u]);
             }
-            u32 pos = warp_reserve(nchild, nout, lane);
+            (void)nchild;
+            // spread the children of each item round over all lanes: lane i builds
+            // children i, i+32, ... of the warp, whichever lane's item they came from
 #pragma unroll
             for (int u = 0; u < kIlp; ++u) {
-                for (u64 a = m[u]; a; a &= a - 1) {
+                const int n = __popcll(m[u]);
+                const int incl = warp_incl_scan(n, lane);
+                const int tot = __shfl_sync(kFull, incl, 31);
+                if (tot == 0) continue;
+                b.ys[lane] = m[u];
+                b.ns[lane] = ((u64)(u32)jj[u] << 32) | (u32)wi[u];
+                b.cx[lane] = incl - n;
+                if (lane == 31) b.cx[32] = incl;
+                u32 base = 0;
+                if (lane == 0) base = atomicAdd(nout, (u32)tot);
+                base = __shfl_sync(kFull, base, 0);
+                __syncwarp();
+                for (int k = lane; k < tot; k += 32) {
+                    int lo = 0, hi = 31;  // source lane: last with cx <= k
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (b.cx[mid] <= k) lo = mid; else hi = mid - 1;
+                    }
+                    u64 x = b.ys[lo];
+                    for (int r = k - b.cx[lo]; r > 0; --r) x &= x - 1;
+                    const u32 pos = base + (u32)k;
                     if (pos < cap) {
+                        const u64 jw = b.ns[lo];
                         Rec child;
                         child.pad[0] = child.pad[1] = child.pad[2] = 0;
-                        child_from_lists(c, b.r[jj[u]], L, wi[u], __ffsll((long long)a) - 1, child);
+                        child_from_lists(c, b.r[(int)(jw >> 32)], L, (int)(u32)jw, __ffsll((long long)x) - 1, child);
                         copy_rec(&Fout[pos], &child);
                     }
-                    ++pos;
                 }
+                __syncwarp();
             }
         }
         // dense records: the whole warp, one child gene per lane, tested on the rows
