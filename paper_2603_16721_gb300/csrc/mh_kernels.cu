@@ -242,6 +242,9 @@ struct Batch {
     u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words; expansion: staged
     u64 ns[kMaxWords];              // child masks and their (record, word) of one item per lane
     int cx[33];                     // expansion: exclusive prefix sum of the lanes' child counts
+    u16 po[kBatch][kMaxH - 1];      // leaves: ascending original indices of each record's prefix
+    u64 qm[64];                     // leaves: queue of items to score (non-empty leaves mask,
+    u32 qjw[64];                    //   record << 16 | column word)
 };
 
 // Lane j takes record first + j*stride (if < count) into the warp scratch with
@@ -250,7 +253,7 @@ struct Batch {
 // samples, or all of them with `all_children`) and the bit mask of dense records.
 __device__ __forceinline__ int batch_prepare(const Rec *Fin, u64 first, u64 stride, u32 count, int L, int hi_bound,
                                              bool all_children, Batch &b, int lane, unsigned &dense_mask,
-                                             u64 &visited)
+                                             u64 &visited, const u16 *orig = nullptr)
 {
     const u64 i = first + (u64)lane * stride;
     const bool valid = i < count;
@@ -262,6 +265,17 @@ __device__ __forceinline__ int batch_prepare(const Rec *Fin, u64 first, u64 stri
         ky = b.r[lane].ky;
         kn = b.r[lane].kn;
         if (hi >= lo) visited += (u64)(hi - lo + 1);
+        if (orig) {  // ascending original indices of the prefix genes (leaf keys)
+            for (int q = 0; q < L; ++q) {
+                const u16 v = orig[prefix_gene(b.r[lane].p, q)];
+                int k = q - 1;
+                while (k >= 0 && b.po[lane][k] > v) {
+                    b.po[lane][k + 1] = b.po[lane][k];
+                    --k;
+                }
+                b.po[lane][k + 1] = v;
+            }
+        }
     }
     b.lo[lane] = lo;
     b.hi[lane] = hi;
@@ -387,35 +401,19 @@ __device__ __forceinline__ void child_from_rows(const Cohort &c, const Batch &b,
     out.kn = sat16(kn);
 }
 
-// Ascending original indices of the L genes of a prefix.
-__device__ __forceinline__ void prefix_orig(const Cohort &c, const Prefix &p, int L, int (&po)[kMaxH - 1])
+// Scores the non-empty leaves m of sparse record j of the batch at column word
+// wi: TP / FP from bit-sliced sums of the record's sample columns.  Returns the
+// number scored.
+__device__ __forceinline__ int score_item(const Cohort &c, const Solve &s, const Batch &b, int j, int wi, u64 m,
+                                          int L, u64 thr, Key &best)
 {
-#pragma unroll
-    for (int i = 0; i < kMaxH - 1; ++i) po[i] = 0;
-    for (int i = 0; i < L; ++i) {
-        const int v = c.orig[prefix_gene(p, i)];
-        int j = i - 1;
-        while (j >= 0 && po[j < 0 ? 0 : j] > v) {
-            po[j + 1] = po[j];
-            --j;
-        }
-        po[j + 1] = v;
-    }
-}
-
-// Scores the non-empty leaves m of sparse record r at column word wi: TP / FP
-// from bit-sliced sums of the record's sample columns.  Returns the number scored.
-__device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Rec &r, int wi, u64 m, int L, u64 thr,
-                                       Key &best)
-{
+    const Rec &r = b.r[j];
     const int ky = r.ky, kn = r.kn;
     const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
     u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
     u64 fpl[kPlanesN] = {0, 0, 0, 0};
     for (int q = 0; q < ky; ++q) planes_add(tpl, c.CT[(size_t)r.ids[q] * c.GW + wi], pt);
     for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)r.ids[kListT + q] * c.GW + wi], pn);
-    int po[kMaxH - 1];
-    bool have_po = false;
     int n = 0;
     while (m) {
         const int bt = __ffsll((long long)m) - 1;
@@ -425,10 +423,9 @@ __device__ __noinline__ int score_word(const Cohort &c, const Solve &s, const Re
         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
         ++n;
         if (s1 < best.s || s1 < thr) continue;
-        if (!have_po) {
-            prefix_orig(c, r.p, L, po);
-            have_po = true;
-        }
+        int po[kMaxH - 1];
+#pragma unroll
+        for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[j][q] : 0;
         const Key k = leaf_key(s1, po, L, c.orig[wi * 64 + bt]);
         if (key_better(k, best)) best = k;
     }
@@ -673,13 +670,17 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
     const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
-        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited);
+        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited,
+                                        c.orig);
         prefixes += (u64)(gw + (kb + lane) * nw < count);
         // only candidates at least as good as the best score known to exist can win
         u64 thr = 0;
         if (lane == 0) thr = *(volatile u64 *)s.best_hint;
         thr = warp_max_u64(thr > best.s ? thr : best.s);
-        int j = 0;
+        // items whose record can still reach the threshold queue up and are scored
+        // 32 at a time, one per lane, whichever lane found them
+        int j = 0, qn = 0;
+        const unsigned lt = (1u << lane) - 1u;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
             u64 m[kIlp], rw[kIlp];
@@ -688,13 +689,40 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
             for (int u = 0; u < kIlp; ++u) {
                 alive += (u64)__popcll(m[u]);
                 words += (u64)ky[u];
-                if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
-                    const Rec &r = b.r[jj[u]];
-                    scored += (u64)score_word(c, s, r, wi[u], m[u], L, thr, best);
-                    words += (u64)(ky[u] + r.kn);
+                const bool need = m[u] && s.a_num * (u64)ky[u] + nn_term >= thr;
+                const unsigned bal = __ballot_sync(kFull, need);
+                if (need) {
+                    const int slot = qn + __popc(bal & lt);
+                    b.qm[slot] = m[u];
+                    b.qjw[slot] = ((u32)jj[u] << 16) | (u32)wi[u];
+                }
+                qn += __popc(bal);
+                if (qn >= 32) {
+                    __syncwarp();
+                    {
+                        const u32 jw = b.qjw[lane];
+                        const int jr = (int)(jw >> 16);
+                        scored += (u64)score_item(c, s, b, jr, (int)(jw & 0xffffu), b.qm[lane], L, thr, best);
+                        words += (u64)(b.r[jr].ky + b.r[jr].kn);
+                    }
+                    __syncwarp();
+                    if (lane < qn - 32) {
+                        b.qm[lane] = b.qm[32 + lane];
+                        b.qjw[lane] = b.qjw[32 + lane];
+                    }
+                    qn -= 32;
+                    __syncwarp();
                 }
             }
         }
+        __syncwarp();
+        if (lane < qn) {
+            const u32 jw = b.qjw[lane];
+            const int jr = (int)(jw >> 16);
+            scored += (u64)score_item(c, s, b, jr, (int)(jw & 0xffffu), b.qm[lane], L, thr, best);
+            words += (u64)(b.r[jr].ky + b.r[jr].kn);
+        }
+        __syncwarp();
         // dense records: the whole warp, one leaf gene per lane, tested and scored
         // on the rows (popcounts over the prefix's non-zero words only)
         while (dense) {
@@ -707,7 +735,8 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
             dense_setup(c, s, p, L, b, by, bn, lane);
             if (lane == 0) ++dense_n;
             int po[kMaxH - 1];
-            prefix_orig(c, p, L, po);
+#pragma unroll
+            for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[jd][q] : 0;
             const bool score = s.a_num * (u64)ky + nn_term >= thr;
             const int nzy = __popc(by);
             for (int gb = lo; gb <= hi; gb += 32) {
