@@ -200,27 +200,41 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
     return MH_OK;
 }
 
-// Grows the frontier of depth l to hold at least n entries (within the budget).
+// Grows the frontier of depth l to at least n records per shard (within the budget).
 int ensure_frontier(mh_handle *H, int l, u64 n)
 {
     if (n <= H->cap[l]) return MH_OK;
-    u64 want = std::max<u64>(n + n / 4, 1u << 16);
-    if (want > 0xffffffffull) want = 0xffffffffull;
-    const int64_t old_bytes = (int64_t)H->cap[l] * (int64_t)sizeof(Rec);
-    const int64_t new_bytes = (int64_t)want * (int64_t)sizeof(Rec);
-    if ((size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget() || n > 0xffffffffull)
-        return fail(MH_ENOMEM, "depth-%d frontier needs %llu entries (%.1f GB), above the frontier budget", l,
-                    (unsigned long long)n, (double)n * sizeof(Rec) / 1e9);
+    u64 want = std::max<u64>(n + n / 4, 1u << 11);
+    if (want > 0xffffffffull / kShards) want = 0xffffffffull / kShards;
+    const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)sizeof(Rec);
+    const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
+    if ((size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget() || n > want)
+        return fail(MH_ENOMEM, "depth-%d frontier needs %llu records per shard (%.1f GB), above the frontier budget",
+                    l, (unsigned long long)n, (double)n * kShards * sizeof(Rec) / 1e9);
     MH_CUDA(cudaStreamSynchronize(H->stream));
     cudaFree(H->dF[l]);
     H->dF[l] = nullptr;
     H->frontier_bytes -= old_bytes;
     H->device_bytes -= old_bytes;
     H->cap[l] = 0;
-    int rc = dalloc(&H->dF[l], (size_t)want, &H->device_bytes);
+    int rc = dalloc(&H->dF[l], (size_t)want * kShards, &H->device_bytes);
     if (rc) return rc;
     H->cap[l] = (u32)want;
     H->frontier_bytes += new_bytes;
+    return MH_OK;
+}
+
+// After an overflow: grows every depth whose busiest shard outgrew its region.
+int grow_overflowed(mh_handle *H, int h, const u32 *hc)
+{
+    for (int l = 1; l < h; ++l) {
+        u32 mx = 0;
+        for (int i = 0; i < kShards; ++i) mx = std::max(mx, hc[shard_slot(l, i)]);
+        if (mx > H->cap[l]) {
+            const int rc = ensure_frontier(H, l, mx);
+            if (rc) return rc;
+        }
+    }
     return MH_OK;
 }
 
@@ -235,11 +249,11 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)kCountStride, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dCounts, (size_t)kCountWords, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms) : 0;
-        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountStride)));
+        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountWords)));
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
         cudaFree(H->dCnt);
@@ -258,7 +272,8 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dSlots, (size_t)slots, &H->device_bytes))) return rc;
         H->ws_slots = slots;
     }
-    if ((rc = ensure_frontier(H, 1, (u64)H->G))) return rc;
+    // depth 1: a warp appends its 32 genes to one of kShards regions
+    if ((rc = ensure_frontier(H, 1, (u64)(H->G + kShards - 1) / kShards + 64))) return rc;
     for (int l = 2; l < h; ++l)
         if ((rc = ensure_frontier(H, l, 1))) return rc;
     return MH_OK;
@@ -417,7 +432,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
             MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, H->pgrid, st));
             ++launches;
             MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
-            MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountStride,
+            MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountWords,
                                     cudaMemcpyDeviceToHost, st));
             MH_CUDA(cudaStreamSynchronize(st));
             const int *hs = H->hState;
@@ -428,14 +443,12 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 return fail(MH_ETIMEOUT, "a grid barrier of the persistent solve timed out in round %d", rounds_done);
             }
             if (hs[3]) {
-                for (int l = 1; l < h; ++l) {
-                    if (hc[l] > H->cap[l] && (rc = ensure_frontier(H, l, hc[l]))) {
-                        destroy_events();
-                        return rc;
-                    }
+                if ((rc = grow_overflowed(H, h, hc))) {
+                    destroy_events();
+                    return rc;
                 }
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
-                MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st));
+                MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
                 continue;
             }
@@ -446,7 +459,12 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     // the round index and the done / overflow flags on the device.  After a batch
     // the host reads the state; an overflowed frontier is grown and its round rerun.
     int batch = 4;
+    Frontiers fl;
     while (!done) {
+        for (int l = 0; l < kMaxH; ++l) {
+            fl.F[l] = H->dF[l];
+            fl.cap[l] = H->cap[l];
+        }
         const size_t first_ev = round_ev.size();
         const int n = std::min(batch, max_rounds - rounds_done);
         for (int b = 0; b < n; ++b) {
@@ -456,17 +474,16 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 e.valid = true;
                 MH_CUDA(cudaEventRecord(e.ev[0], st));
             }
-            launch_level1(c, s, H->dF[1], counts + 1, H->cap[1], st);
+            launch_level1(c, s, fl, counts, st);
             ++launches;
             if (opts->time_kernels) MH_CUDA(cudaEventRecord(e.ev[1], st));
             for (int l = 2; l <= h - 1; ++l) {
-                launch_expand(c, s, l, H->dF[l - 1], counts + (l - 1), H->cap[l - 1], H->dF[l], counts + l,
-                              H->cap[l], grid, st);
+                launch_expand(c, s, l, fl, counts, grid, st);
                 ++launches;
             }
             if (opts->time_kernels) MH_CUDA(cudaEventRecord(e.ev[2], st));
             if (h >= 2) {
-                launch_leaf(c, s, H->dF[h - 1], counts + (h - 1), H->cap[h - 1], grid, st);
+                launch_leaf(c, s, fl, counts, grid, st);
                 ++launches;
                 ++leaf_launches;
             }
@@ -480,7 +497,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         }
         MH_CUDA(cudaGetLastError());
         MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
-        MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountStride, cudaMemcpyDeviceToHost,
+        MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost,
                                 st));
         MH_CUDA(cudaStreamSynchronize(st));
         const int *hs = H->hState;
@@ -490,14 +507,12 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
             // a frontier of round rounds_done did not fit: grow it, forget the round's
             // partial counters and frontier sizes, and run the round again
             for (size_t e = first_ev; e < round_ev.size(); ++e) round_ev[e].valid = false;
-            for (int l = 1; l < h; ++l) {
-                if (hc[l] > H->cap[l] && (rc = ensure_frontier(H, l, hc[l]))) {
-                    destroy_events();
-                    return rc;
-                }
+            if ((rc = grow_overflowed(H, h, hc))) {
+                destroy_events();
+                return rc;
             }
             MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
-            MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st));
+            MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st));
             MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
             continue;
         }

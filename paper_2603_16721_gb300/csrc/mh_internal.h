@@ -21,6 +21,14 @@ constexpr int kMaxWarpsPerBlock = 32;
 constexpr int kErrTimeout = 4;     // same value as MH_ETIMEOUT
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kCountStride = 16;   // u32 slots per counter array (>= kMaxH + 1)
+// Frontier appends are spread over kShards counters, each in its own 128-byte
+// line, so that thousands of warps do not serialise on one atomic: depth l,
+// shard i counts the records of region i of the depth-l frontier
+// (counts[(l * kShards + i) * kShardStride]).
+constexpr int kShards = 32;
+constexpr int kShardStride = 32;
+constexpr int kCountWords = kMaxH * kShards * kShardStride;
+__host__ __device__ constexpr int shard_slot(int level, int shard) { return (level * kShards + shard) * kShardStride; }
 
 // Device view of one cohort, genes in search order (most sparse first, §III-C).
 struct Cohort {
@@ -97,7 +105,7 @@ enum {
     kWorkCount = 20
 };
 
-// Frontier buffers of the persistent solve (depth l at index l).
+// Frontier buffers (depth l at index l): kShards regions of cap[l] records each.
 struct Frontiers {
     Rec *F[kMaxH];
     u32 cap[kMaxH];
@@ -112,13 +120,13 @@ struct GridSync {
 void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
 // Rounds run on the device: every kernel reads the round index and the done /
 // overflow flags from Solve::state, so the host can enqueue many rounds ahead.
+// counts: kCountWords u32 (see shard_slot); cap values are per shard.
 void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts,
                        cudaStream_t st);
-void launch_level1(const Cohort &c, const Solve &s, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st);
-void launch_expand(const Cohort &c, const Solve &s, int level, const Rec *Fin, const u32 *nin, u32 cap_in,
-                   Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st);
-void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin, u32 cap_in, int grid,
-                 cudaStream_t st);
+void launch_level1(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, cudaStream_t st);
+void launch_expand(const Cohort &c, const Solve &s, int level, const Frontiers &f, u32 *counts, int grid,
+                   cudaStream_t st);
+void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, int grid, cudaStream_t st);
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
 
 // Persistent solve: all rounds in one cooperative launch of `grid` blocks

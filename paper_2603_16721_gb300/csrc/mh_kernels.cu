@@ -156,13 +156,6 @@ __device__ void block_commit_best(Key best, Key *slots)
     }
 }
 
-__device__ __forceinline__ void count_level(const Solve &s, int round, int level, u64 visited, u64 pruned)
-{
-    u64 *c = s.cnt + ((size_t)round * s.h + (level - 1)) * 2;
-    if (visited) atomicAdd(c, visited);
-    if (pruned) atomicAdd(c + 1, pruned);
-}
-
 __device__ __forceinline__ u64 range_word(int wi, int lo, int hi)
 {
     u64 m = ~0ull;
@@ -207,13 +200,49 @@ enum { kStK = 0, kStDone = 1, kStError = 2, kStOverflow = 3, kStRound = 4, kStMa
 
 __device__ __forceinline__ bool halted(const Solve &s) { return s.state[kStDone] | s.state[kStOverflow]; }
 
-// A consumer whose input frontier did not fit raises the overflow flag; the host
-// grows the frontier and runs the round again.
-__device__ __forceinline__ bool input_overflowed(const Solve &s, u32 count, u32 cap)
+// Sharded frontier of one depth as a consumer sees it: lane i reads the record
+// count of shard i; the exclusive prefix sums map a record index to its shard.
+// Returns the number of records, or -1 if a shard overflowed its region (then
+// the round must be rerun with a larger frontier).
+__device__ __forceinline__ long long front_open(const u32 *counts, int level, u32 cap_s, int *soff, int lane)
 {
-    if (count <= cap) return false;
-    if (threadIdx.x == 0) s.state[kStOverflow] = 1;
-    return true;
+    const u32 n = __ldcg(&counts[shard_slot(level, lane)]);
+    if (__any_sync(kFull, n > cap_s)) return -1;
+    const int incl = warp_incl_scan((int)n, lane);
+    soff[lane] = incl - (int)n;
+    if (lane == 31) soff[32] = incl;
+    __syncwarp();
+    return __shfl_sync(kFull, incl, 31);
+}
+
+// Address of record i of a sharded frontier (soff from front_open).
+__device__ __forceinline__ const Rec *front_rec(const Rec *F, u32 cap_s, const int *soff, u32 i)
+{
+    int lo = 0, hi = kShards - 1;  // last shard with soff <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((u32)soff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return F + (size_t)lo * cap_s + (i - (u32)soff[lo]);
+}
+
+// The shard a warp appends to: neighbouring warps use different counters.
+__device__ __forceinline__ int my_shard()
+{
+    return (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kShards);
+}
+
+// Block-wide accumulation of counters: warps add into shared memory, then one
+// global atomic per counter and block (not per warp) at the end of a phase.
+constexpr int kAccN = 8;
+__device__ __forceinline__ void acc_begin(u64 *acc)
+{
+    if (threadIdx.x < kAccN) acc[threadIdx.x] = 0;
+    __syncthreads();
+}
+__device__ __forceinline__ void acc_add(u64 *acc, int i, u64 v)
+{
+    if (v) atomicAdd(&acc[i], v);
 }
 
 __device__ __forceinline__ void copy_rec(Rec *dst, const Rec *src)
@@ -239,27 +268,26 @@ struct Batch {
     Rec r[kBatch];
     int lo[kBatch], hi[kBatch];     // child range (0-based, inclusive); lo > hi when empty
     int off[kBatch + 1];            // exclusive prefix sum of the sparse records' column words
+    int soff[kShards + 1];          // input frontier: exclusive prefix sums of the shard counts
     u64 ys[kMaxWords];              // dense path: y_{l-1} and n_{l-1} words; expansion: staged
     u64 ns[kMaxWords];              // child masks and their (record, word) of one item per lane
     int cx[33];                     // expansion: exclusive prefix sum of the lanes' child counts
     u16 po[kBatch][kMaxH - 1];      // leaves: ascending original indices of each record's prefix
-    u64 qm[64];                     // leaves: queue of items to score (non-empty leaves mask,
-    u32 qjw[64];                    //   record << 16 | column word)
 };
 
 // Lane j takes record first + j*stride (if < count) into the warp scratch with
 // its child range [last gene + 1, hi_bound]; counts its children as visited.
 // Returns the number of column words of the batch's sparse records (those with
 // samples, or all of them with `all_children`) and the bit mask of dense records.
-__device__ __forceinline__ int batch_prepare(const Rec *Fin, u64 first, u64 stride, u32 count, int L, int hi_bound,
-                                             bool all_children, Batch &b, int lane, unsigned &dense_mask,
-                                             u64 &visited, const u16 *orig = nullptr)
+__device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 cap_s, u64 first, u64 stride, u32 count, int L,
+                                             int hi_bound, bool all_children, Batch &b, int lane,
+                                             unsigned &dense_mask, u64 &visited, const u16 *orig = nullptr)
 {
     const u64 i = first + (u64)lane * stride;
     const bool valid = i < count;
     int lo = 1, hi = 0, ky = 0, kn = 0;
     if (valid) {
-        load_rec(&b.r[lane], &Fin[i]);
+        load_rec(&b.r[lane], front_rec(Fin, cap_s, b.soff, (u32)i));
         lo = prefix_gene(b.r[lane].p, L - 1) + 1;
         hi = hi_bound;
         ky = b.r[lane].ky;
@@ -344,13 +372,14 @@ __device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, i
     for (int u = 0; u < kIlp; ++u) m[u] &= rw[u];
 }
 
-// Reserves n consecutive frontier slots for each lane with one atomic per warp.
-__device__ __forceinline__ u32 warp_reserve(int n, u32 *nout, int lane)
+// Reserves n consecutive slots of the warp's shard for each lane with one atomic
+// per warp; returns the lane's first slot within the shard.
+__device__ __forceinline__ u32 warp_reserve(int n, u32 *shard_count, int lane)
 {
     const int incl = warp_incl_scan(n, lane);
     const int total = __shfl_sync(kFull, incl, 31);
     u32 base = 0;
-    if (total && lane == 0) base = atomicAdd(nout, (u32)total);
+    if (total && lane == 0) base = atomicAdd(shard_count, (u32)total);
     base = __shfl_sync(kFull, base, 0);
     return base + (u32)(incl - n);
 }
@@ -481,12 +510,16 @@ __device__ void rescore_candidates(const Cohort &c, const Solve &s)
 // the leaves and are scored here (the block's best goes to its slot); otherwise
 // the non-empty ones (all of them with pruning off) become depth-1 records.
 // Every thread of the block must call it.
-__device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1, u32 *n1, u32 cap1)
+__device__ void phase_level1(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts)
 {
+    __shared__ u64 acc[kAccN];
     const int lane = threadIdx.x & 31;
     const int h = s.h;
+    acc_begin(acc);
     if (h > 1) rescore_candidates(c, s);
     const int last = c.G - h;  // 0-based inclusive bound of depth 1
+    u32 *my_count = counts + shard_slot(1, my_shard());
+    Rec *out = f.F[1] + (size_t)my_shard() * f.cap[1];
     Key best = key_empty();
     for (int base = blockIdx.x * blockDim.x; base < c.G; base += gridDim.x * blockDim.x) {
         const int g = base + threadIdx.x;
@@ -498,7 +531,10 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1
         }
         const bool nonempty = ky > 0;
         const unsigned bin = __ballot_sync(kFull, in), bne = __ballot_sync(kFull, nonempty);
-        if (lane == 0) count_level(s, round, 1, (u64)__popc(bin), (u64)__popc(bin & ~bne));
+        if (lane == 0) {
+            acc_add(acc, 0, (u64)__popc(bin));
+            acc_add(acc, 1, (u64)__popc(bin & ~bne));
+        }
         if (h == 1) {
             if (nonempty) {
                 int fp = 0;
@@ -512,8 +548,8 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1
             continue;
         }
         const bool keep = s.prune ? in : nonempty;
-        const u32 pos = warp_reserve(keep ? 1 : 0, n1, lane);
-        if (!keep || pos >= cap1) continue;
+        const u32 pos = warp_reserve(keep ? 1 : 0, my_count, lane);
+        if (!keep || pos >= f.cap[1]) continue;
         Rec r;
         r.p.w0 = (u64)g;
         r.p.w1 = 0;
@@ -533,52 +569,76 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, Rec *F1
         }
         r.ky = sat16(ky);
         r.kn = sat16(kn);
-        copy_rec(&F1[pos], &r);
+        copy_rec(&out[pos], &r);
     }
     if (h == 1) block_commit_best(best, s.slots);
+    __syncthreads();
+    if (threadIdx.x < 2 && acc[threadIdx.x])
+        atomicAdd(s.cnt + ((size_t)round * h) * 2 + threadIdx.x, acc[threadIdx.x]);
 }
 
-// Depths 2 .. h-1: the non-empty children (all children with pruning off) of
-// every depth-(level-1) record become depth-level records.
-// Per-warp cycle statistics of a phase (k = 0 expand, 1 leaf), for diagnostics.
-__device__ __forceinline__ void warp_cycles(const Solve &s, int k, long long t0, int lane)
+// Per-warp cycle statistics of a phase (k = 0 expand, 1 leaf), for diagnostics,
+// into the block accumulator slots 5 (sum), 6 (max), 7 (count).
+__device__ __forceinline__ void warp_cycles(u64 *acc, long long t0, int lane)
 {
     if (lane == 0) {
         const u64 dt = (u64)(clock64() - t0);
-        atomicAdd(s.work + kWorkWarpSum + k, dt);
-        atomicMax(s.work + kWorkWarpMax + k, dt);
-        atomicAdd(s.work + kWorkWarpN + k, 1ull);
+        atomicAdd(&acc[5], dt);
+        atomicMax(&acc[6], dt);
+        atomicAdd(&acc[7], 1ull);
     }
 }
 
-__device__ void phase_expand(const Cohort &c, const Solve &s, int round, int level, const Rec *Fin, u32 count,
-                             Rec *Fout, u32 *nout, u32 cap, Batch &b)
+__device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc, int k)
 {
+    if (threadIdx.x == 5 && acc[5]) atomicAdd(s.work + kWorkWarpSum + k, acc[5]);
+    if (threadIdx.x == 6 && acc[6]) atomicMax(s.work + kWorkWarpMax + k, acc[6]);
+    if (threadIdx.x == 7 && acc[7]) atomicAdd(s.work + kWorkWarpN + k, acc[7]);
+}
+
+// Depths 2 .. h-1: the non-empty children (all children with pruning off) of
+// every depth-(level-1) record become depth-level records.  Every thread of the
+// block must call it; returns false (for every thread) if the input frontier
+// overflowed.
+__device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int level, const Frontiers &f, u32 *counts,
+                             Batch &b)
+{
+    __shared__ u64 acc[kAccN];
+    __shared__ int overflow;
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = level - 1;
+    if (threadIdx.x == 0) overflow = 0;
+    acc_begin(acc);
+    const long long n_in = front_open(counts, level - 1, f.cap[level - 1], b.soff, lane);
+    if (n_in < 0 && lane == 0) overflow = 1;
+    __syncthreads();
+    if (overflow) return false;
+    const u32 count = (u32)n_in;
+    const Rec *Fin = f.F[level - 1];
+    const u32 cap_in = f.cap[level - 1];
+    const u32 cap = f.cap[level];
+    u32 *my_count = counts + shard_slot(level, my_shard());
+    Rec *Fout = f.F[level] + (size_t)my_shard() * cap;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
     const bool all_children = s.prune != 0;
     const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
-        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, hi_bound, all_children, b, lane, dense,
-                                        visited);
+        const int total = batch_prepare(Fin, cap_in, gw + kb * nw, nw, count, L, hi_bound, all_children, b, lane,
+                                        dense, visited);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
             u64 m[kIlp], rw[kIlp];
             sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
-            int nchild = 0;
 #pragma unroll
             for (int u = 0; u < kIlp; ++u) {
                 alive += (u64)__popcll(m[u]);
                 if (all_children) m[u] = rw[u];
-                nchild += __popcll(m[u]);
             }
-            (void)nchild;
             // spread the children of each item round over all lanes: lane i builds
             // children i, i+32, ... of the warp, whichever lane's item they came from
 #pragma unroll
@@ -592,7 +652,7 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
                 b.cx[lane] = incl - n;
                 if (lane == 31) b.cx[32] = incl;
                 u32 base = 0;
-                if (lane == 0) base = atomicAdd(nout, (u32)tot);
+                if (lane == 0) base = atomicAdd(my_count, (u32)tot);
                 base = __shfl_sync(kFull, base, 0);
                 __syncwarp();
                 for (int k = lane; k < tot; k += 32) {
@@ -636,7 +696,7 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
                 }
                 alive += (u64)(kyc > 0);
                 const bool emit = g <= hi && (all_children || kyc > 0);
-                const u32 pos = warp_reserve(emit ? 1 : 0, nout, lane);
+                const u32 pos = warp_reserve(emit ? 1 : 0, my_count, lane);
                 if (emit && pos < cap) {
                     Rec child;
                     child.pad[0] = child.pad[1] = child.pad[2] = 0;
@@ -649,8 +709,16 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
-    if (lane == 0) count_level(s, round, level, visited, visited - alive);
-    warp_cycles(s, 0, t0, lane);
+    if (lane == 0) {
+        acc_add(acc, 0, visited);
+        acc_add(acc, 1, visited - alive);
+    }
+    warp_cycles(acc, t0, lane);
+    __syncthreads();
+    if (threadIdx.x < 2 && acc[threadIdx.x])
+        atomicAdd(s.cnt + ((size_t)round * s.h + (level - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
+    warp_cycles_flush(s, acc, 0);
+    return true;
 }
 
 // Depth h (leaves): every non-empty leaf is a candidate with score
@@ -658,29 +726,37 @@ __device__ void phase_expand(const Cohort &c, const Solve &s, int round, int lev
 // goes to the block's slot.  A record whose bound a_num * |y| + a_den * Nn is
 // below the best score known to exist cannot hold the round's winner, so its
 // leaves are tested (and counted) but not scored.  Every thread of the block
-// must call it.
-__device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec *Fin, u32 count, Batch &b)
+// must call it; returns false (for every thread) if the input frontier overflowed.
+__device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts, Batch &b)
 {
+    __shared__ u64 acc[kAccN];
+    __shared__ int overflow;
     const long long t0 = clock64();
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const int h = s.h, L = h - 1;
+    if (threadIdx.x == 0) overflow = 0;
+    acc_begin(acc);
+    const long long n_in = front_open(counts, h - 1, f.cap[h - 1], b.soff, lane);
+    if (n_in < 0 && lane == 0) overflow = 1;
+    __syncthreads();
+    if (overflow) return false;
+    const u32 count = (u32)n_in;
+    const Rec *Fin = f.F[h - 1];
+    const u32 cap_in = f.cap[h - 1];
+    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const u64 nn_term = s.a_den * (u64)c.Nn + 1;
     const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
-        const int total = batch_prepare(Fin, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense, visited,
-                                        c.orig);
+        const int total = batch_prepare(Fin, cap_in, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense,
+                                        visited, c.orig);
         prefixes += (u64)(gw + (kb + lane) * nw < count);
         // only candidates at least as good as the best score known to exist can win
         u64 thr = 0;
         if (lane == 0) thr = *(volatile u64 *)s.best_hint;
         thr = warp_max_u64(thr > best.s ? thr : best.s);
-        // items whose record can still reach the threshold queue up and are scored
-        // 32 at a time, one per lane, whichever lane found them
-        int j = 0, qn = 0;
-        const unsigned lt = (1u << lane) - 1u;
+        int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
             u64 m[kIlp], rw[kIlp];
@@ -689,40 +765,12 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
             for (int u = 0; u < kIlp; ++u) {
                 alive += (u64)__popcll(m[u]);
                 words += (u64)ky[u];
-                const bool need = m[u] && s.a_num * (u64)ky[u] + nn_term >= thr;
-                const unsigned bal = __ballot_sync(kFull, need);
-                if (need) {
-                    const int slot = qn + __popc(bal & lt);
-                    b.qm[slot] = m[u];
-                    b.qjw[slot] = ((u32)jj[u] << 16) | (u32)wi[u];
-                }
-                qn += __popc(bal);
-                if (qn >= 32) {
-                    __syncwarp();
-                    {
-                        const u32 jw = b.qjw[lane];
-                        const int jr = (int)(jw >> 16);
-                        scored += (u64)score_item(c, s, b, jr, (int)(jw & 0xffffu), b.qm[lane], L, thr, best);
-                        words += (u64)(b.r[jr].ky + b.r[jr].kn);
-                    }
-                    __syncwarp();
-                    if (lane < qn - 32) {
-                        b.qm[lane] = b.qm[32 + lane];
-                        b.qjw[lane] = b.qjw[32 + lane];
-                    }
-                    qn -= 32;
-                    __syncwarp();
+                if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
+                    scored += (u64)score_item(c, s, b, jj[u], wi[u], m[u], L, thr, best);
+                    words += (u64)(ky[u] + b.r[jj[u]].kn);
                 }
             }
         }
-        __syncwarp();
-        if (lane < qn) {
-            const u32 jw = b.qjw[lane];
-            const int jr = (int)(jw >> 16);
-            scored += (u64)score_item(c, s, b, jr, (int)(jw & 0xffffu), b.qm[lane], L, thr, best);
-            words += (u64)(b.r[jr].ky + b.r[jr].kn);
-        }
-        __syncwarp();
         // dense records: the whole warp, one leaf gene per lane, tested and scored
         // on the rows (popcounts over the prefix's non-zero words only)
         while (dense) {
@@ -776,21 +824,31 @@ __device__ void phase_leaf(const Cohort &c, const Solve &s, int round, const Rec
     prefixes = warp_sum_u64(prefixes);
     scored = warp_sum_u64(scored);
     if (lane == 0) {
-        count_level(s, round, h, visited, visited - alive);
-        if (words) atomicAdd(s.work + kWorkColWords, words);
-        if (prefixes) atomicAdd(s.work + kWorkPrefixes, prefixes);
-        if (scored) atomicAdd(s.work + kWorkScored, scored);
-        if (dense_n) atomicAdd(s.work + kWorkDense, dense_n);
+        acc_add(acc, 0, visited);
+        acc_add(acc, 1, visited - alive);
+        acc_add(acc, 2, words);
+        acc_add(acc, 3, prefixes);
+        acc_add(acc, 4, scored);
     }
-    warp_cycles(s, 1, t0, lane);
+    warp_cycles(acc, t0, lane);
+    // dense records counted through the block's slot 7 is taken: use an atomic per warp (rare)
+    if (lane == 0 && dense_n) atomicAdd(s.work + kWorkDense, dense_n);
+    __syncthreads();
+    if (threadIdx.x < 2 && acc[threadIdx.x])
+        atomicAdd(s.cnt + ((size_t)round * h + (h - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
+    if (threadIdx.x == 2 && acc[2]) atomicAdd(s.work + kWorkColWords, acc[2]);
+    if (threadIdx.x == 3 && acc[3]) atomicAdd(s.work + kWorkPrefixes, acc[3]);
+    if (threadIdx.x == 4 && acc[4]) atomicAdd(s.work + kWorkScored, acc[4]);
+    warp_cycles_flush(s, acc, 1);
     block_commit_best(best, s.slots);
+    return true;
 }
 
 // End of a round, by one block: reduce the per-block bests, record the winner
 // with its TP / FP, clear the tumors it covers (DelCols), keep the best other
-// candidates for the next round's threshold, reset the frontier sizes and advance
-// the round; raise the done flag when nothing was found, every tumor is covered or
-// the round limit is reached.  Every thread of the block must call it.
+// candidates for the next round's threshold, reset the frontier counters and
+// advance the round; raise the done flag when nothing was found, every tumor is
+// covered or the round limit is reached.  Every thread of the block must call it.
 __device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int nslots)
 {
     __shared__ Key wbest[kMaxWarpsPerBlock];
@@ -817,7 +875,7 @@ __device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int
         if (m.s != 0 && mine.s == m.s && mine.t0 == m.t0 && mine.t1 == m.t1 && mine.t2 == m.t2) mine = key_empty();
         if (r == 0 && lane == 0) wbest[warp] = m;
     }
-    if (threadIdx.x < kCountStride) counts[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kMaxH * kShards; i += blockDim.x) counts[i * kShardStride] = 0;
     __syncthreads();
     if (warp == 0) {
         best = lane < nwarps ? wbest[lane] : key_empty();
@@ -903,27 +961,26 @@ __global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
     if (w < kStateWords) s.state[w] = w == kStMaxRounds ? max_rounds : 0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Rec *F1, u32 *n1, u32 cap1)
+__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Frontiers f, u32 *counts)
 {
     if (halted(s)) return;
-    phase_level1(c, s, s.state[kStRound], F1, n1, cap1);
+    phase_level1(c, s, s.state[kStRound], f, counts);
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, const Rec *Fin,
-                                                        const u32 *nin, u32 cap_in, Rec *Fout, u32 *nout, u32 cap)
+__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
-    const u32 count = *nin;
-    if (input_overflowed(s, count, cap_in)) return;
-    phase_expand(c, s, s.state[kStRound], level, Fin, count, Fout, nout, cap, scratch[threadIdx.x >> 5]);
+    if (!phase_expand(c, s, s.state[kStRound], level, f, counts, scratch[threadIdx.x >> 5]) && threadIdx.x == 0)
+        s.state[kStOverflow] = 1;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, const Rec *Fin, const u32 *nin, u32 cap_in)
+__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
-    if (halted(s) || input_overflowed(s, *nin, cap_in)) return;
-    phase_leaf(c, s, s.state[kStRound], Fin, *nin, scratch[threadIdx.x >> 5]);
+    if (halted(s)) return;
+    if (!phase_leaf(c, s, s.state[kStRound], f, counts, scratch[threadIdx.x >> 5]) && threadIdx.x == 0)
+        s.state[kStOverflow] = 1;
 }
 
 __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *counts)
@@ -936,7 +993,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *c
 // Persistent solve: every round of the greedy loop in one cooperative launch.
 
 // Grid barrier with a bounded wait: a block that waits longer than about two
-// seconds records MH_ETIMEOUT in the state and returns false instead of hanging.
+// seconds records a timeout in the state and returns false instead of hanging.
 __device__ __forceinline__ bool grid_sync(GridSync *g, int *state)
 {
     __shared__ int ok;
@@ -996,35 +1053,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Fronti
         __syncthreads();
         if (stop) break;
         const int round = *(volatile int *)&s.state[kStRound];
-        phase_level1(c, s, round, f.F[1], counts + 1, f.cap[1]);
+        phase_level1(c, s, round, f, counts);
         if (!grid_sync(gsync, s.state)) return;
         lap(0);
-        bool overflow = false;
-        for (int l = 2; l <= h - 1 && !overflow; ++l) {
-            const u32 count = __ldcg(&counts[l - 1]);
-            if (count > f.cap[l - 1]) {
-                overflow = true;
-                break;
+        // every block reads the same shard counts after the same barrier, so an
+        // overflow is seen by all of them and they leave together
+        for (int l = 2; l <= h - 1; ++l) {
+            if (!phase_expand(c, s, round, l, f, counts, b)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+                return;
             }
-            phase_expand(c, s, round, l, f.F[l - 1], count, f.F[l], counts + l, f.cap[l], b);
             if (!grid_sync(gsync, s.state)) return;
         }
-        if (!overflow && h >= 2) {
-            lap(1);
-            const u32 count = __ldcg(&counts[h - 1]);
-            if (count > f.cap[h - 1]) {
-                overflow = true;
-            } else {
-                phase_leaf(c, s, round, f.F[h - 1], count, b);
-                if (!grid_sync(gsync, s.state)) return;
-                lap(2);
+        lap(1);
+        if (h >= 2) {
+            if (!phase_leaf(c, s, round, f, counts, b)) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+                return;
             }
+            if (!grid_sync(gsync, s.state)) return;
         }
-        if (overflow) {
-            // every block read the same counts after the same barrier: all leave together
-            if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
-            return;
-        }
+        lap(2);
         if (blockIdx.x == 0) phase_finalize(c, s, counts, gridDim.x);
         if (!grid_sync(gsync, s.state)) return;
         lap(3);
@@ -1053,27 +1102,26 @@ void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int 
     cudaMemsetAsync(s.cand, 0, sizeof(Key) * (size_t)kCandidates, st);
     cudaMemsetAsync(s.work, 0, sizeof(u64) * kWorkCount, st);
     cudaMemsetAsync(s.best_hint, 0, sizeof(u64), st);
-    cudaMemsetAsync(counts, 0, sizeof(u32) * kCountStride, st);
+    cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st);
     k_solve_init<<<1, 64, 0, st>>>(c, s, max_rounds);
 }
 
 int level1_grid(const Cohort &c) { return (c.G + kThreads - 1) / kThreads; }
 
-void launch_level1(const Cohort &c, const Solve &s, Rec *F1, u32 *n1, u32 cap1, cudaStream_t st)
+void launch_level1(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, cudaStream_t st)
 {
-    k_level1<<<level1_grid(c), kThreads, 0, st>>>(c, s, F1, n1, cap1);
+    k_level1<<<level1_grid(c), kThreads, 0, st>>>(c, s, f, counts);
 }
 
-void launch_expand(const Cohort &c, const Solve &s, int level, const Rec *Fin, const u32 *nin, u32 cap_in,
-                   Rec *Fout, u32 *nout, u32 cap, int grid, cudaStream_t st)
+void launch_expand(const Cohort &c, const Solve &s, int level, const Frontiers &f, u32 *counts, int grid,
+                   cudaStream_t st)
 {
-    k_expand<<<grid, kThreads, 0, st>>>(c, s, level, Fin, nin, cap_in, Fout, nout, cap);
+    k_expand<<<grid, kThreads, 0, st>>>(c, s, level, f, counts);
 }
 
-void launch_leaf(const Cohort &c, const Solve &s, const Rec *Fin, const u32 *nin, u32 cap_in, int grid,
-                 cudaStream_t st)
+void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, int grid, cudaStream_t st)
 {
-    k_leaf<<<grid, kThreads, 0, st>>>(c, s, Fin, nin, cap_in);
+    k_leaf<<<grid, kThreads, 0, st>>>(c, s, f, counts);
 }
 
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st)

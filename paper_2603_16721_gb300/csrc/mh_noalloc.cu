@@ -56,7 +56,7 @@ constexpr size_t kOffU = kOffInv + align256(sizeof(u32) * kNaMaxG);
 constexpr size_t kOffState = kOffU + align256(sizeof(u64) * kNaWTp);
 constexpr size_t kOffWork = kOffState + align256(sizeof(int) * kStateWords);
 constexpr size_t kOffCounts = kOffWork + align256(sizeof(u64) * (kWorkCount + 1));
-constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * 2 * kCountStride);
+constexpr size_t kOffRes = kOffCounts + align256(sizeof(u32) * kCountWords);
 constexpr size_t kOffCnt = kOffRes + align256(sizeof(int) * kNaRounds * (kNaMaxH + 2));
 constexpr size_t kOffSlots = kOffCnt + align256(sizeof(u64) * 2 * kNaRounds * kNaMaxH);
 constexpr size_t kOffCand = kOffSlots + align256(sizeof(Key) * kNaMaxSlots);
@@ -244,14 +244,20 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
     u32 *counts = (u32 *)(base + kOffCounts);
-    Rec *F[kMaxH] = {};
-    u32 cap[kMaxH] = {};
-    F[1] = (Rec *)(base + kOffF1);
-    cap[1] = kNaMaxG;
-    F[2] = (Rec *)(base + kOffF2);
-    cap[2] = kNaFrontierCap;
-    F[3] = (Rec *)(base + kOffF3);
-    cap[3] = kNaFrontierCap;
+    // each frontier is split into kShards equal regions (the region is the cap)
+    Frontiers fr;
+    for (int l = 0; l < kMaxH; ++l) {
+        fr.F[l] = nullptr;
+        fr.cap[l] = 0;
+    }
+    fr.F[1] = (Rec *)(base + kOffF1);
+    fr.cap[1] = kNaMaxG / kShards;
+    fr.F[2] = (Rec *)(base + kOffF2);
+    fr.cap[2] = kNaFrontierCap / kShards;
+    fr.F[3] = (Rec *)(base + kOffF3);
+    fr.cap[3] = kNaFrontierCap / kShards;
+    Rec *F[kMaxH] = {fr.F[0], fr.F[1], fr.F[2], fr.F[3]};
+    (void)F;
 
     // store: sort keys (into the depth-2 frontier area, free at this point), pack, transpose
     u32 *keys = (u32 *)F[2];
@@ -275,26 +281,19 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     while (!done) {
         const int n = batch < Nt + 1 - rounds ? batch : Nt + 1 - rounds;
         for (int b = 0; b < n; ++b) {
-            launch_level1(c, s, F[1], counts + 1, cap[1], st);
-            for (int l = 2; l <= h - 1; ++l)
-                launch_expand(c, s, l, F[l - 1], counts + (l - 1), cap[l - 1], F[l], counts + l, cap[l], grid, st);
-            if (h >= 2) launch_leaf(c, s, F[h - 1], counts + (h - 1), cap[h - 1], grid, st);
+            launch_level1(c, s, fr, counts, st);
+            for (int l = 2; l <= h - 1; ++l) launch_expand(c, s, l, fr, counts, grid, st);
+            if (h >= 2) launch_leaf(c, s, fr, counts, grid, st);
             launch_finalize(c, s, counts, st);
         }
         NA_CUDA(cudaGetLastError());
-        u32 hc[kCountStride];
         NA_CUDA(cudaMemcpyAsync(st8, s.state, sizeof st8, cudaMemcpyDeviceToHost, st));
-        NA_CUDA(cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
         NA_CUDA(cudaStreamSynchronize(st));
         rounds = st8[4];
-        if (st8[3]) {
-            for (int l = 1; l < h; ++l)
-                if (hc[l] > cap[l])
-                    return na_fail(MH_ENOMEM,
-                                   "mh_solve_noalloc: depth-%d frontier needs %u entries, the fixed scratch holds %u",
-                                   l, hc[l], cap[l]);
-            return na_fail(MH_ENOMEM, "mh_solve_noalloc: a frontier exceeds the fixed scratch");
-        }
+        if (st8[3])
+            return na_fail(MH_ENOMEM,
+                           "mh_solve_noalloc: a search frontier exceeds the fixed scratch (%u prefixes per depth)",
+                           kNaFrontierCap);
         done = st8[1] != 0 || rounds >= Nt + 1;
         batch = batch * 2 < 64 ? batch * 2 : 64;
     }
