@@ -227,7 +227,7 @@ def run_ours(args):
     H = mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn)
     mh.mh_set_stream(H, stream.cuda_stream)
     for _ in range(args.warmup):
-        mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds)
+        mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds, mode=MODES[args.mode])
     torch.cuda.synchronize()
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -242,7 +242,7 @@ def run_ours(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r = mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds, time_kernels=True)
+        r = mh.mh_solve_ex(H, H_HITS, ALPHA, max_rounds=args.max_rounds, time_kernels=True, mode=MODES[args.mode])
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -320,6 +320,7 @@ def _comb(n, k):
 
 
 H_HITS = H
+MODES = {"persistent": 0, "launches": 1}
 
 
 def main(argv=None):
@@ -330,6 +331,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--max-rounds", type=int, default=0, help="stop each solve after R rounds (profiling)")
     ap.add_argument("--kernels-only", action="store_true", help="time the solves only (profiling runs)")
+    ap.add_argument("--mode", choices=["persistent", "launches"], default="persistent",
+                    help="one persistent kernel per solve, or one launch per phase")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
