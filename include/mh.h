@@ -156,6 +156,22 @@ MH_API void mh_destroy(mh_handle *handle);
 /* Message of the last error on the calling thread ("" if none). */
 MH_API const char *mh_last_error(void);
 
+/* Batched solve: n cohorts (distinct handles, one device) with their options are
+ * solved in ONE cooperative launch.  The co-resident grid is split into n teams of
+ * blocks, team i running the greedy loop of cohort i (Algorithm 1 with P-DFS) at
+ * its own pace; the paper runs one cohort at a time, this is the GB300 batching
+ * of independent problems.  blocks: n block counts (each >= 1, summing to at most
+ * the co-resident grid), or NULL to let the autotuner choose: blocks ~ work^gamma
+ * with the per-cohort work estimated from the tumors' mutation counts, gamma
+ * picked by timing each candidate once per batch shape and cached in the file
+ * named by MH_AUTOTUNE_CACHE (default ~/.cache/mh_autotune.txt; MH_AUTOTUNE=0
+ * disables tuning).  Work runs on the first handle's stream; the call is
+ * synchronous.  out: n result pointers, each as from mh_solve_ex (solve_ms is the
+ * batch's time).  Errors: MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT; on error no
+ * result is returned. */
+MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n, const int32_t *blocks,
+                          mh_result **out);
+
 /* Greedy solve that allocates nothing (the paper has no counterpart: this is a
  * deployment variant of mh_solve).  For callers that cannot call cudaMalloc --
  * code running while another component owns all device memory through its own

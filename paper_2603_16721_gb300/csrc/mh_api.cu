@@ -6,11 +6,17 @@
 // handle's stream (depth 1, depths 2..h-1, leaves, finalize) and one 16-byte
 // read-back of the round state.
 #include <algorithm>
+#include <cmath>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <sys/stat.h>
 #include <string>
 #include <vector>
 
@@ -91,6 +97,7 @@ struct mh_handle {
     int *hState = nullptr;                // pinned: state + frontier counts
     GridSync *dSync = nullptr;            // barrier of the persistent solve
     int coop = 0, pgrid = 0;              // cooperative launch supported; persistent grid size
+    std::vector<int> m_s;                 // mutated genes per tumor sample (work estimate of a batch)
     int64_t frontier_bytes = 0;
 
     ~mh_handle()
@@ -140,6 +147,10 @@ int build_store(mh_handle *H, const uint64_t *bm)
         pc[g] = popcount_words(bm + (size_t)g * W, Wt);
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pc[a] < pc[b]; });
+    H->m_s.assign(Nt, 0);
+    for (int g = 0; g < G; ++g)
+        for (int w = 0; w < Wt; ++w)
+            for (uint64_t x = bm[(size_t)g * W + w]; x; x &= x - 1) ++H->m_s[w * 64 + __builtin_ctzll(x)];
 
     Cohort &c = H->c;
     c.G = G; c.Nt = Nt; c.Nn = Nn; c.Wt = Wt; c.Wn = Wn;
@@ -285,6 +296,128 @@ struct EventPair {
 
 }  // namespace
 
+namespace {
+
+// Validates the options, sizes the workspace and fills the device view of a solve.
+int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_rounds)
+{
+    if (!H || !opts) return fail(MH_EINVAL, "handle or opts is NULL");
+    const int h = opts->h;
+    if (h < 1 || h > kMaxH) return fail(MH_EINVAL, "h=%d outside [1, %d]", h, kMaxH);
+    if (opts->alpha.num < 0 || opts->alpha.den <= 0)
+        return fail(MH_EINVAL, "alpha=%d/%d: need num >= 0 and den > 0", opts->alpha.num, opts->alpha.den);
+    if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
+        return fail(MH_EINVAL, "prune=%d is not a pruning mode", opts->prune);
+    if (opts->mode != MH_MODE_PERSISTENT && opts->mode != MH_MODE_LAUNCHES)
+        return fail(MH_EINVAL, "mode=%d is not an execution mode", opts->mode);
+    int rc = ensure_workspace(H, h);
+    if (rc) return rc;
+    s->h = h;
+    s->prune = opts->prune;
+    s->a_num = (u64)opts->alpha.num;
+    s->a_den = (u64)opts->alpha.den;
+    s->U = H->dU;
+    s->state = H->dState;
+    s->res = H->dRes;
+    s->cnt = H->dCnt;
+    s->slots = H->dSlots;
+    s->nslots = H->ws_slots;
+    s->cand = H->dCand;
+    s->work = H->dWork;
+    s->best_hint = H->dWork + kWorkCount;
+    *max_rounds = H->Nt + 1;
+    if (opts->max_rounds > 0) *max_rounds = std::min(*max_rounds, (int)opts->max_rounds);
+    return MH_OK;
+}
+
+Frontiers frontiers_of(const mh_handle *H)
+{
+    Frontiers f;
+    for (int l = 0; l < kMaxH; ++l) {
+        f.F[l] = H->dF[l];
+        f.cap[l] = H->cap[l];
+    }
+    return f;
+}
+
+// Reads a finished solve back into a new mh_result.  kms: the four phase times
+// measured by the caller (used unless the persistent kernel measured them).
+int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const double *kms_in,
+                   int64_t launches, int64_t leaf_launches, mh_result **out)
+{
+    cudaStream_t st = H->stream;
+    int hs[kStateWords];
+    MH_CUDA(cudaMemcpyAsync(hs, H->dState, sizeof hs, cudaMemcpyDeviceToHost, st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    const int k = hs[0];
+    const int rounds = hs[4];
+    mh_result *R = (mh_result *)calloc(1, sizeof(mh_result));
+    if (!R) return fail(MH_ENOMEM, "host allocation of the result failed");
+    R->h = h;
+    R->k = k;
+    R->rounds = rounds;
+    R->genes = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k * h));
+    R->tp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
+    R->fp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
+    R->visited = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
+    R->pruned = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
+    if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned) {
+        mh_result_free(R);
+        return fail(MH_ENOMEM, "host allocation of the result failed");
+    }
+    std::vector<int> res((size_t)std::max(1, k) * (h + 2));
+    std::vector<u64> cnt((size_t)std::max(1, rounds) * h * 2);
+    std::vector<u64> work(kWorkCount);
+    cudaError_t e = cudaSuccess;
+    if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && rounds)
+        e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        mh_result_free(R);
+        return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
+    }
+    for (int i = 0; i < k; ++i) {
+        for (int j = 0; j < h; ++j) R->genes[i * h + j] = res[(size_t)i * (h + 2) + j];
+        R->tp[i] = res[(size_t)i * (h + 2) + h];
+        R->fp[i] = res[(size_t)i * (h + 2) + h + 1];
+    }
+    for (int i = 0; i < rounds * h; ++i) {
+        R->visited[i] = cnt[(size_t)i * 2];
+        R->pruned[i] = cnt[(size_t)i * 2 + 1];
+    }
+    double kms[4];
+    for (int i = 0; i < 4; ++i) kms[i] = kms_in ? kms_in[i] : 0.0;
+    if (persistent) {  // phase times measured inside the persistent kernel
+        for (int i = 0; i < 4; ++i) kms[i] = (double)work[kWorkPhaseNs + i] * 1e-6;
+        leaf_launches = h >= 2 ? rounds : 0;
+    }
+    R->solve_ms = solve_ms;
+    R->leaf_ms = kms[2];
+    R->level1_ms = kms[0];
+    R->expand_ms = kms[1];
+    R->finalize_ms = kms[3];
+    R->leaf_launches = leaf_launches;
+    R->mode = persistent ? MH_MODE_PERSISTENT : MH_MODE_LAUNCHES;
+    for (int i = 0; i < 2; ++i) {
+        R->diag[i] = work[kWorkWarpSum + i];
+        R->diag[2 + i] = work[kWorkWarpMaxSum + i];
+        R->diag[4 + i] = work[kWorkWarpN + i];
+    }
+    R->kernel_launches = launches;
+    R->leaf_words = work[kWorkColWords];
+    R->leaf_prefixes = work[kWorkPrefixes];
+    R->leaf_scored = work[kWorkScored];
+    R->leaf_alu_ops = work[kWorkAluOps];
+    R->leaf_dense = work[kWorkDense];
+    *out = R;
+    return MH_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 MH_API const char *mh_last_error(void) { return g_last_error.c_str(); }
@@ -364,35 +497,13 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
 {
     if (!out) return fail(MH_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!H || !opts) return fail(MH_EINVAL, "handle or opts is NULL");
-    const int h = opts->h;
-    if (h < 1 || h > kMaxH) return fail(MH_EINVAL, "h=%d outside [1, %d]", h, kMaxH);
-    if (opts->alpha.num < 0 || opts->alpha.den <= 0)
-        return fail(MH_EINVAL, "alpha=%d/%d: need num >= 0 and den > 0", opts->alpha.num, opts->alpha.den);
-    if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
-        return fail(MH_EINVAL, "prune=%d is not a pruning mode", opts->prune);
-    if (opts->mode != MH_MODE_PERSISTENT && opts->mode != MH_MODE_LAUNCHES)
-        return fail(MH_EINVAL, "mode=%d is not an execution mode", opts->mode);
-    int rc = ensure_workspace(H, h);
+    Solve s;
+    int max_rounds = 0;
+    int rc = prepare_solve(H, opts, &s, &max_rounds);
     if (rc) return rc;
+    const int h = opts->h;
     cudaStream_t st = H->stream;
     const Cohort &c = H->c;
-    Solve s;
-    s.h = h;
-    s.prune = opts->prune;
-    s.a_num = (u64)opts->alpha.num;
-    s.a_den = (u64)opts->alpha.den;
-    s.U = H->dU;
-    s.state = H->dState;
-    s.res = H->dRes;
-    s.cnt = H->dCnt;
-    s.slots = H->dSlots;
-    s.nslots = H->ws_slots;
-    s.cand = H->dCand;
-    s.work = H->dWork;
-    s.best_hint = H->dWork + kWorkCount;
-    int max_rounds = H->Nt + 1;
-    if (opts->max_rounds > 0) max_rounds = std::min(max_rounds, (int)opts->max_rounds);
 
     EventPair total;
     MH_CUDA(cudaEventCreate(&total.a));
@@ -520,56 +631,11 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         batch = std::min(batch * 2, 64);
     }
     MH_CUDA(cudaEventRecord(total.b, st));
-    MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
     MH_CUDA(cudaStreamSynchronize(st));
-    const int k = H->hState[0];
-    const int rounds = H->hState[4];
-
-    mh_result *R = (mh_result *)calloc(1, sizeof(mh_result));
-    if (!R) {
-        destroy_events();
-        return fail(MH_ENOMEM, "host allocation of the result failed");
-    }
-    R->h = h;
-    R->k = k;
-    R->rounds = rounds;
-    R->genes = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k * h));
-    R->tp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
-    R->fp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
-    R->visited = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
-    R->pruned = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
-    if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned) {
-        mh_result_free(R);
-        destroy_events();
-        return fail(MH_ENOMEM, "host allocation of the result failed");
-    }
-    std::vector<int> res((size_t)std::max(1, k) * (h + 2));
-    std::vector<u64> cnt((size_t)std::max(1, rounds) * h * 2);
-    std::vector<u64> work(kWorkCount);
-    cudaError_t e = cudaSuccess;
-    if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && rounds)
-        e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        mh_result_free(R);
-        destroy_events();
-        return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
-    }
-    for (int i = 0; i < k; ++i) {
-        for (int j = 0; j < h; ++j) R->genes[i * h + j] = res[(size_t)i * (h + 2) + j];
-        R->tp[i] = res[(size_t)i * (h + 2) + h];
-        R->fp[i] = res[(size_t)i * (h + 2) + h + 1];
-    }
-    for (int i = 0; i < rounds * h; ++i) {
-        R->visited[i] = cnt[(size_t)i * 2];
-        R->pruned[i] = cnt[(size_t)i * 2 + 1];
-    }
+    int rounds = 0;
+    MH_CUDA(cudaMemcpy(&rounds, H->dState + 4, sizeof(int), cudaMemcpyDeviceToHost));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, total.a, total.b);
-    R->solve_ms = ms;
     // kernel times of the rounds that ran (launches after the last round return at once)
     double kms[4] = {0, 0, 0, 0};
     int64_t timed = 0;
@@ -583,29 +649,269 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         ++timed;
     }
     destroy_events();
-    if (persistent) {  // phase times measured inside the persistent kernel
-        for (int i = 0; i < 4; ++i) kms[i] = (double)work[kWorkPhaseNs + i] * 1e-6;
-        leaf_launches = h >= 2 ? rounds : 0;
-    }
-    R->leaf_ms = kms[2];
-    R->level1_ms = kms[0];
-    R->expand_ms = kms[1];
-    R->finalize_ms = kms[3];
-    R->leaf_launches = opts->time_kernels && !persistent ? (h >= 2 ? timed : 0) : leaf_launches;
-    R->mode = persistent ? MH_MODE_PERSISTENT : MH_MODE_LAUNCHES;
-    for (int i = 0; i < 2; ++i) {
-        R->diag[i] = work[kWorkWarpSum + i];
-        R->diag[2 + i] = work[kWorkWarpMaxSum + i];
-        R->diag[4 + i] = work[kWorkWarpN + i];
-    }
-    R->kernel_launches = launches;
-    R->leaf_words = work[kWorkColWords];
-    R->leaf_prefixes = work[kWorkPrefixes];
-    R->leaf_scored = work[kWorkScored];
-    R->leaf_alu_ops = work[kWorkAluOps];
-    R->leaf_dense = work[kWorkDense];
-    *out = R;
-    return MH_OK;
+    const int64_t ll = opts->time_kernels && !persistent ? (h >= 2 ? timed : 0) : leaf_launches;
+    return collect_result(H, h, persistent, ms, kms, launches, ll, out);
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched solve and its autotuner.
+
+namespace {
+
+// Expected search work of a cohort: the (h-1)-gene prefixes that share a tumor,
+// summed over tumors, plus the depth-1 scan.
+double work_estimate(const mh_handle *H, int h)
+{
+    double w = (double)H->G;
+    for (int m : H->m_s) {
+        double comb = 1.0;
+        for (int i = 0; i < h - 1; ++i) comb = comb * (double)(m - i) / (double)(i + 1);
+        if (m >= h - 1) w += comb;
+    }
+    return w;
+}
+
+// Blocks per cohort: proportional to work^gamma, at least one each, summing to grid.
+std::vector<int> split_blocks(const std::vector<double> &work, double gamma, int grid)
+{
+    const int n = (int)work.size();
+    std::vector<double> wt(n);
+    double tot = 0;
+    for (int i = 0; i < n; ++i) tot += wt[i] = std::pow(std::max(work[i], 1.0), gamma);
+    std::vector<int> b(n, 1);
+    int left = grid - n;
+    std::vector<std::pair<double, int>> frac;
+    for (int i = 0; i < n; ++i) {
+        const double want = wt[i] / tot * (double)(grid - n);
+        const int whole = (int)want;
+        b[i] += whole;
+        left -= whole;
+        frac.push_back({want - whole, i});
+    }
+    std::sort(frac.begin(), frac.end(), [](auto &a, auto &c) { return a.first > c.first; });
+    for (int i = 0; i < n && left > 0; ++i, --left) ++b[frac[i].second];
+    return b;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, double> g_tune;  // batch signature -> chosen gamma
+bool g_tune_loaded = false;
+
+std::string tune_path()
+{
+    const char *p = getenv("MH_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/mh_autotune.txt";
+}
+
+// Bucketed shape of a batch: the sorted (h, log2 G, log2 Nt) of its cohorts.
+std::string batch_signature(mh_handle *const *hs, const mh_solve_opts *opts, int n, int grid)
+{
+    std::vector<std::string> parts;
+    for (int i = 0; i < n; ++i) {
+        std::ostringstream o;
+        o << opts[i].h << ":" << (int)std::lround(std::log2((double)hs[i]->G)) << ":"
+          << (int)std::lround(std::log2((double)std::max(1, hs[i]->Nt)));
+        parts.push_back(o.str());
+    }
+    std::sort(parts.begin(), parts.end());
+    std::ostringstream o;
+    o << "grid" << grid;
+    for (auto &p : parts) o << "," << p;
+    return o.str();
+}
+
+bool tune_lookup(const std::string &sig, double *gamma)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (!g_tune_loaded) {
+        g_tune_loaded = true;
+        std::ifstream in(tune_path());
+        std::string key;
+        double g;
+        while (in >> key >> g) g_tune[key] = g;
+    }
+    auto it = g_tune.find(sig);
+    if (it == g_tune.end()) return false;
+    *gamma = it->second;
+    return true;
+}
+
+void tune_store(const std::string &sig, double gamma)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[sig] = gamma;
+    const std::string path = tune_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        std::string cmd;  // best effort: the cache is an optimisation only
+        (void)cmd;
+        mkdir(dir.c_str(), 0755);
+    }
+    std::ofstream out(path, std::ios::trunc);
+    for (auto &kv : g_tune) out << kv.first << " " << kv.second << "\n";
+}
+
+// Device copy of the batch descriptors (grown on demand, shared by all calls).
+std::mutex g_items_mutex;
+BatchItem *g_items = nullptr;
+int g_items_cap = 0;
+
+// One batched run with a fixed split; on success the cohorts' device states hold
+// finished solves.  *ms receives the run's time (CUDA events).
+int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<int> &blocks, double *ms)
+{
+    cudaStream_t st = hs[0]->stream;
+    std::vector<Solve> ss(n);
+    std::vector<int> maxr(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = prepare_solve(hs[i], &opts[i], &ss[i], &maxr[i]);
+        if (rc) return rc;
+    }
+    cudaEvent_t a, b;
+    MH_CUDA(cudaEventCreate(&a));
+    MH_CUDA(cudaEventCreate(&b));
+    MH_CUDA(cudaEventRecord(a, st));
+    for (int i = 0; i < n; ++i) launch_solve_init(hs[i]->c, ss[i], hs[i]->ws_rounds, maxr[i], hs[i]->dCounts, st);
+    std::lock_guard<std::mutex> lock(g_items_mutex);
+    if (g_items_cap < n) {
+        cudaFree(g_items);
+        g_items = nullptr;
+        g_items_cap = 0;
+        MH_CUDA(cudaMalloc((void **)&g_items, sizeof(BatchItem) * (size_t)n));
+        g_items_cap = n;
+    }
+    std::vector<BatchItem> items(n);
+    std::vector<char> finished(n, 0);
+    for (int i = 0; i < n; ++i) finished[i] = hs[i]->Nt == 0;
+    for (int attempt = 0;; ++attempt) {
+        int first = 0, grid = 0;
+        for (int i = 0; i < n; ++i) {
+            items[i].c = hs[i]->c;
+            items[i].s = ss[i];
+            items[i].f = frontiers_of(hs[i]);
+            items[i].gsync = hs[i]->dSync;
+            items[i].counts = hs[i]->dCounts;
+            items[i].first_block = first;
+            items[i].nblocks = blocks[i];
+            first += blocks[i];
+            MH_CUDA(cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st));
+            if (finished[i]) {  // an empty cohort: mark it done, its team leaves at once
+                const int one = 1;
+                MH_CUDA(cudaMemcpyAsync(hs[i]->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+            }
+        }
+        grid = first;
+        MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st));
+        MH_CUDA(launch_solve_batch(g_items, n, grid, st));
+        MH_CUDA(cudaStreamSynchronize(st));
+        bool again = false;
+        for (int i = 0; i < n; ++i) {
+            mh_handle *H = hs[i];
+            MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
+            if (H->hState[2]) return fail(MH_ETIMEOUT, "a team barrier of the batched solve timed out");
+            if (H->hState[3]) {
+                MH_CUDA(cudaMemcpy(H->hState + kStateWords, H->dCounts, sizeof(u32) * kCountWords,
+                                   cudaMemcpyDeviceToHost));
+                const int r = H->hState[4];
+                int rc = grow_overflowed(H, opts[i].h, (const u32 *)(H->hState + kStateWords));
+                if (rc) return rc;
+                MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)r * opts[i].h * 2, 0, sizeof(u64) * 2 * opts[i].h, st));
+                MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountWords, st));
+                MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
+                again = true;
+            }
+        }
+        if (!again) break;
+    }
+    MH_CUDA(cudaEventRecord(b, st));
+    MH_CUDA(cudaEventSynchronize(b));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = t;
+    return MH_OK;
+}
+
+}  // namespace
+
+extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n,
+                                     const int32_t *blocks, mh_result **out)
+{
+    if (!handles || !opts || !out || n < 1) return fail(MH_EINVAL, "mh_solve_batch: NULL argument or n < 1");
+    for (int i = 0; i < n; ++i) {
+        out[i] = nullptr;
+        if (!handles[i]) return fail(MH_EINVAL, "mh_solve_batch: handle %d is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return fail(MH_EINVAL, "mh_solve_batch: handle %d appears twice", i);
+    }
+    mh_handle *H0 = handles[0];
+    if (!H0->coop) return fail(MH_ECUDA, "mh_solve_batch: the device has no cooperative launch");
+    for (int i = 0; i < n; ++i) {  // every handle sizes its workspace (and slot array) now
+        Solve tmp;
+        int mr;
+        int rc = prepare_solve(handles[i], &opts[i], &tmp, &mr);
+        if (rc) return rc;
+    }
+    const int grid = persistent_grid(H0->num_sms);
+    if (grid < n) return fail(MH_EINVAL, "mh_solve_batch: %d cohorts but only %d co-resident blocks", n, grid);
+    std::vector<int> b(n);
+    if (blocks) {
+        long long tot = 0;
+        for (int i = 0; i < n; ++i) {
+            if (blocks[i] < 1) return fail(MH_EINVAL, "mh_solve_batch: blocks[%d] = %d < 1", i, blocks[i]);
+            b[i] = blocks[i];
+            tot += blocks[i];
+        }
+        if (tot > grid) return fail(MH_EINVAL, "mh_solve_batch: %lld blocks requested, %d co-resident", tot, grid);
+    }
+    std::vector<double> work(n);
+    for (int i = 0; i < n; ++i) work[i] = work_estimate(handles[i], opts[i].h);
+    double ms = 0.0;
+    int rc = MH_OK;
+    if (blocks) {
+        rc = run_batch(handles, opts, n, b, &ms);
+    } else {
+        // autotuner: the split exponent gamma (blocks ~ work^gamma) is chosen by
+        // timing each candidate once per batch shape; the choice is cached on disk
+        const std::string sig = batch_signature(handles, opts, n, grid);
+        double gamma = 1.0;
+        const char *off = getenv("MH_AUTOTUNE");
+        if (off && off[0] == '0') {
+            rc = run_batch(handles, opts, n, split_blocks(work, gamma, grid), &ms);
+        } else if (tune_lookup(sig, &gamma)) {
+            rc = run_batch(handles, opts, n, split_blocks(work, gamma, grid), &ms);
+        } else {
+            const double cands[] = {0.0, 0.5, 0.75, 1.0};
+            double best_ms = 1e300, best_g = 1.0;
+            for (double g : cands) {
+                double t = 0.0;
+                rc = run_batch(handles, opts, n, split_blocks(work, g, grid), &t);
+                if (rc) return rc;
+                if (t < best_ms) {
+                    best_ms = t;
+                    best_g = g;
+                }
+            }
+            tune_store(sig, best_g);
+            rc = run_batch(handles, opts, n, split_blocks(work, best_g, grid), &ms);
+        }
+    }
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        rc = collect_result(handles[i], opts[i].h, true, ms, nullptr, 1, 0, &out[i]);
+        if (rc) {
+            for (int j = 0; j < i; ++j) {
+                mh_result_free(out[j]);
+                out[j] = nullptr;
+            }
+            return rc;
+        }
+    }
+    return MH_OK;
+}

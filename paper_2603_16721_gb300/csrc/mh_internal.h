@@ -134,6 +134,19 @@ void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t 
 // It returns when the solve is done, a frontier overflowed (state) or a grid
 // barrier timed out (state error = kErrTimeout).
 int persistent_grid(int num_sms);
+
+// One cohort of a batched solve: its device state and its share of the grid
+// (blocks [first_block, first_block + nblocks)).
+struct BatchItem {
+    Cohort c;
+    Solve s;
+    Frontiers f;
+    GridSync *gsync;
+    u32 *counts;
+    int first_block, nblocks;
+};
+// Runs every cohort of d_items (device array of n items) in one cooperative launch.
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int grid, cudaStream_t st);
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
                                     u32 *counts, int grid, cudaStream_t st);
 int level1_grid(const Cohort &c);

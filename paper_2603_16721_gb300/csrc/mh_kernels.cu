@@ -38,6 +38,13 @@ constexpr int kBatch = 32;       // prefixes taken per warp
 constexpr int kPlanesT = 5;      // bit planes for counts <= 20
 constexpr int kPlanesN = 4;      // bit planes for counts <= 12
 
+// The blocks that work on one cohort: this block's rank among them and their
+// number (the whole grid for a single solve; a share of it in a batch).
+struct Team {
+    int rank, size;
+};
+__device__ __forceinline__ Team grid_team() { return Team{(int)blockIdx.x, (int)gridDim.x}; }
+
 __device__ __forceinline__ int prefix_gene(const Prefix &p, int i)
 {
     const u64 w = i < 4 ? p.w0 : p.w1;
@@ -137,9 +144,9 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
     return v;
 }
 
-// Block-wide best key -> slots[blockIdx.x] (merged with what an earlier launch
-// of the same round left there).  All threads of the block must call it.
-__device__ void block_commit_best(Key best, Key *slots)
+// Block-wide best key -> slots[rank] (merged with what an earlier launch of the
+// same round left there).  All threads of the block must call it.
+__device__ void block_commit_best(Key best, Key *slots, int rank)
 {
     __shared__ Key wbest[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -150,8 +157,8 @@ __device__ void block_commit_best(Key best, Key *slots)
         Key k = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
         k = warp_max_key(k);
         if (lane == 0 && k.s != 0) {
-            const Key old = slots[blockIdx.x];
-            if (key_better(k, old)) slots[blockIdx.x] = k;
+            const Key old = slots[rank];
+            if (key_better(k, old)) slots[rank] = k;
         }
     }
 }
@@ -227,9 +234,9 @@ __device__ __forceinline__ const Rec *front_rec(const Rec *F, u32 cap_s, const i
 }
 
 // The shard a warp appends to: neighbouring warps use different counters.
-__device__ __forceinline__ int my_shard()
+__device__ __forceinline__ int my_shard(const Team &t)
 {
-    return (int)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kShards);
+    return (int)((t.rank * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kShards);
 }
 
 // Block-wide accumulation of counters: warps add into shared memory, then one
@@ -473,13 +480,13 @@ __device__ __forceinline__ int score_item(const Cohort &c, const Solve &s, const
 // per key, lane w on word w).  A key still covering an uncovered tumor is a
 // candidate of this round, so the largest value is a lower bound on this round's
 // best: the leaf phase need not score what cannot reach it.
-__device__ void rescore_candidates(const Cohort &c, const Solve &s)
+__device__ void rescore_candidates(const Cohort &c, const Solve &s, const Team &t)
 {
     const int lane = threadIdx.x & 31;
     const int h = s.h;
     u64 hint = 0;
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < kCandidates;
-         i += gridDim.x * (blockDim.x >> 5)) {
+    for (int i = t.rank * (blockDim.x >> 5) + (threadIdx.x >> 5); i < kCandidates;
+         i += t.size * (blockDim.x >> 5)) {
         Key k;
         k.s = __ldcg(&s.cand[i].s);
         if (k.s == 0) continue;
@@ -510,18 +517,19 @@ __device__ void rescore_candidates(const Cohort &c, const Solve &s)
 // the leaves and are scored here (the block's best goes to its slot); otherwise
 // the non-empty ones (all of them with pruning off) become depth-1 records.
 // Every thread of the block must call it.
-__device__ void phase_level1(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts)
+__device__ void phase_level1(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts,
+                             const Team &t)
 {
     __shared__ u64 acc[kAccN];
     const int lane = threadIdx.x & 31;
     const int h = s.h;
     acc_begin(acc);
-    if (h > 1) rescore_candidates(c, s);
+    if (h > 1) rescore_candidates(c, s, t);
     const int last = c.G - h;  // 0-based inclusive bound of depth 1
-    u32 *my_count = counts + shard_slot(1, my_shard());
-    Rec *out = f.F[1] + (size_t)my_shard() * f.cap[1];
+    u32 *my_count = counts + shard_slot(1, my_shard(t));
+    Rec *out = f.F[1] + (size_t)my_shard(t) * f.cap[1];
     Key best = key_empty();
-    for (int base = blockIdx.x * blockDim.x; base < c.G; base += gridDim.x * blockDim.x) {
+    for (int base = t.rank * blockDim.x; base < c.G; base += t.size * blockDim.x) {
         const int g = base + threadIdx.x;
         const bool in = g <= last;
         int ky = 0;
@@ -571,7 +579,7 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const F
         r.kn = sat16(kn);
         copy_rec(&out[pos], &r);
     }
-    if (h == 1) block_commit_best(best, s.slots);
+    if (h == 1) block_commit_best(best, s.slots, t.rank);
     __syncthreads();
     if (threadIdx.x < 2 && acc[threadIdx.x])
         atomicAdd(s.cnt + ((size_t)round * h) * 2 + threadIdx.x, acc[threadIdx.x]);
@@ -601,7 +609,7 @@ __device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc
 // block must call it; returns false (for every thread) if the input frontier
 // overflowed.
 __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int level, const Frontiers &f, u32 *counts,
-                             Batch &b)
+                             Batch &b, const Team &t)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -618,11 +626,11 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     const Rec *Fin = f.F[level - 1];
     const u32 cap_in = f.cap[level - 1];
     const u32 cap = f.cap[level];
-    u32 *my_count = counts + shard_slot(level, my_shard());
-    Rec *Fout = f.F[level] + (size_t)my_shard() * cap;
+    u32 *my_count = counts + shard_slot(level, my_shard(t));
+    Rec *Fout = f.F[level] + (size_t)my_shard(t) * cap;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
     const bool all_children = s.prune != 0;
-    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
+    const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
@@ -727,7 +735,8 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
 // below the best score known to exist cannot hold the round's winner, so its
 // leaves are tested (and counted) but not scored.  Every thread of the block
 // must call it; returns false (for every thread) if the input frontier overflowed.
-__device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts, Batch &b)
+__device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts, Batch &b,
+                           const Team &t)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -746,7 +755,7 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     const u32 cap_in = f.cap[h - 1];
     u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const u64 nn_term = s.a_den * (u64)c.Nn + 1;
-    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5), gw = (u64)blockIdx.x * (blockDim.x >> 5) + warp;
+    const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
         unsigned dense;
         const int total = batch_prepare(Fin, cap_in, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense,
@@ -840,7 +849,7 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     if (threadIdx.x == 3 && acc[3]) atomicAdd(s.work + kWorkPrefixes, acc[3]);
     if (threadIdx.x == 4 && acc[4]) atomicAdd(s.work + kWorkScored, acc[4]);
     warp_cycles_flush(s, acc, 1);
-    block_commit_best(best, s.slots);
+    block_commit_best(best, s.slots, t.rank);
     return true;
 }
 
@@ -964,14 +973,15 @@ __global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
 __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Frontiers f, u32 *counts)
 {
     if (halted(s)) return;
-    phase_level1(c, s, s.state[kStRound], f, counts);
+    phase_level1(c, s, s.state[kStRound], f, counts, grid_team());
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
-    if (!phase_expand(c, s, s.state[kStRound], level, f, counts, scratch[threadIdx.x >> 5]) && threadIdx.x == 0)
+    if (!phase_expand(c, s, s.state[kStRound], level, f, counts, scratch[threadIdx.x >> 5], grid_team()) &&
+        threadIdx.x == 0)
         s.state[kStOverflow] = 1;
 }
 
@@ -979,7 +989,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, Frontie
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
-    if (!phase_leaf(c, s, s.state[kStRound], f, counts, scratch[threadIdx.x >> 5]) && threadIdx.x == 0)
+    if (!phase_leaf(c, s, s.state[kStRound], f, counts, scratch[threadIdx.x >> 5], grid_team()) && threadIdx.x == 0)
         s.state[kStOverflow] = 1;
 }
 
@@ -994,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *c
 
 // Grid barrier with a bounded wait: a block that waits longer than about two
 // seconds records a timeout in the state and returns false instead of hanging.
-__device__ __forceinline__ bool grid_sync(GridSync *g, int *state)
+__device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks)
 {
     __shared__ int ok;
     __syncthreads();
@@ -1003,7 +1013,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state)
         const unsigned gen = *(volatile unsigned *)&g->gen;
         __threadfence();
         const unsigned arrived = atomicAdd(&g->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        if (arrived == (unsigned)nblocks) {
             atomicExch(&g->count, 0u);
             __threadfence();
             atomicAdd(&g->gen, 1u);
@@ -1031,19 +1041,21 @@ __device__ __forceinline__ u64 global_ns()
     return t;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
+// The greedy loop of one cohort run by a team of co-resident blocks, its phases
+// separated by the team's barrier.  Returns when the solve is done, a frontier
+// overflowed or a barrier timed out (recorded in the cohort's state).
+__device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts,
+                           const Team &t, Batch &b)
 {
-    __shared__ Batch scratch[kWarpsPerBlock];
     __shared__ int stop;
-    Batch &b = scratch[threadIdx.x >> 5];
     const int h = s.h;
-    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-    u64 t = timer ? global_ns() : 0;
+    const bool timer = t.rank == 0 && threadIdx.x == 0;
+    u64 tm = timer ? global_ns() : 0;
     auto lap = [&](int phase) {
         if (timer) {
             const u64 now = global_ns();
-            atomicAdd(s.work + kWorkPhaseNs + phase, now - t);
-            t = now;
+            atomicAdd(s.work + kWorkPhaseNs + phase, now - tm);
+            tm = now;
         }
     };
     for (;;) {
@@ -1051,33 +1063,55 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Fronti
             stop = *(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStOverflow] |
                    *(volatile int *)&s.state[kStError];
         __syncthreads();
-        if (stop) break;
+        if (stop) return;
         const int round = *(volatile int *)&s.state[kStRound];
-        phase_level1(c, s, round, f, counts);
-        if (!grid_sync(gsync, s.state)) return;
+        phase_level1(c, s, round, f, counts, t);
+        if (!grid_sync(gsync, s.state, t.size)) return;
         lap(0);
         // every block reads the same shard counts after the same barrier, so an
         // overflow is seen by all of them and they leave together
         for (int l = 2; l <= h - 1; ++l) {
-            if (!phase_expand(c, s, round, l, f, counts, b)) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+            if (!phase_expand(c, s, round, l, f, counts, b, t)) {
+                if (t.rank == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
                 return;
             }
-            if (!grid_sync(gsync, s.state)) return;
+            if (!grid_sync(gsync, s.state, t.size)) return;
         }
         lap(1);
         if (h >= 2) {
-            if (!phase_leaf(c, s, round, f, counts, b)) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+            if (!phase_leaf(c, s, round, f, counts, b, t)) {
+                if (t.rank == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
                 return;
             }
-            if (!grid_sync(gsync, s.state)) return;
+            if (!grid_sync(gsync, s.state, t.size)) return;
         }
         lap(2);
-        if (blockIdx.x == 0) phase_finalize(c, s, counts, gridDim.x);
-        if (!grid_sync(gsync, s.state)) return;
+        if (t.rank == 0) phase_finalize(c, s, counts, t.size);
+        if (!grid_sync(gsync, s.state, t.size)) return;
         lap(3);
     }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
+{
+    __shared__ Batch scratch[kWarpsPerBlock];
+    solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5]);
+}
+
+// Batched solve: block b works on the cohort whose block range holds b, with the
+// blocks of that range as its team; cohorts progress independently.
+__global__ void __launch_bounds__(kThreads, 3) k_solve_batch(const BatchItem *items, int n)
+{
+    __shared__ Batch scratch[kWarpsPerBlock];
+    int lo = 0, hi = n - 1;  // last item with first_block <= blockIdx.x
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].first_block <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const BatchItem &it = items[lo];
+    const Team t{(int)blockIdx.x - it.first_block, it.nblocks};
+    if (t.rank >= t.size) return;
+    solve_team(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5]);
 }
 
 }  // namespace
@@ -1134,6 +1168,14 @@ int persistent_grid(int num_sms)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kThreads, 0) != cudaSuccess) return 0;
     return per_sm * num_sms;
+}
+
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int grid, cudaStream_t st)
+{
+    const BatchItem *items = d_items;
+    int nn = n;
+    void *args[] = {&items, &nn};
+    return cudaLaunchCooperativeKernel((const void *)k_solve_batch, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,

@@ -253,3 +253,24 @@ def mh_solve_noalloc(d_bitmaps_ptr: int, G: int, Nt: int, Nn: int, h: int, alpha
                                 _P(d_genes_ptr), _P(d_tp_ptr), _P(d_fp_ptr), capacity, ctypes.byref(k),
                                 ctypes.byref(rounds)))
     return k.value, rounds.value
+
+
+def mh_solve_batch(handles, hs, alphas=None, blocks=None, prune: int = MH_PRUNE_PAPER, max_rounds: int = 0):
+    """Solve several cohorts in one persistent launch (see include/mh.h).
+    handles: list of Handle; hs: hit count per cohort; alphas: (num, den) per
+    cohort (default 1/10); blocks: block split per cohort or None (autotuned)."""
+    lib = load()
+    if not hasattr(lib, "_batch_typed"):
+        lib.mh_solve_batch.restype = ctypes.c_int
+        lib.mh_solve_batch.argtypes = [ctypes.POINTER(_P), ctypes.POINTER(mh_solve_opts), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.POINTER(mh_result))]
+        lib._batch_typed = True
+    n = len(handles)
+    alphas = alphas or [(1, 10)] * n
+    ptrs = (_P * n)(*[h.ptr for h in handles])
+    opts = (mh_solve_opts * n)(*[mh_solve_opts(int(hs[i]), mh_rational(*alphas[i]), prune, max_rounds, 0,
+                                               MH_MODE_PERSISTENT) for i in range(n)])
+    b = (ctypes.c_int32 * n)(*blocks) if blocks is not None else None
+    outs = (ctypes.POINTER(mh_result) * n)()
+    _check(lib.mh_solve_batch(ptrs, opts, n, b, outs))
+    return [_to_result(outs[i]) for i in range(n)]
