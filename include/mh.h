@@ -157,11 +157,14 @@ MH_API void mh_destroy(mh_handle *handle);
 MH_API const char *mh_last_error(void);
 
 /* Batched solve: n cohorts (distinct handles, one device) with their options are
- * solved in ONE cooperative launch.  The co-resident grid is split into n teams of
- * blocks, team i running the greedy loop of cohort i (Algorithm 1 with P-DFS) at
- * its own pace; the paper runs one cohort at a time, this is the GB300 batching
- * of independent problems.  blocks: n block counts (each >= 1, summing to at most
- * the co-resident grid), or NULL to let the autotuner choose: blocks ~ work^gamma
+ * solved by cooperative launches of one persistent kernel.  The co-resident grid
+ * is split into teams of blocks, team i running the greedy loop of cohort i
+ * (Algorithm 1 with P-DFS) at its own pace; each time a cohort finishes, the
+ * launch ends at the others' next round boundary and the unfinished cohorts
+ * share the whole grid again (one launch per finished cohort at most).  The paper
+ * runs one cohort at a time; this is the GB300 batching of independent problems.
+ * blocks: n block counts (each >= 1, summing to at most the co-resident grid; kept
+ * fixed), or NULL to let the autotuner choose: blocks ~ work^gamma
  * with the per-cohort work estimated from the tumors' mutation counts, gamma
  * picked by timing each candidate once per batch shape and cached in the file
  * named by MH_AUTOTUNE_CACHE (default ~/.cache/mh_autotune.txt; MH_AUTOTUNE=0

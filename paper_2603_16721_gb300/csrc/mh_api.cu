@@ -761,11 +761,15 @@ std::mutex g_items_mutex;
 BatchItem *g_items = nullptr;
 int g_items_cap = 0;
 
-// One batched run with a fixed split; on success the cohorts' device states hold
-// finished solves.  *ms receives the run's time (CUDA events).
-int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<int> &blocks, double *ms)
+// One batched run: all cohorts start from "nothing covered"; the grid is split
+// between the unfinished cohorts (blocks ~ work^gamma, or the fixed split) and,
+// each time a cohort finishes, the launch ends and the remaining cohorts share
+// the whole grid again.  *ms receives the run's time (CUDA events).
+int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, double gamma,
+              const std::vector<int> *fixed, double *ms)
 {
     cudaStream_t st = hs[0]->stream;
+    const int grid = persistent_grid(hs[0]->num_sms);
     std::vector<Solve> ss(n);
     std::vector<int> maxr(n);
     for (int i = 0; i < n; ++i) {
@@ -782,35 +786,44 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         cudaFree(g_items);
         g_items = nullptr;
         g_items_cap = 0;
-        MH_CUDA(cudaMalloc((void **)&g_items, sizeof(BatchItem) * (size_t)n));
+        MH_CUDA(cudaMalloc((void **)&g_items, sizeof(BatchItem) * (size_t)n + 256));
         g_items_cap = n;
     }
-    std::vector<BatchItem> items(n);
+    int *d_yield = (int *)((char *)g_items + sizeof(BatchItem) * (size_t)g_items_cap);
     std::vector<char> finished(n, 0);
     for (int i = 0; i < n; ++i) finished[i] = hs[i]->Nt == 0;
-    for (int attempt = 0;; ++attempt) {
-        int first = 0, grid = 0;
-        for (int i = 0; i < n; ++i) {
-            items[i].c = hs[i]->c;
-            items[i].s = ss[i];
-            items[i].f = frontiers_of(hs[i]);
-            items[i].gsync = hs[i]->dSync;
-            items[i].counts = hs[i]->dCounts;
-            items[i].first_block = first;
-            items[i].nblocks = blocks[i];
-            first += blocks[i];
-            MH_CUDA(cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st));
-            if (finished[i]) {  // an empty cohort: mark it done, its team leaves at once
-                const int one = 1;
-                MH_CUDA(cudaMemcpyAsync(hs[i]->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st));
-            }
+    for (;;) {
+        std::vector<int> act;
+        for (int i = 0; i < n; ++i)
+            if (!finished[i]) act.push_back(i);
+        if (act.empty()) break;
+        std::vector<int> blocks;
+        if (fixed) {
+            for (int i : act) blocks.push_back((*fixed)[i]);
+        } else {
+            std::vector<double> w;
+            for (int i : act) w.push_back(work[i]);
+            blocks = split_blocks(w, gamma, grid);
         }
-        grid = first;
-        MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st));
-        MH_CUDA(launch_solve_batch(g_items, n, grid, st));
+        std::vector<BatchItem> items(act.size());
+        int first = 0;
+        for (size_t k = 0; k < act.size(); ++k) {
+            const int i = act[k];
+            items[k].c = hs[i]->c;
+            items[k].s = ss[i];
+            items[k].f = frontiers_of(hs[i]);
+            items[k].gsync = hs[i]->dSync;
+            items[k].counts = hs[i]->dCounts;
+            items[k].first_block = first;
+            items[k].nblocks = blocks[k];
+            first += blocks[k];
+            MH_CUDA(cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st));
+        }
+        MH_CUDA(cudaMemsetAsync(d_yield, 0, sizeof(int), st));
+        MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st));
+        MH_CUDA(launch_solve_batch(g_items, (int)items.size(), act.size() > 1 ? d_yield : nullptr, first, st));
         MH_CUDA(cudaStreamSynchronize(st));
-        bool again = false;
-        for (int i = 0; i < n; ++i) {
+        for (int i : act) {
             mh_handle *H = hs[i];
             MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
             if (H->hState[2]) return fail(MH_ETIMEOUT, "a team barrier of the batched solve timed out");
@@ -823,10 +836,9 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)r * opts[i].h * 2, 0, sizeof(u64) * 2 * opts[i].h, st));
                 MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
-                again = true;
             }
+            finished[i] = H->hState[1] != 0;
         }
-        if (!again) break;
     }
     MH_CUDA(cudaEventRecord(b, st));
     MH_CUDA(cudaEventSynchronize(b));
@@ -875,7 +887,7 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     double ms = 0.0;
     int rc = MH_OK;
     if (blocks) {
-        rc = run_batch(handles, opts, n, b, &ms);
+        rc = run_batch(handles, opts, n, work, 1.0, &b, &ms);
     } else {
         // autotuner: the split exponent gamma (blocks ~ work^gamma) is chosen by
         // timing each candidate once per batch shape; the choice is cached on disk
@@ -883,15 +895,15 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         double gamma = 1.0;
         const char *off = getenv("MH_AUTOTUNE");
         if (off && off[0] == '0') {
-            rc = run_batch(handles, opts, n, split_blocks(work, gamma, grid), &ms);
+            rc = run_batch(handles, opts, n, work, gamma, nullptr, &ms);
         } else if (tune_lookup(sig, &gamma)) {
-            rc = run_batch(handles, opts, n, split_blocks(work, gamma, grid), &ms);
+            rc = run_batch(handles, opts, n, work, gamma, nullptr, &ms);
         } else {
             const double cands[] = {0.0, 0.5, 0.75, 1.0};
             double best_ms = 1e300, best_g = 1.0;
             for (double g : cands) {
                 double t = 0.0;
-                rc = run_batch(handles, opts, n, split_blocks(work, g, grid), &t);
+                rc = run_batch(handles, opts, n, work, g, nullptr, &t);
                 if (rc) return rc;
                 if (t < best_ms) {
                     best_ms = t;
@@ -899,7 +911,7 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
                 }
             }
             tune_store(sig, best_g);
-            rc = run_batch(handles, opts, n, split_blocks(work, best_g, grid), &ms);
+            rc = run_batch(handles, opts, n, work, best_g, nullptr, &ms);
         }
     }
     if (rc) return rc;

@@ -145,8 +145,10 @@ struct BatchItem {
     u32 *counts;
     int first_block, nblocks;
 };
-// Runs every cohort of d_items (device array of n items) in one cooperative launch.
-cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int grid, cudaStream_t st);
+// Runs the cohorts of d_items (device array of n items) in one cooperative launch.
+// With d_yield (a zeroed device int), the launch ends as soon as one cohort
+// finishes: every other team stops at its next round boundary.
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, int grid, cudaStream_t st);
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
                                     u32 *counts, int grid, cudaStream_t st);
 int level1_grid(const Cohort &c);

@@ -1045,7 +1045,7 @@ __device__ __forceinline__ u64 global_ns()
 // separated by the team's barrier.  Returns when the solve is done, a frontier
 // overflowed or a barrier timed out (recorded in the cohort's state).
 __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts,
-                           const Team &t, Batch &b)
+                           const Team &t, Batch &b, int *yield = nullptr)
 {
     __shared__ int stop;
     const int h = s.h;
@@ -1059,9 +1059,14 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         }
     };
     for (;;) {
-        if (threadIdx.x == 0)
-            stop = *(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStOverflow] |
-                   *(volatile int *)&s.state[kStError];
+        if (threadIdx.x == 0) {
+            const int done = *(volatile int *)&s.state[kStDone];
+            stop = done | *(volatile int *)&s.state[kStOverflow] | *(volatile int *)&s.state[kStError] |
+                   (yield ? *(volatile int *)yield : 0);
+            // a batch team that finishes asks the others to stop at their next round
+            // boundary, so that the host can give its blocks to the unfinished cohorts
+            if (done && yield && t.rank == 0) atomicExch(yield, 1);
+        }
         __syncthreads();
         if (stop) return;
         const int round = *(volatile int *)&s.state[kStRound];
@@ -1100,7 +1105,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Fronti
 
 // Batched solve: block b works on the cohort whose block range holds b, with the
 // blocks of that range as its team; cohorts progress independently.
-__global__ void __launch_bounds__(kThreads, 3) k_solve_batch(const BatchItem *items, int n)
+__global__ void __launch_bounds__(kThreads, 3) k_solve_batch(const BatchItem *items, int n, int *yield)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     int lo = 0, hi = n - 1;  // last item with first_block <= blockIdx.x
@@ -1111,7 +1116,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve_batch(const BatchItem *it
     const BatchItem &it = items[lo];
     const Team t{(int)blockIdx.x - it.first_block, it.nblocks};
     if (t.rank >= t.size) return;
-    solve_team(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5]);
+    solve_team(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5], yield);
 }
 
 }  // namespace
@@ -1170,11 +1175,12 @@ int persistent_grid(int num_sms)
     return per_sm * num_sms;
 }
 
-cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int grid, cudaStream_t st)
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, int grid, cudaStream_t st)
 {
     const BatchItem *items = d_items;
     int nn = n;
-    void *args[] = {&items, &nn};
+    int *yield = d_yield;
+    void *args[] = {&items, &nn, &yield};
     return cudaLaunchCooperativeKernel((const void *)k_solve_batch, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
