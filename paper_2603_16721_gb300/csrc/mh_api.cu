@@ -818,6 +818,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             items[k].nblocks = blocks[k];
             first += blocks[k];
             MH_CUDA(cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st));
+            MH_CUDA(cudaMemsetAsync(hs[i]->dState + 6, 0, sizeof(int), st));  // yield request
         }
         MH_CUDA(cudaMemsetAsync(d_yield, 0, sizeof(int), st));
         MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st));

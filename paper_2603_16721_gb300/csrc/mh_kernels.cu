@@ -203,7 +203,7 @@ __device__ __forceinline__ u16 sat16(int v) { return (u16)(v < 0xffff ? v : 0xff
 
 // Round state (Solve::state): a kernel of a round does nothing once the solve is
 // done or a frontier of the round has overflowed.
-enum { kStK = 0, kStDone = 1, kStError = 2, kStOverflow = 3, kStRound = 4, kStMaxRounds = 5 };
+enum { kStK = 0, kStDone = 1, kStError = 2, kStOverflow = 3, kStRound = 4, kStMaxRounds = 5, kStYield = 6 };
 
 __device__ __forceinline__ bool halted(const Solve &s) { return s.state[kStDone] | s.state[kStOverflow]; }
 
@@ -1059,14 +1059,11 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         }
     };
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int done = *(volatile int *)&s.state[kStDone];
-            stop = done | *(volatile int *)&s.state[kStOverflow] | *(volatile int *)&s.state[kStError] |
-                   (yield ? *(volatile int *)yield : 0);
-            // a batch team that finishes asks the others to stop at their next round
-            // boundary, so that the host can give its blocks to the unfinished cohorts
-            if (done && yield && t.rank == 0) atomicExch(yield, 1);
-        }
+        // the decision to stop is read from the cohort's state, written before the
+        // barrier that ended the previous round: every block of the team agrees
+        if (threadIdx.x == 0)
+            stop = *(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStOverflow] |
+                   *(volatile int *)&s.state[kStError] | *(volatile int *)&s.state[kStYield];
         __syncthreads();
         if (stop) return;
         const int round = *(volatile int *)&s.state[kStRound];
@@ -1091,7 +1088,15 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
             if (!grid_sync(gsync, s.state, t.size)) return;
         }
         lap(2);
-        if (t.rank == 0) phase_finalize(c, s, counts, t.size);
+        if (t.rank == 0) {
+            phase_finalize(c, s, counts, t.size);
+            // batch: a team that finished asks the others to stop after their current
+            // round, so that the host can hand its blocks to the unfinished cohorts
+            if (yield && threadIdx.x == 0) {
+                if (*(volatile int *)&s.state[kStDone]) atomicExch(yield, 1);
+                else if (*(volatile int *)yield) s.state[kStYield] = 1;
+            }
+        }
         if (!grid_sync(gsync, s.state, t.size)) return;
         lap(3);
     }
