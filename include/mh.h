@@ -165,7 +165,8 @@ MH_API const char *mh_last_error(void);
  * runs one cohort at a time; this is the GB300 batching of independent problems.
  * blocks: n block counts (each >= 1, summing to at most the co-resident grid; kept
  * fixed), or NULL to let the autotuner choose: blocks ~ work^gamma
- * with the per-cohort work estimated from the tumors' mutation counts, gamma
+ * with the per-cohort work estimated from the tumors' mutation counts (the gene
+ * sets of size h-1, or of size h, that share a tumor), model and gamma
  * picked by timing each candidate once per batch shape and cached in the file
  * named by MH_AUTOTUNE_CACHE (default ~/.cache/mh_autotune.txt; MH_AUTOTUNE=0
  * disables tuning).  Work runs on the first handle's stream; the call is

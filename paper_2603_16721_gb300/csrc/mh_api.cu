@@ -660,15 +660,16 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
 
 namespace {
 
-// Expected search work of a cohort: the (h-1)-gene prefixes that share a tumor,
-// summed over tumors, plus the depth-1 scan.
-double work_estimate(const mh_handle *H, int h)
+// Expected search work of a cohort: the gene sets of size d that share a tumor,
+// summed over tumors (d = h - 1: the prefixes the leaves hang from; d = h: the
+// non-empty leaves), plus the depth-1 scan.
+double work_estimate(const mh_handle *H, int d)
 {
     double w = (double)H->G;
     for (int m : H->m_s) {
         double comb = 1.0;
-        for (int i = 0; i < h - 1; ++i) comb = comb * (double)(m - i) / (double)(i + 1);
-        if (m >= h - 1) w += comb;
+        for (int i = 0; i < d; ++i) comb = comb * (double)(m - i) / (double)(i + 1);
+        if (m >= d) w += comb;
     }
     return w;
 }
@@ -696,7 +697,7 @@ std::vector<int> split_blocks(const std::vector<double> &work, double gamma, int
 }
 
 std::mutex g_tune_mutex;
-std::map<std::string, double> g_tune;  // batch signature -> chosen gamma
+std::map<std::string, double> g_tune;  // batch signature -> chosen model (10 * d_extra + gamma)
 bool g_tune_loaded = false;
 
 std::string tune_path()
@@ -883,36 +884,43 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         }
         if (tot > grid) return fail(MH_EINVAL, "mh_solve_batch: %lld blocks requested, %d co-resident", tot, grid);
     }
-    std::vector<double> work(n);
-    for (int i = 0; i < n; ++i) work[i] = work_estimate(handles[i], opts[i].h);
+    // two work models: prefixes (d = h - 1) or leaves (d = h) sharing a tumor
+    std::vector<double> work_p(n), work_l(n);
+    for (int i = 0; i < n; ++i) {
+        work_p[i] = work_estimate(handles[i], opts[i].h - 1);
+        work_l[i] = work_estimate(handles[i], opts[i].h);
+    }
     double ms = 0.0;
     int rc = MH_OK;
     if (blocks) {
-        rc = run_batch(handles, opts, n, work, 1.0, &b, &ms);
+        rc = run_batch(handles, opts, n, work_p, 1.0, &b, &ms);
     } else {
-        // autotuner: the split exponent gamma (blocks ~ work^gamma) is chosen by
-        // timing each candidate once per batch shape; the choice is cached on disk
+        // autotuner: the work model and the split exponent gamma (blocks ~ work^gamma)
+        // are chosen by timing each candidate once per batch shape; the choice is
+        // cached on disk (encoded as 10 * model + gamma)
         const std::string sig = batch_signature(handles, opts, n, grid);
-        double gamma = 1.0;
+        double choice = 1.0;
         const char *off = getenv("MH_AUTOTUNE");
-        if (off && off[0] == '0') {
-            rc = run_batch(handles, opts, n, work, gamma, nullptr, &ms);
-        } else if (tune_lookup(sig, &gamma)) {
-            rc = run_batch(handles, opts, n, work, gamma, nullptr, &ms);
+        if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
+            const bool leaves = choice >= 10.0;
+            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), nullptr, &ms);
         } else {
-            const double cands[] = {0.0, 0.5, 0.75, 1.0};
-            double best_ms = 1e300, best_g = 1.0;
-            for (double g : cands) {
-                double t = 0.0;
-                rc = run_batch(handles, opts, n, work, g, nullptr, &t);
-                if (rc) return rc;
-                if (t < best_ms) {
-                    best_ms = t;
-                    best_g = g;
+            const double gammas[] = {0.5, 0.75, 1.0};
+            double best_ms = 1e300, best = 1.0;
+            for (int model = 0; model < 2; ++model) {
+                for (double g : gammas) {
+                    double t = 0.0;
+                    rc = run_batch(handles, opts, n, model ? work_l : work_p, g, nullptr, &t);
+                    if (rc) return rc;
+                    if (t < best_ms) {
+                        best_ms = t;
+                        best = 10.0 * model + g;
+                    }
                 }
             }
-            tune_store(sig, best_g);
-            rc = run_batch(handles, opts, n, work, best_g, nullptr, &ms);
+            tune_store(sig, best);
+            const bool leaves = best >= 10.0;
+            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, best - (leaves ? 10.0 : 0.0), nullptr, &ms);
         }
     }
     if (rc) return rc;
