@@ -176,6 +176,49 @@ MH_API const char *mh_last_error(void);
 MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n, const int32_t *blocks,
                           mh_result **out);
 
+/* ---- Served runtime: continuous batching of solves ------------------------
+ * A server owns a scheduler thread.  Submitted requests (a cohort in host
+ * memory, h, alpha) wait in FIFO order until a slot and device memory are free:
+ * admission uploads the cohort (as mh_create) when its estimated footprint
+ * (store, workspace and, for h >= 3, the search frontiers estimated from the
+ * (h-1)-gene sets sharing a tumor) fits the memory budget.  Active requests are
+ * solved together, a team of blocks each, by the batched kernel; a launch ends at
+ * a round boundary when a request finishes or a queued request can start, so new
+ * requests join at the next round of the others (continuous batching) and every
+ * cohort stays resident on the device between its rounds.  Results are those of
+ * mh_solve (MH_MODE_PERSISTENT); a served result's solve_ms is the request's
+ * latency from submission to completion. */
+typedef struct mh_server mh_server;
+typedef struct {
+    int64_t hbm_budget_bytes; /* device memory for active requests; <= 0: 80% of the free memory */
+    int32_t slots;            /* requests solved concurrently; <= 0: 8 */
+} mh_server_opts;
+
+/* Starts a server on the current device.  opts may be NULL (defaults).
+ * Errors: MH_ECUDA (no cooperative launch), MH_ENOMEM. */
+MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out);
+
+/* Queues a request; the packed rows (HOST memory, layout above) are copied, so the
+ * caller may free them on return.  Non-blocking.  *ticket identifies the request.
+ * Errors: MH_EINVAL.  A request larger than the whole budget later completes
+ * with MH_EREJECT. */
+MH_API int mh_submit(mh_server *server, const uint64_t *bitmaps, int32_t G, int32_t Nt, int32_t Nn, int32_t h,
+                     mh_rational alpha, uint64_t *ticket);
+
+/* Result of a finished request (the ticket is then released): MH_OK with *out set,
+ * MH_EAGAIN while it is queued or running, or the request's own error. */
+MH_API int mh_poll(mh_server *server, uint64_t ticket, mh_result **out);
+
+/* As mh_poll, waiting up to timeout_ms (< 0: without limit); MH_EAGAIN on timeout. */
+MH_API int mh_wait(mh_server *server, uint64_t ticket, int32_t timeout_ms, mh_result **out);
+
+/* Launches made so far, queued and active requests, device bytes reserved. */
+MH_API int mh_server_stats(mh_server *server, int64_t *launches, int32_t *queued, int32_t *active,
+                           int64_t *bytes_in_use);
+
+/* Finishes every submitted request, then stops the server; results not taken are freed. */
+MH_API void mh_server_destroy(mh_server *server);
+
 /* Greedy solve that allocates nothing (the paper has no counterpart: this is a
  * deployment variant of mh_solve).  For callers that cannot call cudaMalloc --
  * code running while another component owns all device memory through its own

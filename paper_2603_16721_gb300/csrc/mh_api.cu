@@ -6,6 +6,10 @@
 // handle's stream (depth 1, depths 2..h-1, leaves, finalize) and one 16-byte
 // read-back of the round state.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cmath>
 #include <fstream>
 #include <map>
@@ -936,3 +940,388 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     }
     return MH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Served runtime: continuous batching of greedy solves.
+//
+// A scheduler thread keeps a set of active requests, each solved by a team of
+// blocks of one cooperative launch of the batched kernel.  The launch ends at the
+// next round boundary whenever an active request finishes, or when the scheduler
+// raises the yield flag (host memory mapped into the device) because a new request
+// is waiting for a free slot; between launches the scheduler retires finished
+// requests, admits queued ones within the memory budget (uploading their cohorts),
+// and relaunches with the grid split between the active requests again.
+
+namespace {
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerReq {
+    uint64_t ticket = 0;
+    std::vector<uint64_t> bm;
+    int G = 0, Nt = 0, Nn = 0;
+    mh_solve_opts opts{};
+    double t_submit = 0, t_done = 0;
+    int64_t footprint = 0;
+    mh_handle *H = nullptr;
+    int status = -1;  // -1 pending, MH_OK done, else the error
+    std::string msg;
+    mh_result *res = nullptr;
+    Solve s{};
+};
+
+// Device memory a request needs: its store, workspace and (for h >= 3) the
+// frontiers, estimated from the (h-1)-gene sets that share a tumor.
+int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h)
+{
+    const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64;
+    std::vector<int> m(Nt, 0);
+    for (int g = 0; g < G; ++g)
+        for (int w = 0; w < Wt; ++w)
+            for (uint64_t x = bm[(size_t)g * (Wt + Wn) + w]; x; x &= x - 1) ++m[w * 64 + __builtin_ctzll(x)];
+    const int64_t gw = ((G + 63) / 64 + 2);
+    int64_t bytes = (int64_t)G * (Wt + Wn + 4) * 8 + (int64_t)(Nt + Nn) * gw * 8;
+    bytes += (int64_t)((G + kShards - 1) / kShards + 64) * kShards * (int64_t)sizeof(Rec);
+    if (h >= 3) {
+        double sets = 0;
+        for (int x : m) {
+            double comb = 1.0;
+            for (int i = 0; i < h - 1; ++i) comb = comb * (double)(x - i) / (double)(i + 1);
+            if (x >= h - 1) sets += comb;
+        }
+        bytes += (int64_t)(sets * 1.25 * (double)sizeof(Rec));
+    }
+    return bytes + (64 << 20);
+}
+
+}  // namespace
+
+struct mh_server {
+    mh_server_opts o{};
+    cudaStream_t st = nullptr;
+    int grid = 0, num_sms = 0;
+    int64_t budget = 0, in_use = 0;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<ServerReq *> queue;
+    std::vector<ServerReq *> active;
+    std::map<uint64_t, ServerReq *> all;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    int *h_yield = nullptr, *d_yield = nullptr;
+    BatchItem *d_items = nullptr;
+    int items_cap = 0;
+    int64_t launches = 0;
+
+    void finish(ServerReq *r, int status, const char *msg)
+    {
+        r->status = status;
+        if (msg) r->msg = msg;
+        r->t_done = now_s();
+        if (r->res) r->res->solve_ms = (r->t_done - r->t_submit) * 1e3;
+    }
+
+    // Admission: uploads queued requests while a slot and memory are free.
+    void admit()
+    {
+        std::vector<ServerReq *> in;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            while (!queue.empty() && (int)(active.size() + in.size()) < o.slots) {
+                ServerReq *r = queue.front();
+                if (r->footprint > budget) {
+                    queue.pop_front();
+                    finish(r, MH_EREJECT, "request needs more device memory than the server budget");
+                    cv.notify_all();
+                    continue;
+                }
+                if (in_use + r->footprint > budget && !(active.empty() && in.empty())) break;
+                queue.pop_front();
+                in_use += r->footprint;
+                in.push_back(r);
+            }
+        }
+        for (ServerReq *r : in) {
+            int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st, &r->H);
+            int maxr = 0;
+            if (rc == MH_OK) rc = prepare_solve(r->H, &r->opts, &r->s, &maxr);
+            if (rc == MH_OK) {
+                r->bm.clear();
+                r->bm.shrink_to_fit();
+                launch_solve_init(r->H->c, r->s, r->H->ws_rounds, maxr, r->H->dCounts, st);
+                if (r->Nt == 0) {
+                    const int one = 1;
+                    cudaMemcpyAsync(r->H->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+                }
+                cudaStreamSynchronize(st);
+            }
+            std::lock_guard<std::mutex> lock(mu);
+            if (rc != MH_OK) {
+                if (r->H) mh_destroy(r->H);
+                r->H = nullptr;
+                in_use -= r->footprint;
+                finish(r, rc, mh_last_error());
+                cv.notify_all();
+            } else {
+                active.push_back(r);
+            }
+        }
+    }
+
+    // Retires finished requests; grows overflowed frontiers.  Returns false on a
+    // device error (every active request then fails).
+    bool retire()
+    {
+        std::vector<ServerReq *> keep;
+        for (ServerReq *r : active) {
+            mh_handle *H = r->H;
+            int st8[kStateWords];
+            cudaMemcpy(st8, H->dState, sizeof st8, cudaMemcpyDeviceToHost);
+            int rc = MH_OK;
+            if (st8[2]) rc = fail(MH_ETIMEOUT, "a team barrier of the served solve timed out");
+            if (rc == MH_OK && st8[3]) {
+                std::vector<u32> hc(kCountWords);
+                cudaMemcpy(hc.data(), H->dCounts, sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost);
+                rc = grow_overflowed(H, r->opts.h, hc.data());
+                if (rc == MH_OK) {
+                    cudaMemsetAsync(H->dCnt + (size_t)st8[4] * r->opts.h * 2, 0, sizeof(u64) * 2 * r->opts.h, st);
+                    cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountWords, st);
+                    cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st);
+                    cudaStreamSynchronize(st);
+                    keep.push_back(r);
+                    continue;
+                }
+            }
+            if (rc == MH_OK && !st8[1]) {
+                keep.push_back(r);
+                continue;
+            }
+            if (rc == MH_OK) rc = collect_result(H, r->opts.h, true, 0.0, nullptr, 1, 0, &r->res);
+            mh_destroy(H);
+            r->H = nullptr;
+            std::lock_guard<std::mutex> lock(mu);
+            in_use -= r->footprint;
+            finish(r, rc, rc == MH_OK ? nullptr : mh_last_error());
+            cv.notify_all();
+        }
+        std::lock_guard<std::mutex> lock(mu);
+        active.swap(keep);
+        return true;
+    }
+
+    void run_active()
+    {
+        const int n = (int)active.size();
+        std::vector<double> work(n);
+        for (int i = 0; i < n; ++i) work[i] = work_estimate(active[i]->H, active[i]->opts.h - 1);
+        const std::vector<int> blocks = split_blocks(work, 0.75, grid);
+        if (items_cap < n) {
+            cudaFree(d_items);
+            d_items = nullptr;
+            items_cap = 0;
+            if (cudaMalloc((void **)&d_items, sizeof(BatchItem) * (size_t)n) != cudaSuccess) return;
+            items_cap = n;
+        }
+        std::vector<BatchItem> items(n);
+        int first = 0;
+        for (int i = 0; i < n; ++i) {
+            mh_handle *H = active[i]->H;
+            items[i].c = H->c;
+            items[i].s = active[i]->s;
+            items[i].f = frontiers_of(H);
+            items[i].gsync = H->dSync;
+            items[i].counts = H->dCounts;
+            items[i].first_block = first;
+            items[i].nblocks = blocks[i];
+            first += blocks[i];
+            cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st);
+            cudaMemsetAsync(H->dState + 6, 0, sizeof(int), st);
+        }
+        *(volatile int *)h_yield = 0;
+        cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
+        cudaEvent_t ev;
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (launch_solve_batch(d_items, n, d_yield, first, st) != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return;
+        }
+        ++launches;
+        cudaEventRecord(ev, st);
+        // while the launch runs, ask it to yield when a queued request could start
+        while (cudaEventQuery(ev) == cudaErrorNotReady) {
+            bool want = false;
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                want = !queue.empty() && (int)active.size() < o.slots;
+            }
+            if (want) *(volatile int *)h_yield = 1;
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        }
+        cudaEventDestroy(ev);
+    }
+
+    int dev = 0;
+
+    void loop()
+    {
+        cudaSetDevice(dev);  // the current device is per host thread
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                cv.wait(lock, [&] { return stop || !queue.empty() || !active.empty(); });
+                if (stop && queue.empty() && active.empty()) return;
+            }
+            admit();
+            if (active.empty()) continue;
+            run_active();
+            retire();
+        }
+    }
+};
+
+extern "C" {
+
+MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
+{
+    if (!out) return fail(MH_EINVAL, "out is NULL");
+    *out = nullptr;
+    mh_server *S = new (std::nothrow) mh_server();
+    if (!S) return fail(MH_ENOMEM, "host allocation of the server failed");
+    if (opts) S->o = *opts;
+    if (S->o.slots <= 0) S->o.slots = 8;
+    int dev = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    S->dev = dev;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&S->h_yield, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&S->d_yield, S->h_yield, 0);
+    if (e != cudaSuccess) {
+        delete S;
+        return fail(MH_ECUDA, "mh_server_create: %s", cudaGetErrorString(e));
+    }
+    S->grid = persistent_grid(S->num_sms);
+    if (S->o.slots > S->grid) S->o.slots = S->grid;
+    if (S->o.hbm_budget_bytes > 0) {
+        S->budget = S->o.hbm_budget_bytes;
+    } else {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        S->budget = (int64_t)(free_b * 0.8);
+    }
+    S->th = std::thread([S] { S->loop(); });
+    *out = S;
+    return MH_OK;
+}
+
+MH_API int mh_submit(mh_server *S, const uint64_t *bitmaps, int32_t G, int32_t Nt, int32_t Nn, int32_t h,
+                     mh_rational alpha, uint64_t *ticket)
+{
+    if (!S || !ticket) return fail(MH_EINVAL, "server or ticket is NULL");
+    int rc = validate_dims(G, Nt, Nn);
+    if (rc) return rc;
+    if (!bitmaps) return fail(MH_EINVAL, "bitmaps is NULL");
+    if (h < 1 || h > kMaxH) return fail(MH_EINVAL, "h=%d outside [1, %d]", h, kMaxH);
+    if (alpha.num < 0 || alpha.den <= 0) return fail(MH_EINVAL, "alpha=%d/%d", alpha.num, alpha.den);
+    ServerReq *r = new (std::nothrow) ServerReq();
+    if (!r) return fail(MH_ENOMEM, "host allocation of the request failed");
+    const size_t words = (size_t)G * (size_t)((Nt + 63) / 64 + (Nn + 63) / 64);
+    r->bm.assign(bitmaps, bitmaps + words);
+    r->G = G;
+    r->Nt = Nt;
+    r->Nn = Nn;
+    r->opts.h = h;
+    r->opts.alpha = alpha;
+    r->opts.mode = MH_MODE_PERSISTENT;
+    r->footprint = estimate_footprint(bitmaps, G, Nt, Nn, h);
+    r->t_submit = now_s();
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stop) {
+        delete r;
+        return fail(MH_EINVAL, "the server is shutting down");
+    }
+    r->ticket = S->next_ticket++;
+    S->all[r->ticket] = r;
+    S->queue.push_back(r);
+    *ticket = r->ticket;
+    S->cv.notify_all();
+    return MH_OK;
+}
+
+static int take_result(mh_server *S, std::map<uint64_t, ServerReq *>::iterator it, mh_result **out)
+{
+    ServerReq *r = it->second;
+    const int st = r->status;
+    if (st == MH_OK) {
+        *out = r->res;
+        r->res = nullptr;
+    } else {
+        fail(st, "%s", r->msg.c_str());
+    }
+    S->all.erase(it);
+    delete r;
+    return st;
+}
+
+MH_API int mh_poll(mh_server *S, uint64_t ticket, mh_result **out)
+{
+    if (!S || !out) return fail(MH_EINVAL, "server or out is NULL");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(MH_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    if (it->second->status < 0) return MH_EAGAIN;
+    return take_result(S, it, out);
+}
+
+MH_API int mh_wait(mh_server *S, uint64_t ticket, int32_t timeout_ms, mh_result **out)
+{
+    if (!S || !out) return fail(MH_EINVAL, "server or out is NULL");
+    *out = nullptr;
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(MH_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    ServerReq *r = it->second;
+    auto ready = [&] { return r->status >= 0; };
+    if (timeout_ms < 0) S->cv.wait(lock, ready);
+    else if (!S->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), ready)) return MH_EAGAIN;
+    return take_result(S, S->all.find(ticket), out);
+}
+
+MH_API int mh_server_stats(mh_server *S, int64_t *launches, int32_t *queued, int32_t *active, int64_t *bytes_in_use)
+{
+    if (!S) return fail(MH_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (launches) *launches = S->launches;
+    if (queued) *queued = (int32_t)S->queue.size();
+    if (active) *active = (int32_t)S->active.size();
+    if (bytes_in_use) *bytes_in_use = S->in_use;
+    return MH_OK;
+}
+
+MH_API void mh_server_destroy(mh_server *S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    for (auto &kv : S->all) {
+        if (kv.second->res) mh_result_free(kv.second->res);
+        delete kv.second;
+    }
+    cudaFree(S->d_items);
+    if (S->h_yield) cudaFreeHost(S->h_yield);
+    if (S->st) cudaStreamDestroy(S->st);
+    delete S;
+}
+
+}  // extern "C"

@@ -1093,8 +1093,12 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
             // batch: a team that finished asks the others to stop after their current
             // round, so that the host can hand its blocks to the unfinished cohorts
             if (yield && threadIdx.x == 0) {
-                if (*(volatile int *)&s.state[kStDone]) atomicExch(yield, 1);
-                else if (*(volatile int *)yield) s.state[kStYield] = 1;
+                if (*(volatile int *)&s.state[kStDone]) {
+                    *(volatile int *)yield = 1;  // may be host memory: a plain store, made visible
+                    __threadfence_system();
+                } else if (*(volatile int *)yield) {
+                    s.state[kStYield] = 1;
+                }
             }
         }
         if (!grid_sync(gsync, s.state, t.size)) return;

@@ -274,3 +274,79 @@ def mh_solve_batch(handles, hs, alphas=None, blocks=None, prune: int = MH_PRUNE_
     outs = (ctypes.POINTER(mh_result) * n)()
     _check(lib.mh_solve_batch(ptrs, opts, n, b, outs))
     return [_to_result(outs[i]) for i in range(n)]
+
+
+class mh_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32)]
+
+
+class Server:
+    """Served runtime (continuous batching): mh_server_create / mh_submit /
+    mh_poll / mh_wait / mh_server_destroy."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 0):
+        lib = load()
+        if not hasattr(lib, "_server_typed"):
+            lib.mh_server_create.restype = ctypes.c_int
+            lib.mh_server_create.argtypes = [ctypes.POINTER(mh_server_opts), ctypes.POINTER(_P)]
+            lib.mh_submit.restype = ctypes.c_int
+            lib.mh_submit.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      mh_rational, ctypes.POINTER(ctypes.c_uint64)]
+            lib.mh_poll.restype = ctypes.c_int
+            lib.mh_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.POINTER(mh_result))]
+            lib.mh_wait.restype = ctypes.c_int
+            lib.mh_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(mh_result))]
+            lib.mh_server_stats.restype = ctypes.c_int
+            lib.mh_server_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+            lib.mh_server_destroy.restype = None
+            lib.mh_server_destroy.argtypes = [_P]
+            lib._server_typed = True
+        self.ptr = _P()
+        o = mh_server_opts(hbm_budget_bytes, slots)
+        _check(lib.mh_server_create(ctypes.byref(o), ctypes.byref(self.ptr)))
+
+    def submit(self, bitmaps, G, Nt, Nn, h, alpha=(1, 10)) -> int:
+        bm = np.ascontiguousarray(bitmaps, dtype=np.uint64)
+        t = ctypes.c_uint64()
+        _check(load().mh_submit(self.ptr, bm.ctypes.data, G, Nt, Nn, h, mh_rational(*alpha), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket):
+        """Result if finished, None while queued or running."""
+        p = ctypes.POINTER(mh_result)()
+        rc = load().mh_poll(self.ptr, ticket, ctypes.byref(p))
+        if rc == MH_EAGAIN:
+            return None
+        _check(rc)
+        return _to_result(p)
+
+    def wait(self, ticket, timeout_ms: int = -1):
+        p = ctypes.POINTER(mh_result)()
+        rc = load().mh_wait(self.ptr, ticket, timeout_ms, ctypes.byref(p))
+        if rc == MH_EAGAIN:
+            return None
+        _check(rc)
+        return _to_result(p)
+
+    def stats(self):
+        a, q, b, m = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().mh_server_stats(self.ptr, ctypes.byref(a), ctypes.byref(q), ctypes.byref(b), ctypes.byref(m)))
+        return {"launches": a.value, "queued": q.value, "active": b.value, "bytes_in_use": m.value}
+
+    def close(self):
+        if self.ptr:
+            load().mh_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
