@@ -374,6 +374,83 @@ def run_batch16(args):
     return 0
 
 
+def run_served(args):
+    """Served workload: a trace of requests (c3-law cohorts, Poisson arrivals at 5/s,
+    h from {2: .3, 3: .5, 4: .2}) replayed in real time against (i) the served
+    runtime (continuous batching) and (ii) a plain FIFO loop of one solve (one
+    persistent launch) per request; latency = arrival to result."""
+    import threading
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_2603_16721_gb300 import mh
+    specs, gaps = synth.served200()
+    n = min(args.requests, len(specs))
+    specs = specs[:n]
+    arrivals = np.cumsum(gaps[:n]) - gaps[0]
+    cohorts = [synth.generate(sp) for sp in specs]
+    torch.cuda.synchronize()
+    # warm-up: one request of each h, both paths
+    for h in (2, 3, 4):
+        c = next(c for c, sp in zip(cohorts, specs) if sp.h == h)
+        with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
+            mh.mh_solve(H, h)
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+    # (ii) plain FIFO loop
+    plain_res, plain_lat, service = [], [], []
+    t0 = time.perf_counter()
+    for i, (c, sp) in enumerate(zip(cohorts, specs)):
+        now = time.perf_counter() - t0
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        ts = time.perf_counter()
+        with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
+            plain_res.append(mh.mh_solve(H, sp.h))
+        te = time.perf_counter()
+        service.append(te - ts)
+        plain_lat.append(te - t0 - arrivals[i])
+    plain_span = time.perf_counter() - t0
+
+    # (i) served: requests submitted at their arrival times
+    with mh.Server(slots=args.slots) as S:
+        tickets = [None] * n
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, (c, sp) in enumerate(zip(cohorts, specs)):
+                now = time.perf_counter() - t0
+                if now < arrivals[i]:
+                    time.sleep(arrivals[i] - now)
+                tickets[i] = S.submit(c.bitmaps, c.G, c.Nt, c.Nn, sp.h)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        served_res = [S.wait(t) for t in tickets]
+        served_span = time.perf_counter() - t0
+        stats = S.stats()
+    served_lat = [r.solve_ms / 1e3 for r in served_res]
+    same = all(a.records() == b.records() for a, b in zip(plain_res, served_res))
+    mean_service = sum(service) / n
+    print(json.dumps({
+        "metric": "served_wsc_solves_per_s", "value": n / served_span, "unit": "solves/s",
+        "p50_ms": 1e3 * pct(served_lat, 0.50), "p99_ms": 1e3 * pct(served_lat, 0.99),
+        "plain": {"value": n / plain_span, "p50_ms": 1e3 * pct(plain_lat, 0.50), "p99_ms": 1e3 * pct(plain_lat, 0.99),
+                  "mean_service_ms": 1e3 * mean_service, "capacity_solves_per_s": 1.0 / mean_service},
+        "offered_load_req_per_s": n / max(arrivals[-1], 1e-9), "requests": n, "slots": args.slots,
+        "identical_to_plain": same, "server_launches": stats["launches"],
+        "config": {"workload": f"served: first {n} of 200 requests, c3-law cohorts (G=19000, Nt=800, Nn=400), "
+                               "seeds 1000-1199, Poisson 5 req/s, h from {2:.3,3:.5,4:.2}, trace seed 5000"},
+    }))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,13 +461,18 @@ def main(argv=None):
     ap.add_argument("--kernels-only", action="store_true", help="time the solves only (profiling runs)")
     ap.add_argument("--mode", choices=["persistent", "launches"], default="persistent",
                     help="one persistent kernel per solve, or one launch per phase")
-    ap.add_argument("--workload", choices=["c2", "batch16"], default="c2",
-                    help="c2: the headline single-cohort solve; batch16: the batched workload")
+    ap.add_argument("--workload", choices=["c2", "batch16", "served200"], default="c2",
+                    help="c2: the headline single-cohort solve; batch16: the batched workload; "
+                         "served200: the served request trace")
+    ap.add_argument("--requests", type=int, default=200, help="served200: requests replayed")
+    ap.add_argument("--slots", type=int, default=8, help="served200: concurrent requests")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch16":
         return run_batch16(args)
+    if args.workload == "served200":
+        return run_served(args)
     return run_ours(args)
 
 
