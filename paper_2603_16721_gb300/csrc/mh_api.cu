@@ -52,8 +52,8 @@ int fail(int code, const char *fmt, ...)
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
     } while (0)
 
-constexpr size_t kFrontierBudgetDefault = size_t(16) << 30;  // bytes for all frontiers of a handle
-
+// Frontier memory of one handle: MH_FRONTIER_BUDGET_MB if set, else 80% of the
+// device memory that is free when a frontier grows.
 size_t frontier_budget()
 {
     const char *v = getenv("MH_FRONTIER_BUDGET_MB");
@@ -61,7 +61,9 @@ size_t frontier_budget()
         const long long mb = atoll(v);
         if (mb > 0) return size_t(mb) << 20;
     }
-    return kFrontierBudgetDefault;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return size_t(16) << 30;
+    return (size_t)(free_b * 0.8);
 }
 
 template <typename T>
@@ -223,7 +225,10 @@ int ensure_frontier(mh_handle *H, int l, u64 n)
     if (want > 0xffffffffull / kShards) want = 0xffffffffull / kShards;
     const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)sizeof(Rec);
     const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
-    if ((size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget() || n > want)
+    const char *fixed = getenv("MH_FRONTIER_BUDGET_MB");
+    const bool over = (fixed && *fixed) ? (size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget()
+                                        : (size_t)(new_bytes - old_bytes) > frontier_budget();
+    if (over || n > want)
         return fail(MH_ENOMEM, "depth-%d frontier needs %llu records per shard (%.1f GB), above the frontier budget",
                     l, (unsigned long long)n, (double)n * kShards * sizeof(Rec) / 1e9);
     MH_CUDA(cudaStreamSynchronize(H->stream));
