@@ -162,7 +162,7 @@ int build_store(mh_handle *H, const uint64_t *bm)
     c.G = G; c.Nt = Nt; c.Nn = Nn; c.Wt = Wt; c.Wn = Wn;
     c.WTp = std::max(2, (Wt + 1) & ~1);
     c.WNp = std::max(2, (Wn + 1) & ~1);
-    c.GW = column_words(G);
+    c.GW = std::max(2, (((G + 63) / 64) + 1) & ~1);
 
     std::vector<u64> T((size_t)G * c.WTp, 0), N((size_t)G * c.WNp, 0);
     std::vector<u16> orig(G);

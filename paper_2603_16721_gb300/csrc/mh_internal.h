@@ -21,8 +21,6 @@ constexpr int kMaxWarpsPerBlock = 32;
 constexpr int kErrTimeout = 4;     // same value as MH_ETIMEOUT
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kCountStride = 16;   // u32 slots per counter array (>= kMaxH + 1)
-constexpr int kItemWords = 8;      // column words per sibling-test item (columns are padded to a multiple)
-__host__ __device__ constexpr int column_words(int G) { return ((G + 63) / 64 + kItemWords - 1) / kItemWords * kItemWords; }
 // Frontier appends are spread over kShards counters, each in its own 128-byte
 // line, so that thousands of warps do not serialise on one atomic: depth l,
 // shard i counts the records of region i of the depth-l frontier
@@ -37,7 +35,7 @@ struct Cohort {
     int G, Nt, Nn;
     int Wt, Wn;     // words holding Nt / Nn bits
     int WTp, WNp;   // row strides in words (even: 16-byte aligned rows)
-    int GW;         // words of one sample-major column over the G sorted genes (a multiple of kItemWords)
+    int GW;         // words of one sample-major column over the G sorted genes (even)
     const u64 *T;   // G x WTp   tumor rows, gene-major
     const u64 *N;   // G x WNp   normal rows, gene-major
     const u64 *CT;  // Nt x GW   tumor bits, sample-major: bit g of column s = T[g] bit s

@@ -318,9 +318,8 @@ __device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 cap_s, u64 firs
     const bool live = valid && hi >= lo;
     const bool dense = live && is_dense(ky, kn);
     dense_mask = __ballot_sync(kFull, dense);
-    // items of kItemWords column words (aligned), from the one holding lo
-    const int nw = (live && !dense && (ky > 0 || all_children))
-                       ? ((hi >> 6) / kItemWords - (lo >> 6) / kItemWords + 1) : 0;
+    // items of two column words (one 16-byte load per sample) from the even word at or below lo
+    const int nw = (live && !dense && (ky > 0 || all_children)) ? ((hi >> 7) - (lo >> 7) + 1) : 0;
     const int incl = warp_incl_scan(nw, lane);
     b.off[lane] = incl - nw;
     if (lane == 31) b.off[kBatch] = incl;
@@ -348,41 +347,48 @@ __device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, con
     __syncwarp();
 }
 
-// Sibling masks of item t of a batch: kItemWords consecutive column words w0..
-// (w0 a multiple of kItemWords) of one record, read with 16-byte loads; each
-// sample's column contributes one OR per word.  j is the lane's running record
-// index (items are visited in increasing order).
-__device__ __forceinline__ void sibling_item(const Cohort &c, const Batch &b, int t, int total, int &j, int &w0,
-                                             int &ky, u64 (&m)[kItemWords])
+// Sibling masks of the items t0, t0+32, ... (kIlp of them) of a batch; an item is
+// the pair of column words wi, wi+1 (wi even) of one record, read with one
+// 16-byte load per sample, and the loads of all items are issued together.  j is
+// the lane's running record index (items are visited in increasing order).
+constexpr int kIlp = 2;
+__device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, int t0, int total, int &j,
+                                              int (&jj)[kIlp], int (&wi)[kIlp], int (&ky)[kIlp], u64 (&m)[kIlp][2],
+                                              u64 (&rw)[kIlp][2])
 {
+    int kmax = 0;
 #pragma unroll
-    for (int i = 0; i < kItemWords; ++i) m[i] = 0;
-    ky = 0;
-    w0 = 0;
-    if (t >= total) return;
-    while (t >= b.off[j + 1]) ++j;
-    const int lo = b.lo[j], hi = b.hi[j];
-    w0 = ((lo >> 6) / kItemWords + (t - b.off[j])) * kItemWords;
-    ky = b.r[j].ky;
-    const u16 *ids = b.r[j].ids;
-    for (int q = 0; q < ky; ++q) {
-        const ulonglong2 *col = reinterpret_cast<const ulonglong2 *>(c.CT + (size_t)ids[q] * c.GW + w0);
+    for (int u = 0; u < kIlp; ++u) {
+        const int t = t0 + 32 * u;
+        ky[u] = 0;
+        wi[u] = 0;
+        rw[u][0] = rw[u][1] = 0;
+        m[u][0] = m[u][1] = 0;
+        if (t < total) {
+            while (t >= b.off[j + 1]) ++j;
+            wi[u] = ((b.lo[j] >> 6) & ~1) + 2 * (t - b.off[j]);
+            ky[u] = b.r[j].ky;
+            rw[u][0] = range_word(wi[u], b.lo[j], b.hi[j]);
+            rw[u][1] = range_word(wi[u] + 1, b.lo[j], b.hi[j]);
+        }
+        jj[u] = j;
+        kmax = ky[u] > kmax ? ky[u] : kmax;
+    }
+    for (int q = 0; q < kmax; ++q) {
 #pragma unroll
-        for (int i = 0; i < kItemWords / 2; ++i) {
-            const ulonglong2 x = col[i];
-            m[2 * i] |= x.x;
-            m[2 * i + 1] |= x.y;
+        for (int u = 0; u < kIlp; ++u) {
+            if (q < ky[u]) {
+                const ulonglong2 x =
+                    *reinterpret_cast<const ulonglong2 *>(c.CT + (size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]);
+                m[u][0] |= x.x;
+                m[u][1] |= x.y;
+            }
         }
     }
-    const int wlo = lo >> 6, whi = hi >> 6;
 #pragma unroll
-    for (int i = 0; i < kItemWords; ++i) {
-        const int w = w0 + i;
-        if (w < wlo || w > whi) m[i] = 0;
-        else {
-            if (w == wlo) m[i] &= ~0ull << (lo & 63);
-            if (w == whi) m[i] &= ~0ull >> (63 - (hi & 63));
-        }
+    for (int u = 0; u < kIlp; ++u) {
+        m[u][0] &= rw[u][0];
+        m[u][1] &= rw[u][1];
     }
 }
 
@@ -645,35 +651,23 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
                                         dense, visited);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
-        for (int tb = 0; tb < total; tb += 32) {
-            int w0, ky;
-            u64 m[kItemWords];
-            sibling_item(c, b, tb + lane, total, j, w0, ky, m);
-            int nall = 0;
-#pragma unroll
-            for (int i = 0; i < kItemWords; ++i) {
-                alive += (u64)__popcll(m[i]);
-                if (all_children && tb + lane < total) {  // every child of the range, empty or not
-                    const int w = w0 + i, wlo = b.lo[j] >> 6, whi = b.hi[j] >> 6;
-                    u64 r = (w < wlo || w > whi) ? 0ull : ~0ull;
-                    if (w == wlo) r &= ~0ull << (b.lo[j] & 63);
-                    if (w == whi) r &= ~0ull >> (63 - (b.hi[j] & 63));
-                    m[i] = r;
-                }
-                nall += __popcll(m[i]);
-            }
-            if (!__any_sync(kFull, nall != 0)) continue;
+        for (int tb = 0; tb < total; tb += 32 * kIlp) {
+            int jj[kIlp], wi[kIlp], ky[kIlp];
+            u64 m[kIlp][2], rw[kIlp][2];
+            sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
             // spread the children of each column word over all lanes: lane i builds
             // children i, i+32, ... of the warp, whichever lane's word they came from
 #pragma unroll
-            for (int i = 0; i < kItemWords; ++i) {
-                const u64 mv = m[i];
+            for (int v = 0; v < 2 * kIlp; ++v) {
+                const int u = v >> 1, hw = v & 1;
+                alive += (u64)__popcll(m[u][hw]);
+                const u64 mv = all_children ? rw[u][hw] : m[u][hw];
                 const int n = __popcll(mv);
                 const int incl = warp_incl_scan(n, lane);
                 const int tot = __shfl_sync(kFull, incl, 31);
                 if (tot == 0) continue;
                 b.ys[lane] = mv;
-                b.ns[lane] = ((u64)(u32)j << 32) | (u32)(w0 + i);
+                b.ns[lane] = ((u64)(u32)jj[u] << 32) | (u32)(wi[u] + hw);
                 b.cx[lane] = incl - n;
                 if (lane == 31) b.cx[32] = incl;
                 u32 base = 0;
@@ -783,18 +777,21 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
         if (lane == 0) thr = *(volatile u64 *)s.best_hint;
         thr = warp_max_u64(thr > best.s ? thr : best.s);
         int j = 0;
-        for (int t = lane; t < total; t += 32) {
-            int w0, ky;
-            u64 m[kItemWords];
-            sibling_item(c, b, t, total, j, w0, ky, m);
-            words += (u64)(kItemWords * ky);
-            const bool bound = s.a_num * (u64)ky + nn_term >= thr;
+        for (int tb = 0; tb < total; tb += 32 * kIlp) {
+            int jj[kIlp], wi[kIlp], ky[kIlp];
+            u64 m[kIlp][2], rw[kIlp][2];
+            sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
 #pragma unroll
-            for (int i = 0; i < kItemWords; ++i) {
-                alive += (u64)__popcll(m[i]);
-                if (m[i] && bound) {
-                    scored += (u64)score_item(c, s, b, j, w0 + i, m[i], L, thr, best);
-                    words += (u64)(ky + b.r[j].kn);
+            for (int u = 0; u < kIlp; ++u) {
+                words += 2ull * (u64)ky[u];
+                const bool bound = s.a_num * (u64)ky[u] + nn_term >= thr;
+#pragma unroll
+                for (int hw = 0; hw < 2; ++hw) {
+                    alive += (u64)__popcll(m[u][hw]);
+                    if (m[u][hw] && bound) {
+                        scored += (u64)score_item(c, s, b, jj[u], wi[u] + hw, m[u][hw], L, thr, best);
+                        words += (u64)(ky[u] + b.r[jj[u]].kn);
+                    }
                 }
             }
         }

@@ -217,7 +217,8 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     if (c.WTp < 2) c.WTp = 2;
     c.WNp = (c.Wn + 1) & ~1;
     if (c.WNp < 2) c.WNp = 2;
-    c.GW = column_words(G);
+    c.GW = (((G + 63) / 64) + 1) & ~1;
+    if (c.GW < 2) c.GW = 2;
     u64 *T = (u64 *)(base + kOffT);
     u64 *N = (u64 *)(base + kOffN);
     u64 *CT = (u64 *)(base + kOffCT);
