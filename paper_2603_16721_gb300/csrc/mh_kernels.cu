@@ -165,7 +165,6 @@ __device__ void block_commit_best(Key best, Key *slots, int rank)
 
 __device__ __forceinline__ u64 range_word(int wi, int lo, int hi)
 {
-    if (wi < (lo >> 6) || wi > (hi >> 6)) return 0;
     u64 m = ~0ull;
     if (wi == (lo >> 6)) m &= ~0ull << (lo & 63);
     if (wi == (hi >> 6)) m &= ~0ull >> (63 - (hi & 63));
@@ -318,8 +317,7 @@ __device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 cap_s, u64 firs
     const bool live = valid && hi >= lo;
     const bool dense = live && is_dense(ky, kn);
     dense_mask = __ballot_sync(kFull, dense);
-    // items of two column words (one 16-byte load per sample) from the even word at or below lo
-    const int nw = (live && !dense && (ky > 0 || all_children)) ? ((hi >> 7) - (lo >> 7) + 1) : 0;
+    const int nw = (live && !dense && (ky > 0 || all_children)) ? (hi >> 6) - (lo >> 6) + 1 : 0;
     const int incl = warp_incl_scan(nw, lane);
     b.off[lane] = incl - nw;
     if (lane == 31) b.off[kBatch] = incl;
@@ -347,14 +345,13 @@ __device__ __forceinline__ void dense_setup(const Cohort &c, const Solve &s, con
     __syncwarp();
 }
 
-// Sibling masks of the items t0, t0+32, ... (kIlp of them) of a batch; an item is
-// the pair of column words wi, wi+1 (wi even) of one record, read with one
-// 16-byte load per sample, and the loads of all items are issued together.  j is
-// the lane's running record index (items are visited in increasing order).
-constexpr int kIlp = 2;
+// Sibling masks of the items t0, t0+32, ... (kIlp of them) of a batch: the
+// column loads of all of them are issued together.  j is the lane's running
+// record index (items are visited in increasing order).
+constexpr int kIlp = 4;
 __device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, int t0, int total, int &j,
-                                              int (&jj)[kIlp], int (&wi)[kIlp], int (&ky)[kIlp], u64 (&m)[kIlp][2],
-                                              u64 (&rw)[kIlp][2])
+                                              int (&jj)[kIlp], int (&wi)[kIlp], int (&ky)[kIlp], u64 (&m)[kIlp],
+                                              u64 (&rw)[kIlp])
 {
     int kmax = 0;
 #pragma unroll
@@ -362,34 +359,24 @@ __device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, i
         const int t = t0 + 32 * u;
         ky[u] = 0;
         wi[u] = 0;
-        rw[u][0] = rw[u][1] = 0;
-        m[u][0] = m[u][1] = 0;
+        rw[u] = 0;
+        m[u] = 0;
         if (t < total) {
             while (t >= b.off[j + 1]) ++j;
-            wi[u] = ((b.lo[j] >> 6) & ~1) + 2 * (t - b.off[j]);
+            wi[u] = (b.lo[j] >> 6) + (t - b.off[j]);
             ky[u] = b.r[j].ky;
-            rw[u][0] = range_word(wi[u], b.lo[j], b.hi[j]);
-            rw[u][1] = range_word(wi[u] + 1, b.lo[j], b.hi[j]);
+            rw[u] = range_word(wi[u], b.lo[j], b.hi[j]);
         }
         jj[u] = j;
         kmax = ky[u] > kmax ? ky[u] : kmax;
     }
     for (int q = 0; q < kmax; ++q) {
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-            if (q < ky[u]) {
-                const ulonglong2 x =
-                    *reinterpret_cast<const ulonglong2 *>(c.CT + (size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]);
-                m[u][0] |= x.x;
-                m[u][1] |= x.y;
-            }
-        }
+        for (int u = 0; u < kIlp; ++u)
+            if (q < ky[u]) m[u] |= c.CT[(size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]];
     }
 #pragma unroll
-    for (int u = 0; u < kIlp; ++u) {
-        m[u][0] &= rw[u][0];
-        m[u][1] &= rw[u][1];
-    }
+    for (int u = 0; u < kIlp; ++u) m[u] &= rw[u];
 }
 
 // Reserves n consecutive slots of the warp's shard for each lane with one atomic
@@ -653,21 +640,23 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
-            u64 m[kIlp][2], rw[kIlp][2];
+            u64 m[kIlp], rw[kIlp];
             sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
-            // spread the children of each column word over all lanes: lane i builds
-            // children i, i+32, ... of the warp, whichever lane's word they came from
 #pragma unroll
-            for (int v = 0; v < 2 * kIlp; ++v) {
-                const int u = v >> 1, hw = v & 1;
-                alive += (u64)__popcll(m[u][hw]);
-                const u64 mv = all_children ? rw[u][hw] : m[u][hw];
-                const int n = __popcll(mv);
+            for (int u = 0; u < kIlp; ++u) {
+                alive += (u64)__popcll(m[u]);
+                if (all_children) m[u] = rw[u];
+            }
+            // spread the children of each item round over all lanes: lane i builds
+            // children i, i+32, ... of the warp, whichever lane's item they came from
+#pragma unroll
+            for (int u = 0; u < kIlp; ++u) {
+                const int n = __popcll(m[u]);
                 const int incl = warp_incl_scan(n, lane);
                 const int tot = __shfl_sync(kFull, incl, 31);
                 if (tot == 0) continue;
-                b.ys[lane] = mv;
-                b.ns[lane] = ((u64)(u32)jj[u] << 32) | (u32)(wi[u] + hw);
+                b.ys[lane] = m[u];
+                b.ns[lane] = ((u64)(u32)jj[u] << 32) | (u32)wi[u];
                 b.cx[lane] = incl - n;
                 if (lane == 31) b.cx[32] = incl;
                 u32 base = 0;
@@ -779,19 +768,15 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
-            u64 m[kIlp][2], rw[kIlp][2];
+            u64 m[kIlp], rw[kIlp];
             sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
 #pragma unroll
             for (int u = 0; u < kIlp; ++u) {
-                words += 2ull * (u64)ky[u];
-                const bool bound = s.a_num * (u64)ky[u] + nn_term >= thr;
-#pragma unroll
-                for (int hw = 0; hw < 2; ++hw) {
-                    alive += (u64)__popcll(m[u][hw]);
-                    if (m[u][hw] && bound) {
-                        scored += (u64)score_item(c, s, b, jj[u], wi[u] + hw, m[u][hw], L, thr, best);
-                        words += (u64)(ky[u] + b.r[jj[u]].kn);
-                    }
+                alive += (u64)__popcll(m[u]);
+                words += (u64)ky[u];
+                if (m[u] && s.a_num * (u64)ky[u] + nn_term >= thr) {
+                    scored += (u64)score_item(c, s, b, jj[u], wi[u], m[u], L, thr, best);
+                    words += (u64)(ky[u] + b.r[jj[u]].kn);
                 }
             }
         }
