@@ -370,10 +370,16 @@ __device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, i
         jj[u] = j;
         kmax = ky[u] > kmax ? ky[u] : kmax;
     }
-    for (int q = 0; q < kmax; ++q) {
+    // two samples of every item per step: all their loads are in flight together
+    for (int q = 0; q < kmax; q += 2) {
+        u64 x0[kIlp], x1[kIlp];
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u)
-            if (q < ky[u]) m[u] |= c.CT[(size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]];
+        for (int u = 0; u < kIlp; ++u) {
+            x0[u] = q < ky[u] ? __ldg(c.CT + (size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]) : 0ull;
+            x1[u] = q + 1 < ky[u] ? __ldg(c.CT + (size_t)b.r[jj[u]].ids[q + 1] * c.GW + wi[u]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) m[u] |= x0[u] | x1[u];
     }
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) m[u] &= rw[u];
