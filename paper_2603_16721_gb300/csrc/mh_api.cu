@@ -263,7 +263,8 @@ int leaf_grid(const mh_handle *H) { return std::max(1, H->num_sms * 4); }
 int ensure_workspace(mh_handle *H, int h)
 {
     const int rounds = H->Nt + 2;
-    const int slots = std::max(std::max(level1_grid(H->c), leaf_grid(H)), persistent_grid(H->num_sms));
+    const int slots = std::max(std::max(level1_grid(H->c), leaf_grid(H)),
+                               std::max(persistent_grid(H->num_sms, true), batch_grid(H->num_sms)));
     int rc;
     if (!H->dU) {
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
@@ -272,7 +273,7 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dCounts, (size_t)kCountWords, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes))) return rc;
-        H->pgrid = H->coop ? persistent_grid(H->num_sms) : 0;
+        H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
         MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountWords)));
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
@@ -306,6 +307,8 @@ struct EventPair {
 }  // namespace
 
 namespace {
+
+double work_estimate(const mh_handle *H, int d);
 
 // Validates the options, sizes the workspace and fills the device view of a solve.
 int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_rounds)
@@ -537,6 +540,9 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, st);
     ++launches;
     const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
+    // large build for cohorts whose deepest frontier is expected to hold millions of prefixes
+    const bool large = work_estimate(H, h - 1) > 4.0e6;
+    const int pgrid = persistent_grid(H->num_sms, large);
     int rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
     if (persistent) {
@@ -549,7 +555,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 f.cap[l] = H->cap[l];
             }
             MH_CUDA(cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st));
-            MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, H->pgrid, st));
+            MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, pgrid, large, st));
             ++launches;
             MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
             MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountWords,
@@ -779,7 +785,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
               const std::vector<int> *fixed, double *ms)
 {
     cudaStream_t st = hs[0]->stream;
-    const int grid = persistent_grid(hs[0]->num_sms);
+    const int grid = batch_grid(hs[0]->num_sms);
     std::vector<Solve> ss(n);
     std::vector<int> maxr(n);
     for (int i = 0; i < n; ++i) {
@@ -881,7 +887,7 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         int rc = prepare_solve(handles[i], &opts[i], &tmp, &mr);
         if (rc) return rc;
     }
-    const int grid = persistent_grid(H0->num_sms);
+    const int grid = batch_grid(H0->num_sms);
     if (grid < n) return fail(MH_EINVAL, "mh_solve_batch: %d cohorts but only %d co-resident blocks", n, grid);
     std::vector<int> b(n);
     if (blocks) {
@@ -1211,7 +1217,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
         delete S;
         return fail(MH_ECUDA, "mh_server_create: %s", cudaGetErrorString(e));
     }
-    S->grid = persistent_grid(S->num_sms);
+    S->grid = batch_grid(S->num_sms);
     if (S->o.slots > S->grid) S->o.slots = S->grid;
     if (S->o.hbm_budget_bytes > 0) {
         S->budget = S->o.hbm_budget_bytes;

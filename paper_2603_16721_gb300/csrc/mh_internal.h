@@ -130,10 +130,12 @@ void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *count
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
 
 // Persistent solve: all rounds in one cooperative launch of `grid` blocks
-// (persistent_grid() = the co-resident maximum, 0 if it cannot be determined).
+// (persistent_grid(): one block per SM for a small cohort, the co-resident
+// maximum of the large build otherwise; 0 if it cannot be determined).
 // It returns when the solve is done, a frontier overflowed (state) or a grid
 // barrier timed out (state error = kErrTimeout).
-int persistent_grid(int num_sms);
+int persistent_grid(int num_sms, bool large);
+int batch_grid(int num_sms);
 
 // One cohort of a batched solve: its device state and its share of the grid
 // (blocks [first_block, first_block + nblocks)).
@@ -150,7 +152,7 @@ struct BatchItem {
 // finishes: every other team stops at its next round boundary.
 cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, int grid, cudaStream_t st);
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
-                                    u32 *counts, int grid, cudaStream_t st);
+                                    u32 *counts, int grid, bool large, cudaStream_t st);
 int level1_grid(const Cohort &c);
 
 // Message returned by mh_last_error() on the calling thread.

@@ -1112,7 +1112,12 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
+// Two builds of the persistent solve: one block per SM with registers to spare
+// (cheaper grid barriers: the small, latency-bound cohorts) and four blocks per SM
+// (more warps to hide memory latency: the large ones).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5]);
@@ -1120,7 +1125,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_solve(Cohort c, Solve s, Fronti
 
 // Batched solve: block b works on the cohort whose block range holds b, with the
 // blocks of that range as its team; cohorts progress independently.
-__global__ void __launch_bounds__(kThreads, 3) k_solve_batch(const BatchItem *items, int n, int *yield)
+__global__ void __launch_bounds__(kThreads, 4) k_solve_batch(const BatchItem *items, int n, int *yield)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     int lo = 0, hi = n - 1;  // last item with first_block <= blockIdx.x
@@ -1183,10 +1188,20 @@ void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t 
     k_finalize<<<1, kThreads, 0, st>>>(c, s, counts);
 }
 
-int persistent_grid(int num_sms)
+int persistent_grid(int num_sms, bool large)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kThreads, 0) != cudaSuccess) return 0;
+    const cudaError_t e = large
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<4>, kThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<1>, kThreads, 0);
+    if (e != cudaSuccess || per_sm < 1) return 0;
+    return (large ? per_sm : 1) * num_sms;
+}
+
+int batch_grid(int num_sms)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch, kThreads, 0) != cudaSuccess) return 0;
     return per_sm * num_sms;
 }
 
@@ -1200,13 +1215,14 @@ cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, in
 }
 
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
-                                    u32 *counts, int grid, cudaStream_t st)
+                                    u32 *counts, int grid, bool large, cudaStream_t st)
 {
     Cohort cc = c;
     Solve ss = s;
     Frontiers ff = f;
     void *args[] = {&cc, &ss, &ff, &gsync, &counts};
-    return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(kThreads), args, 0, st);
+    const void *fn = large ? (const void *)k_solve<4> : (const void *)k_solve<1>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
 }  // namespace mh
