@@ -105,9 +105,13 @@ struct mh_handle {
     int coop = 0, pgrid = 0;              // cooperative launch supported; persistent grid size
     std::vector<int> m_s;                 // mutated genes per tumor sample (work estimate of a batch)
     int64_t frontier_bytes = 0;
+    cudaEvent_t evk[2] = {};              // around each cooperative launch of a persistent solve
+    bool presized[kMaxH] = {};            // frontier of depth l sized from its bound
 
     ~mh_handle()
     {
+        for (int i = 0; i < 2; ++i)
+            if (evk[i]) cudaEventDestroy(evk[i]);
         cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dCN); cudaFree(dOrig); cudaFree(dInv);
         cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
         cudaFree(dSlots); cudaFree(dCand); cudaFree(dCounts); cudaFree(dSync);
@@ -217,11 +221,12 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
     return MH_OK;
 }
 
-// Grows the frontier of depth l to at least n records per shard (within the budget).
-int ensure_frontier(mh_handle *H, int l, u64 n)
+// Grows the frontier of depth l to at least n records per shard (within the budget),
+// with a quarter more room unless `exact`.
+int ensure_frontier(mh_handle *H, int l, u64 n, bool exact = false)
 {
     if (n <= H->cap[l]) return MH_OK;
-    u64 want = std::max<u64>(n + n / 4, 1u << 11);
+    u64 want = std::max<u64>(exact ? n : n + n / 4, 1u << 11);
     if (want > 0xffffffffull / kShards) want = 0xffffffffull / kShards;
     const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)sizeof(Rec);
     const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
@@ -310,6 +315,33 @@ namespace {
 
 double work_estimate(const mh_handle *H, int d);
 
+// Sizes the frontiers of depths 2..h-1 once per handle from a bound on their first
+// round: a non-empty depth-l prefix shares a tumor s, so it is one of the C(m_s, l)
+// l-sets of the genes mutated in s (m_s of them); at most sum_s C(m_s, l) records.
+// The shards fill unevenly, hence 15% more per shard.  A bound above half the
+// frontier budget is skipped (the frontier then grows when it overflows), and so is
+// everything with MH_FRONTIER_PRESIZE=0 (frontiers grown on overflow only).
+int presize_frontiers(mh_handle *H, int h)
+{
+    const char *v = getenv("MH_FRONTIER_PRESIZE");
+    if (v && v[0] == '0') return MH_OK;
+    for (int l = 2; l < h; ++l) {
+        if (H->presized[l]) continue;
+        H->presized[l] = true;
+        double e = 0.0;
+        for (int m : H->m_s) {
+            double comb = 1.0;
+            for (int i = 0; i < l; ++i) comb = comb * (double)(m - i) / (double)(i + 1);
+            if (m >= l) e += comb;
+        }
+        const double per_shard = e * 1.15 / kShards + 64.0;
+        if (per_shard * kShards * sizeof(Rec) > 0.5 * (double)frontier_budget()) continue;
+        const int rc = ensure_frontier(H, l, (u64)per_shard, true);
+        if (rc) return rc;
+    }
+    return MH_OK;
+}
+
 // Validates the options, sizes the workspace and fills the device view of a solve.
 int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_rounds)
 {
@@ -324,6 +356,7 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
         return fail(MH_EINVAL, "mode=%d is not an execution mode", opts->mode);
     int rc = ensure_workspace(H, h);
     if (rc) return rc;
+    if (opts->prune == MH_PRUNE_PAPER && (rc = presize_frontiers(H, h))) return rc;
     s->h = h;
     s->prune = opts->prune;
     s->a_num = (u64)opts->alpha.num;
@@ -355,7 +388,7 @@ Frontiers frontiers_of(const mh_handle *H)
 // Reads a finished solve back into a new mh_result.  kms: the four phase times
 // measured by the caller (used unless the persistent kernel measured them).
 int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const double *kms_in,
-                   int64_t launches, int64_t leaf_launches, mh_result **out)
+                   int64_t launches, int64_t leaf_launches, mh_result **out, double kernel_ms = 0.0)
 {
     cudaStream_t st = H->stream;
     int hs[kStateWords];
@@ -407,6 +440,7 @@ int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const 
         leaf_launches = h >= 2 ? rounds : 0;
     }
     R->solve_ms = solve_ms;
+    R->kernel_ms = persistent ? kernel_ms : (kms_in ? kms[0] + kms[1] + kms[2] + kms[3] : 0.0);
     R->leaf_ms = kms[2];
     R->level1_ms = kms[0];
     R->expand_ms = kms[1];
@@ -545,7 +579,10 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     const int pgrid = persistent_grid(H->num_sms, large);
     int rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
+    double kernel_ms = 0.0;  // the cooperative launches alone
     if (persistent) {
+        for (int i = 0; i < 2; ++i)
+            if (!H->evk[i]) MH_CUDA(cudaEventCreate(&H->evk[i]));
         // One cooperative launch runs every round; it returns early only when a
         // frontier overflowed (grown here, then the round is run again).
         while (!done) {
@@ -555,7 +592,9 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 f.cap[l] = H->cap[l];
             }
             MH_CUDA(cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st));
+            MH_CUDA(cudaEventRecord(H->evk[0], st));
             MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, pgrid, large, st));
+            MH_CUDA(cudaEventRecord(H->evk[1], st));
             ++launches;
             MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
             MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountWords,
@@ -564,6 +603,9 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
             const int *hs = H->hState;
             const u32 *hc = (const u32 *)(H->hState + kStateWords);
             rounds_done = hs[4];
+            float kx = 0.f;
+            cudaEventElapsedTime(&kx, H->evk[0], H->evk[1]);
+            kernel_ms += kx;
             if (hs[2]) {
                 destroy_events();
                 return fail(MH_ETIMEOUT, "a grid barrier of the persistent solve timed out in round %d", rounds_done);
@@ -665,7 +707,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     }
     destroy_events();
     const int64_t ll = opts->time_kernels && !persistent ? (h >= 2 ? timed : 0) : leaf_launches;
-    return collect_result(H, h, persistent, ms, kms, launches, ll, out);
+    return collect_result(H, h, persistent, ms, kms, launches, ll, out, kernel_ms);
 }
 
 }  // extern "C"
@@ -772,20 +814,43 @@ void tune_store(const std::string &sig, double gamma)
     for (auto &kv : g_tune) out << kv.first << " " << kv.second << "\n";
 }
 
-// Device copy of the batch descriptors (grown on demand, shared by all calls).
+// Device copy of the batch descriptors (grown on demand, shared by all calls),
+// followed by the yield flag, the block-numbering table and the start barrier.
 std::mutex g_items_mutex;
 BatchItem *g_items = nullptr;
 int g_items_cap = 0;
+
+size_t batch_ws_bytes(int n)
+{
+    return sizeof(BatchItem) * (size_t)n + 256 + sizeof(int) * kBatchTabInts + sizeof(GridSync);
+}
+
+BatchMap batch_map_at(BatchItem *items, int cap, int num_sms)
+{
+    char *base = (char *)items + sizeof(BatchItem) * (size_t)cap + 256;
+    return BatchMap{(int *)base, (GridSync *)(base + sizeof(int) * kBatchTabInts), batch_blocks_per_sm(), num_sms};
+}
+
+// Blocks per cohort of a batched launch: whole SMs (blocks ~ work^gamma rounded to
+// the blocks one SM holds) when there are no more cohorts than SMs.
+std::vector<int> split_grid(const std::vector<double> &work, double gamma, int num_sms)
+{
+    const int per_sm = batch_blocks_per_sm();
+    if ((int)work.size() > num_sms) return split_blocks(work, gamma, per_sm * num_sms);
+    std::vector<int> b = split_blocks(work, gamma, num_sms);
+    for (int &x : b) x *= per_sm;
+    return b;
+}
 
 // One batched run: all cohorts start from "nothing covered"; the grid is split
 // between the unfinished cohorts (blocks ~ work^gamma, or the fixed split) and,
 // each time a cohort finishes, the launch ends and the remaining cohorts share
 // the whole grid again.  *ms receives the run's time (CUDA events).
 int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, double gamma,
-              const std::vector<int> *fixed, double *ms)
+              const std::vector<int> *fixed, double *ms, int *sm_major = nullptr)
 {
+    if (sm_major) *sm_major = 1;
     cudaStream_t st = hs[0]->stream;
-    const int grid = batch_grid(hs[0]->num_sms);
     std::vector<Solve> ss(n);
     std::vector<int> maxr(n);
     for (int i = 0; i < n; ++i) {
@@ -802,10 +867,11 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         cudaFree(g_items);
         g_items = nullptr;
         g_items_cap = 0;
-        MH_CUDA(cudaMalloc((void **)&g_items, sizeof(BatchItem) * (size_t)n + 256));
+        MH_CUDA(cudaMalloc((void **)&g_items, batch_ws_bytes(n)));
         g_items_cap = n;
     }
     int *d_yield = (int *)((char *)g_items + sizeof(BatchItem) * (size_t)g_items_cap);
+    const BatchMap map = batch_map_at(g_items, g_items_cap, hs[0]->num_sms);
     std::vector<char> finished(n, 0);
     for (int i = 0; i < n; ++i) finished[i] = hs[i]->Nt == 0;
     for (;;) {
@@ -819,7 +885,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         } else {
             std::vector<double> w;
             for (int i : act) w.push_back(work[i]);
-            blocks = split_blocks(w, gamma, grid);
+            blocks = split_grid(w, gamma, hs[0]->num_sms);
         }
         std::vector<BatchItem> items(act.size());
         int first = 0;
@@ -838,8 +904,11 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         }
         MH_CUDA(cudaMemsetAsync(d_yield, 0, sizeof(int), st));
         MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st));
-        MH_CUDA(launch_solve_batch(g_items, (int)items.size(), act.size() > 1 ? d_yield : nullptr, first, st));
+        MH_CUDA(launch_solve_batch(g_items, (int)items.size(), act.size() > 1 ? d_yield : nullptr, map, st));
         MH_CUDA(cudaStreamSynchronize(st));
+        int fell_back = 0;  // the launch numbered its blocks by blockIdx.x
+        MH_CUDA(cudaMemcpy(&fell_back, map.tab + 2 * kMaxSmid + 1, sizeof(int), cudaMemcpyDeviceToHost));
+        if (fell_back && sm_major) *sm_major = 0;
         for (int i : act) {
             mh_handle *H = hs[i];
             MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
@@ -906,9 +975,9 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         work_l[i] = work_estimate(handles[i], opts[i].h);
     }
     double ms = 0.0;
-    int rc = MH_OK;
+    int rc = MH_OK, smm = 0;
     if (blocks) {
-        rc = run_batch(handles, opts, n, work_p, 1.0, &b, &ms);
+        rc = run_batch(handles, opts, n, work_p, 1.0, &b, &ms, &smm);
     } else {
         // autotuner: the work model and the split exponent gamma (blocks ~ work^gamma)
         // are chosen by timing each candidate once per batch shape; the choice is
@@ -918,7 +987,8 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         const char *off = getenv("MH_AUTOTUNE");
         if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
             const bool leaves = choice >= 10.0;
-            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), nullptr, &ms);
+            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), nullptr, &ms,
+                           &smm);
         } else {
             const double gammas[] = {0.5, 0.75, 1.0};
             double best_ms = 1e300, best = 1.0;
@@ -935,12 +1005,14 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
             }
             tune_store(sig, best);
             const bool leaves = best >= 10.0;
-            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, best - (leaves ? 10.0 : 0.0), nullptr, &ms);
+            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, best - (leaves ? 10.0 : 0.0), nullptr, &ms,
+                           &smm);
         }
     }
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
-        rc = collect_result(handles[i], opts[i].h, true, ms, nullptr, 1, 0, &out[i]);
+        rc = collect_result(handles[i], opts[i].h, true, ms, nullptr, 1, 0, &out[i], ms);
+        if (rc == MH_OK) out[i]->diag[6] = (uint64_t)smm;
         if (rc) {
             for (int j = 0; j < i; ++j) {
                 mh_result_free(out[j]);
@@ -1129,12 +1201,12 @@ struct mh_server {
         const int n = (int)active.size();
         std::vector<double> work(n);
         for (int i = 0; i < n; ++i) work[i] = work_estimate(active[i]->H, active[i]->opts.h - 1);
-        const std::vector<int> blocks = split_blocks(work, 0.75, grid);
+        const std::vector<int> blocks = split_grid(work, 0.75, num_sms);
         if (items_cap < n) {
             cudaFree(d_items);
             d_items = nullptr;
             items_cap = 0;
-            if (cudaMalloc((void **)&d_items, sizeof(BatchItem) * (size_t)n) != cudaSuccess) return;
+            if (cudaMalloc((void **)&d_items, batch_ws_bytes(n)) != cudaSuccess) return;
             items_cap = n;
         }
         std::vector<BatchItem> items(n);
@@ -1156,7 +1228,7 @@ struct mh_server {
         cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
         cudaEvent_t ev;
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (launch_solve_batch(d_items, n, d_yield, first, st) != cudaSuccess) {
+        if (launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms), st) != cudaSuccess) {
             cudaEventDestroy(ev);
             return;
         }

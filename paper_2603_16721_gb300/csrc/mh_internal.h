@@ -147,10 +147,25 @@ struct BatchItem {
     u32 *counts;
     int first_block, nblocks;
 };
-// Runs the cohorts of d_items (device array of n items) in one cooperative launch.
-// With d_yield (a zeroed device int), the launch ends as soon as one cohort
-// finishes: every other team stops at its next round boundary.
-cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, int grid, cudaStream_t st);
+// Block numbering of a batched launch.  Teams are ranges of "SM-major" block
+// numbers: the blocks resident on one SM get consecutive numbers, so a team whose
+// range is a multiple of the blocks per SM owns whole SMs (its L1 and shared memory
+// are not shared with another cohort).  tab: kBatchTabInts device ints owned by the
+// caller (reset by the launcher); sync: a GridSync for the launch's start.
+constexpr int kMaxSmid = 1024;
+constexpr int kBatchTabInts = 2 * kMaxSmid + 2;
+struct BatchMap {
+    int *tab;
+    GridSync *sync;
+    int per_sm, num_sms;
+};
+// Runs the cohorts of d_items (device array of n items) in one cooperative launch
+// of the whole batch grid (per_sm x num_sms blocks; blocks beyond the items' ranges
+// return at once).  With d_yield (a zeroed int in device or mapped host memory),
+// the launch ends as soon as one cohort finishes or overflows a frontier: every
+// other team stops at its next round boundary.
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, const BatchMap &map, cudaStream_t st);
+int batch_blocks_per_sm();
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
                                     u32 *counts, int grid, bool large, cudaStream_t st);
 int level1_grid(const Cohort &c);

@@ -1078,9 +1078,21 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         lap(0);
         // every block reads the same shard counts after the same barrier, so an
         // overflow is seen by all of them and they leave together
+        // on an overflow the team stops; in a batch it also asks the other teams to
+        // stop at their next round boundary, so that the host can grow the frontier
+        // and relaunch without leaving the team's blocks idle
+        auto overflow = [&]() {
+            if (t.rank == 0 && threadIdx.x == 0) {
+                s.state[kStOverflow] = 1;
+                if (yield) {
+                    *(volatile int *)yield = 1;
+                    __threadfence_system();
+                }
+            }
+        };
         for (int l = 2; l <= h - 1; ++l) {
             if (!phase_expand(c, s, round, l, f, counts, b, t)) {
-                if (t.rank == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+                overflow();
                 return;
             }
             if (!grid_sync(gsync, s.state, t.size)) return;
@@ -1088,7 +1100,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         lap(1);
         if (h >= 2) {
             if (!phase_leaf(c, s, round, f, counts, b, t)) {
-                if (t.rank == 0 && threadIdx.x == 0) s.state[kStOverflow] = 1;
+                overflow();
                 return;
             }
             if (!grid_sync(gsync, s.state, t.size)) return;
@@ -1123,19 +1135,66 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5]);
 }
 
-// Batched solve: block b works on the cohort whose block range holds b, with the
+// SM-major number of the calling block (thread 0): SMs are ranked in the order
+// their first block arrives, blocks within an SM in arrival order.  Returns -1 if
+// the numbering cannot be formed (an SM id out of range, more blocks on an SM than
+// expected, or a wait for the SM's rank that did not end).
+__device__ int sm_major_block(const BatchMap &m)
+{
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    if (smid >= (unsigned)kMaxSmid) return -1;
+    const int slot = atomicAdd(&m.tab[smid], 1);
+    int r;
+    if (slot == 0) {
+        r = atomicAdd(&m.tab[2 * kMaxSmid], 1);
+        atomicExch(&m.tab[kMaxSmid + smid], r);
+    } else {
+        unsigned spins = 0;
+        while ((r = *(volatile int *)&m.tab[kMaxSmid + smid]) < 0) {
+            __nanosleep(32);
+            if (++spins > (1u << 22)) return -1;
+        }
+    }
+    if (slot >= m.per_sm || r >= m.num_sms) return -1;
+    return r * m.per_sm + slot;
+}
+
+// Batched solve: block b (SM-major number, or blockIdx.x if that numbering failed
+// anywhere in the grid) works on the cohort whose block range holds b, with the
 // blocks of that range as its team; cohorts progress independently.
-__global__ void __launch_bounds__(kThreads, 4) k_solve_batch(const BatchItem *items, int n, int *yield)
+__global__ void __launch_bounds__(kThreads, 4) k_solve_batch(const BatchItem *items, int n, int *yield, BatchMap map)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
-    int lo = 0, hi = n - 1;  // last item with first_block <= blockIdx.x
+    __shared__ int vb_s;
+    if (threadIdx.x == 0) {
+        vb_s = sm_major_block(map);
+        if (vb_s < 0) atomicExch(&map.tab[2 * kMaxSmid + 1], 1);
+    }
+    if (!grid_sync(map.sync, items[0].s.state, (int)gridDim.x)) return;
+    const bool sm_major = *(volatile int *)&map.tab[2 * kMaxSmid + 1] == 0;
+    const int vb = sm_major ? vb_s : (int)blockIdx.x;
+    int lo = 0, hi = n - 1;  // last item with first_block <= vb
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (items[mid].first_block <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        if (items[mid].first_block <= vb) lo = mid; else hi = mid - 1;
     }
-    const BatchItem &it = items[lo];
-    const Team t{(int)blockIdx.x - it.first_block, it.nblocks};
-    if (t.rank >= t.size) return;
+    // the block's item in shared memory: the phases read its fields in their inner
+    // loops, and shared memory cannot alias the global stores in between (a global
+    // copy would be re-read after every store)
+    __shared__ BatchItem it;
+    static_assert(sizeof(BatchItem) % 4 == 0, "BatchItem is copied as 32-bit words");
+    for (int i = threadIdx.x; i < (int)(sizeof(BatchItem) / 4); i += blockDim.x)
+        ((int *)&it)[i] = ((const int *)&items[lo])[i];
+    __syncthreads();
+    Team t{vb - it.first_block, it.nblocks};
+    if (t.rank < 0 || t.rank >= t.size) return;
+    // a team of whole SMs ranks its blocks SM-minor (rank r on SM r mod #SMs), so
+    // that neighbouring work items, handed to neighbouring ranks, go to different SMs
+    if (sm_major && it.first_block % map.per_sm == 0 && it.nblocks % map.per_sm == 0) {
+        const int nsm = it.nblocks / map.per_sm;
+        t.rank = (t.rank % map.per_sm) * nsm + t.rank / map.per_sm;
+    }
     solve_team(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5], yield);
 }
 
@@ -1198,19 +1257,28 @@ int persistent_grid(int num_sms, bool large)
     return (large ? per_sm : 1) * num_sms;
 }
 
-int batch_grid(int num_sms)
+int batch_blocks_per_sm()
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch, kThreads, 0) != cudaSuccess) return 0;
-    return per_sm * num_sms;
+    return per_sm;
 }
 
-cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, int grid, cudaStream_t st)
+int batch_grid(int num_sms) { return batch_blocks_per_sm() * num_sms; }
+
+cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, const BatchMap &m, cudaStream_t st)
 {
     const BatchItem *items = d_items;
     int nn = n;
     int *yield = d_yield;
-    void *args[] = {&items, &nn, &yield};
+    BatchMap map = m;
+    cudaError_t e = cudaMemsetAsync(map.tab, 0, sizeof(int) * kMaxSmid, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(map.tab + kMaxSmid, 0xff, sizeof(int) * kMaxSmid, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(map.tab + 2 * kMaxSmid, 0, sizeof(int) * 2, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(map.sync, 0, sizeof(GridSync), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&items, &nn, &yield, &map};
+    const int grid = map.per_sm * map.num_sms;
     return cudaLaunchCooperativeKernel((const void *)k_solve_batch, dim3(grid), dim3(kThreads), args, 0, st);
 }
 

@@ -55,7 +55,7 @@ class mh_result(ctypes.Structure):
                 ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
                 ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64),
                 ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
-                ("mode", ctypes.c_int32), ("diag", ctypes.c_uint64 * 8)]
+                ("mode", ctypes.c_int32), ("diag", ctypes.c_uint64 * 8), ("kernel_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -133,6 +133,7 @@ class Result:
     finalize_ms: float = 0.0
     mode: int = 0
     diag: tuple = ()
+    kernel_ms: float = 0.0
 
     @property
     def k(self) -> int:
@@ -160,7 +161,7 @@ def _to_result(p) -> Result:
                  leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
                  leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense),
                  level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms),
-                 mode=int(r.mode), diag=tuple(int(x) for x in r.diag))
+                 mode=int(r.mode), diag=tuple(int(x) for x in r.diag), kernel_ms=float(r.kernel_ms))
     load().mh_result_free(p)
     return out
 

@@ -2,6 +2,7 @@
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -64,3 +65,24 @@ def test_build_is_idempotent():
     t0 = os.path.getmtime(_build.LIB)
     __graft_entry__.build()
     assert os.path.getmtime(_build.LIB) == t0
+
+
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct, from a C program compiled against include/mh.h."""
+    src = tmp_path / "layout.c"
+    body = "".join(f'printf("%zu\\n", offsetof({struct}, {f}));' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "mh.h"\n'
+                   f'int main(void) {{ printf("%zu\\n", sizeof({struct})); {body} return 0; }}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    return [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+
+
+@pytest.mark.parametrize("struct,cls", [("mh_result", "mh_result"), ("mh_solve_opts", "mh_solve_opts"),
+                                        ("mh_server_opts", "mh_server_opts")])
+def test_binding_structs_match_header_layout(tmp_path, struct, cls):
+    c = getattr(mh, cls)
+    names = [f[0] for f in c._fields_]
+    got = _c_layout(tmp_path, struct, names)
+    assert got[0] == ctypes.sizeof(c)
+    assert got[1:] == [getattr(c, n).offset for n in names]

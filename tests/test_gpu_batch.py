@@ -79,3 +79,13 @@ def test_batch_rejects_bad_splits(mh):
         mh.mh_solve_batch([a, b], [2, 2], blocks=[10 ** 6, 1])
     a.close()
     b.close()
+
+
+def test_batch_blocks_numbered_sm_major(mh):
+    """A batched launch numbers its blocks SM by SM (teams own whole SMs)."""
+    cohorts = _mixed_cohorts()[:3]
+    handles = [mh.mh_create(bm, G, Nt, Nn) for bm, G, Nt, Nn, h in cohorts]
+    got = mh.mh_solve_batch(handles, [c[4] for c in cohorts], blocks=[8, 8, 8])
+    assert all(r.diag[6] == 1 for r in got)
+    for H in handles:
+        H.close()

@@ -181,3 +181,23 @@ def test_invalid_inputs_rejected(mh):
             with pytest.raises(mh.MHError) as e:
                 mh.mh_solve(H, h, a)
             assert e.value.code == mh.MH_EINVAL
+
+
+def test_frontier_growth_on_overflow(mh, monkeypatch):
+    """Frontiers sized only by growth: the first rounds overflow the initial regions,
+    the host grows them and reruns the round; results and counters are unchanged."""
+    monkeypatch.setenv("MH_FRONTIER_PRESIZE", "0")
+    c = synth.generate(synth.c2_law(1500, 300, 200, seed=4, h=4))
+    ref = oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, 4)
+    for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
+        got = _gpu(mh, c.bitmaps, c.G, c.Nt, c.Nn, 4, mode=mode)
+        _same(got, ref)
+        if mode == mh.MH_MODE_PERSISTENT:
+            assert got.kernel_launches > 2   # init + at least one relaunch after an overflow
+    handles = [mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) for _ in range(2)]
+    try:
+        for r in mh.mh_solve_batch(handles, [4, 4], blocks=[8, 8]):
+            _same(r, ref)
+    finally:
+        for H in handles:
+            H.close()
