@@ -52,9 +52,34 @@ int fail(int code, const char *fmt, ...)
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
     } while (0)
 
+// Device memory of handles comes from one stream-ordered pool per device that keeps
+// what is freed (release threshold: unlimited), so creating and destroying handles
+// (a served request each) neither maps memory again nor synchronises the device.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+
+int device_pool(int dev, cudaMemPool_t *out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return fail(MH_ECUDA, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        MH_CUDA(cudaMemPoolCreate(&g_pools[dev], &props));
+        unsigned long long keep = ~0ull;
+        MH_CUDA(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    *out = g_pools[dev];
+    return MH_OK;
+}
+
 // Frontier memory of one handle: MH_FRONTIER_BUDGET_MB if set, else 80% of the
-// device memory that is free when a frontier grows.
-size_t frontier_budget()
+// device memory that is free (including what the pool holds unused) when a
+// frontier grows.
+size_t frontier_budget(int dev = -1)
 {
     const char *v = getenv("MH_FRONTIER_BUDGET_MB");
     if (v && *v) {
@@ -63,17 +88,61 @@ size_t frontier_budget()
     }
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return size_t(16) << 30;
+    if (dev >= 0 && dev < kMaxDevices && g_pools[dev]) {
+        unsigned long long reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(g_pools[dev], cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(g_pools[dev], cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+            reserved > used)
+            free_b += (size_t)(reserved - used);
+    }
     return (size_t)(free_b * 0.8);
 }
 
+// n elements from the device's pool, ordered on stream st.
 template <typename T>
-int dalloc(T **p, size_t n, int64_t *acct)
+int dalloc(T **p, size_t n, int64_t *acct, int dev, cudaStream_t st)
 {
     *p = nullptr;
     if (n == 0) n = 1;
-    MH_CUDA(cudaMalloc((void **)p, n * sizeof(T)));
+    cudaMemPool_t pool;
+    const int rc = device_pool(dev, &pool);
+    if (rc) return rc;
+    MH_CUDA(cudaMallocFromPoolAsync((void **)p, n * sizeof(T), pool, st));
     if (acct) *acct += (int64_t)(n * sizeof(T));
     return MH_OK;
+}
+
+void dfree(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
+// Pinned host buffers for the round state read-back (state + frontier counts),
+// recycled instead of freed: freeing pinned memory synchronises the device.
+constexpr size_t kStateBytes = sizeof(int) * (kStateWords + kCountWords);
+std::mutex g_pinned_mutex;
+std::vector<int *> g_pinned_free;
+
+int *pinned_state_get()
+{
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mutex);
+        if (!g_pinned_free.empty()) {
+            int *p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    int *p = nullptr;
+    if (cudaMallocHost((void **)&p, kStateBytes) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void pinned_state_put(int *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mutex);
+    g_pinned_free.push_back(p);
 }
 
 }  // namespace
@@ -86,7 +155,7 @@ struct mh_handle {
     int G = 0, Nt = 0, Nn = 0;
     Cohort c{};
     cudaStream_t stream = nullptr;
-    int num_sms = 0;
+    int num_sms = 0, dev = 0;
     int64_t device_bytes = 0;
     // cohort store
     u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr, *dCN = nullptr;
@@ -108,15 +177,17 @@ struct mh_handle {
     cudaEvent_t evk[2] = {};              // around each cooperative launch of a persistent solve
     bool presized[kMaxH] = {};            // frontier of depth l sized from its bound
 
+    // device memory goes back to the pool in the order of the handle's stream
     ~mh_handle()
     {
         for (int i = 0; i < 2; ++i)
             if (evk[i]) cudaEventDestroy(evk[i]);
-        cudaFree(dT); cudaFree(dN); cudaFree(dCT); cudaFree(dCN); cudaFree(dOrig); cudaFree(dInv);
-        cudaFree(dU); cudaFree(dCnt); cudaFree(dWork); cudaFree(dState); cudaFree(dRes);
-        cudaFree(dSlots); cudaFree(dCand); cudaFree(dCounts); cudaFree(dSync);
-        for (int l = 0; l < kMaxH; ++l) cudaFree(dF[l]);
-        if (hState) cudaFreeHost(hState);
+        for (void *p : {(void *)dT, (void *)dN, (void *)dCT, (void *)dCN, (void *)dOrig, (void *)dInv, (void *)dU,
+                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand,
+                        (void *)dCounts, (void *)dSync})
+            dfree(p, stream);
+        for (int l = 0; l < kMaxH; ++l) dfree(dF[l], stream);
+        pinned_state_put(hState);
     }
 };
 
@@ -179,22 +250,34 @@ int build_store(mh_handle *H, const uint64_t *bm)
         orig[i] = (u16)g;
         inv[g] = (u32)i;
     }
+    // sample-major copies: bit i of column s is set iff sorted gene i has sample s
+    // (a scatter of the set bits: the rows are sparse)
+    std::vector<u64> CT((size_t)Nt * c.GW, 0), CN((size_t)Nn * c.GW, 0);
+    for (int i = 0; i < G; ++i) {
+        const u64 bit = 1ull << (i & 63);
+        for (int w = 0; w < Wt; ++w)
+            for (u64 x = T[(size_t)i * c.WTp + w]; x; x &= x - 1)
+                CT[(size_t)(w * 64 + __builtin_ctzll(x)) * c.GW + (i >> 6)] |= bit;
+        for (int w = 0; w < Wn; ++w)
+            for (u64 x = N[(size_t)i * c.WNp + w]; x; x &= x - 1)
+                CN[(size_t)(w * 64 + __builtin_ctzll(x)) * c.GW + (i >> 6)] |= bit;
+    }
     int rc;
-    if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes))) return rc;
-    if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes))) return rc;
-    if ((rc = dalloc(&H->dCT, (size_t)Nt * c.GW, &H->device_bytes))) return rc;
-    if ((rc = dalloc(&H->dCN, (size_t)Nn * c.GW, &H->device_bytes))) return rc;
-    if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes))) return rc;
-    if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes))) return rc;
-    MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
-    MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, H->stream));
-    MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, H->stream));
-    MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, H->stream));
+    cudaStream_t st = H->stream;
+    if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dCT, CT.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dCN, CN.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
+    MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
+    if (!CT.empty()) MH_CUDA(cudaMemcpyAsync(H->dCT, CT.data(), CT.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
+    if (!CN.empty()) MH_CUDA(cudaMemcpyAsync(H->dCN, CN.data(), CN.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, st));
     c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.CN = H->dCN; c.orig = H->dOrig; c.inv = H->dInv;
-    launch_transpose(c, H->dT, c.WTp, Nt, H->dCT, H->stream);
-    launch_transpose(c, H->dN, c.WNp, Nn, H->dCN, H->stream);
-    MH_CUDA(cudaGetLastError());
-    MH_CUDA(cudaStreamSynchronize(H->stream));  // host vectors go out of scope
+    MH_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
     return MH_OK;
 }
 
@@ -206,6 +289,7 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
     H->stream = stream;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
+    H->dev = dev;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&H->coop, cudaDevAttrCooperativeLaunch, dev);
     if (e != cudaSuccess) {
@@ -232,17 +316,16 @@ int ensure_frontier(mh_handle *H, int l, u64 n, bool exact = false)
     const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
     const char *fixed = getenv("MH_FRONTIER_BUDGET_MB");
     const bool over = (fixed && *fixed) ? (size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget()
-                                        : (size_t)(new_bytes - old_bytes) > frontier_budget();
+                                        : (size_t)(new_bytes - old_bytes) > frontier_budget(H->dev);
     if (over || n > want)
         return fail(MH_ENOMEM, "depth-%d frontier needs %llu records per shard (%.1f GB), above the frontier budget",
                     l, (unsigned long long)n, (double)n * kShards * sizeof(Rec) / 1e9);
-    MH_CUDA(cudaStreamSynchronize(H->stream));
-    cudaFree(H->dF[l]);
+    dfree(H->dF[l], H->stream);  // stream-ordered: after the kernels that used it
     H->dF[l] = nullptr;
     H->frontier_bytes -= old_bytes;
     H->device_bytes -= old_bytes;
     H->cap[l] = 0;
-    int rc = dalloc(&H->dF[l], (size_t)want * kShards, &H->device_bytes);
+    int rc = dalloc(&H->dF[l], (size_t)want * kShards, &H->device_bytes, H->dev, H->stream);
     if (rc) return rc;
     H->cap[l] = (u32)want;
     H->frontier_bytes += new_bytes;
@@ -271,31 +354,33 @@ int ensure_workspace(mh_handle *H, int h)
     const int slots = std::max(std::max(level1_grid(H->c), leaf_grid(H)),
                                std::max(persistent_grid(H->num_sms, true), batch_grid(H->num_sms)));
     int rc;
+    const int dev = H->dev;
+    cudaStream_t st = H->stream;
     if (!H->dU) {
-        if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)kCountWords, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dSync, 1, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCounts, (size_t)kCountWords, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
-        MH_CUDA(cudaMallocHost((void **)&H->hState, sizeof(int) * (kStateWords + kCountWords)));
+        if (!(H->hState = pinned_state_get())) return fail(MH_ENOMEM, "pinned host allocation failed");
     }
     if (h > H->ws_h || rounds > H->ws_rounds) {
-        cudaFree(H->dCnt);
-        cudaFree(H->dRes);
+        dfree(H->dCnt, st);
+        dfree(H->dRes, st);
         H->dCnt = nullptr;
         H->dRes = nullptr;
         const int hh = std::max(h, H->ws_h);
-        if ((rc = dalloc(&H->dCnt, (size_t)rounds * hh * 2, &H->device_bytes))) return rc;
-        if ((rc = dalloc(&H->dRes, (size_t)rounds * (hh + 2), &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dCnt, (size_t)rounds * hh * 2, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dRes, (size_t)rounds * (hh + 2), &H->device_bytes, dev, st))) return rc;
         H->ws_h = hh;
         H->ws_rounds = rounds;
     }
     if (slots > H->ws_slots) {
-        cudaFree(H->dSlots);
+        dfree(H->dSlots, st);
         H->dSlots = nullptr;
-        if ((rc = dalloc(&H->dSlots, (size_t)slots, &H->device_bytes))) return rc;
+        if ((rc = dalloc(&H->dSlots, (size_t)slots, &H->device_bytes, dev, st))) return rc;
         H->ws_slots = slots;
     }
     // depth 1: a warp appends its 32 genes to one of kShards regions
@@ -335,7 +420,7 @@ int presize_frontiers(mh_handle *H, int h)
             if (m >= l) e += comb;
         }
         const double per_shard = e * 1.15 / kShards + 64.0;
-        if (per_shard * kShards * sizeof(Rec) > 0.5 * (double)frontier_budget()) continue;
+        if (per_shard * kShards * sizeof(Rec) > 0.5 * (double)frontier_budget(H->dev)) continue;
         const int rc = ensure_frontier(H, l, (u64)per_shard, true);
         if (rc) return rc;
     }
@@ -514,9 +599,7 @@ MH_API int mh_handle_info(const mh_handle *H, int32_t *G, int32_t *Nt, int32_t *
 MH_API void mh_destroy(mh_handle *H)
 {
     if (!H) return;
-    if (H->stream) cudaStreamSynchronize(H->stream);
-    else cudaDeviceSynchronize();
-    delete H;
+    delete H;  // device memory returns to the pool in stream order: no device-wide wait
 }
 
 MH_API void mh_result_free(mh_result *r)
@@ -1054,6 +1137,7 @@ struct ServerReq {
     std::string msg;
     mh_result *res = nullptr;
     Solve s{};
+    int maxr = 0;
 };
 
 // Device memory a request needs: its store, workspace and (for h >= 3) the
@@ -1084,7 +1168,7 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h)
 
 struct mh_server {
     mh_server_opts o{};
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr, st_up = nullptr;  // launches; uploads
     int grid = 0, num_sms = 0;
     int64_t budget = 0, in_use = 0;
     std::thread th;
@@ -1092,6 +1176,7 @@ struct mh_server {
     std::condition_variable cv;
     std::deque<ServerReq *> queue;
     std::vector<ServerReq *> active;
+    std::vector<ServerReq *> ready;  // uploaded, joining at the next launch (scheduler thread only)
     std::map<uint64_t, ServerReq *> all;
     bool stop = false;
     uint64_t next_ticket = 1;
@@ -1108,51 +1193,63 @@ struct mh_server {
         if (r->res) r->res->solve_ms = (r->t_done - r->t_submit) * 1e3;
     }
 
-    // Admission: uploads queued requests while a slot and memory are free.
-    void admit()
+    // Admission of the queue head when a slot and memory are free: the cohort is
+    // packed on the host and uploaded on the upload stream (copies and pool
+    // allocations only, no kernel), so it can run while a launch is on the GPU.
+    // The admitted request waits in `ready` for the next launch.  Returns true
+    // if the head was taken (admitted, or finished with an error).
+    bool admit_one()
     {
-        std::vector<ServerReq *> in;
+        ServerReq *r = nullptr;
         {
             std::lock_guard<std::mutex> lock(mu);
-            while (!queue.empty() && (int)(active.size() + in.size()) < o.slots) {
-                ServerReq *r = queue.front();
-                if (r->footprint > budget) {
-                    queue.pop_front();
-                    finish(r, MH_EREJECT, "request needs more device memory than the server budget");
-                    cv.notify_all();
-                    continue;
-                }
-                if (in_use + r->footprint > budget && !(active.empty() && in.empty())) break;
+            if (queue.empty() || (int)(active.size() + ready.size()) >= o.slots) return false;
+            r = queue.front();
+            if (r->footprint > budget) {
                 queue.pop_front();
-                in_use += r->footprint;
-                in.push_back(r);
-            }
-        }
-        for (ServerReq *r : in) {
-            int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st, &r->H);
-            int maxr = 0;
-            if (rc == MH_OK) rc = prepare_solve(r->H, &r->opts, &r->s, &maxr);
-            if (rc == MH_OK) {
-                r->bm.clear();
-                r->bm.shrink_to_fit();
-                launch_solve_init(r->H->c, r->s, r->H->ws_rounds, maxr, r->H->dCounts, st);
-                if (r->Nt == 0) {
-                    const int one = 1;
-                    cudaMemcpyAsync(r->H->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st);
-                }
-                cudaStreamSynchronize(st);
-            }
-            std::lock_guard<std::mutex> lock(mu);
-            if (rc != MH_OK) {
-                if (r->H) mh_destroy(r->H);
-                r->H = nullptr;
-                in_use -= r->footprint;
-                finish(r, rc, mh_last_error());
+                finish(r, MH_EREJECT, "request needs more device memory than the server budget");
                 cv.notify_all();
-            } else {
-                active.push_back(r);
+                return true;
+            }
+            if (in_use + r->footprint > budget && !(active.empty() && ready.empty())) return false;
+            queue.pop_front();
+            in_use += r->footprint;
+        }
+        int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st_up, &r->H);
+        int maxr = 0;
+        if (rc == MH_OK) rc = prepare_solve(r->H, &r->opts, &r->s, &maxr);
+        if (rc == MH_OK && cudaStreamSynchronize(st_up) != cudaSuccess) rc = fail(MH_ECUDA, "upload failed");
+        std::lock_guard<std::mutex> lock(mu);
+        if (rc != MH_OK) {
+            if (r->H) mh_destroy(r->H);
+            r->H = nullptr;
+            in_use -= r->footprint;
+            finish(r, rc, mh_last_error());
+            cv.notify_all();
+            return true;
+        }
+        r->H->stream = st;  // from now on ordered with the launches
+        r->maxr = maxr;
+        r->bm.clear();
+        r->bm.shrink_to_fit();
+        ready.push_back(r);
+        return true;
+    }
+
+    // Ready requests join the active set: their round state is initialised on the
+    // launch stream, ahead of the next launch.
+    void start_ready()
+    {
+        for (ServerReq *r : ready) {
+            launch_solve_init(r->H->c, r->s, r->H->ws_rounds, r->maxr, r->H->dCounts, st);
+            if (r->Nt == 0) {
+                const int one = 1;
+                cudaMemcpyAsync(r->H->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st);
             }
         }
+        std::lock_guard<std::mutex> lock(mu);
+        active.insert(active.end(), ready.begin(), ready.end());
+        ready.clear();
     }
 
     // Retires finished requests; grows overflowed frontiers.  Returns false on a
@@ -1234,14 +1331,11 @@ struct mh_server {
         }
         ++launches;
         cudaEventRecord(ev, st);
-        // while the launch runs, ask it to yield when a queued request could start
+        // while the launch runs, upload queued requests that fit and ask the launch
+        // to end at the next round boundary once one is ready to join
         while (cudaEventQuery(ev) == cudaErrorNotReady) {
-            bool want = false;
-            {
-                std::lock_guard<std::mutex> lock(mu);
-                want = !queue.empty() && (int)active.size() < o.slots;
-            }
-            if (want) *(volatile int *)h_yield = 1;
+            admit_one();
+            if (!ready.empty()) *(volatile int *)h_yield = 1;
             std::this_thread::sleep_for(std::chrono::microseconds(50));
         }
         cudaEventDestroy(ev);
@@ -1255,10 +1349,12 @@ struct mh_server {
         for (;;) {
             {
                 std::unique_lock<std::mutex> lock(mu);
-                cv.wait(lock, [&] { return stop || !queue.empty() || !active.empty(); });
-                if (stop && queue.empty() && active.empty()) return;
+                cv.wait(lock, [&] { return stop || !queue.empty() || !active.empty() || !ready.empty(); });
+                if (stop && queue.empty() && active.empty() && ready.empty()) return;
             }
-            admit();
+            while (admit_one()) {
+            }
+            start_ready();
             if (active.empty()) continue;
             run_active();
             retire();
@@ -1283,6 +1379,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->st_up, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&S->h_yield, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&S->d_yield, S->h_yield, 0);
     if (e != cudaSuccess) {
@@ -1403,7 +1500,9 @@ MH_API void mh_server_destroy(mh_server *S)
     }
     cudaFree(S->d_items);
     if (S->h_yield) cudaFreeHost(S->h_yield);
+    if (S->st) cudaStreamSynchronize(S->st);
     if (S->st) cudaStreamDestroy(S->st);
+    if (S->st_up) cudaStreamDestroy(S->st_up);
     delete S;
 }
 
