@@ -444,7 +444,7 @@ def run_served(args):
     plain_span = time.perf_counter() - t0
 
     # (i) served: requests submitted at their arrival times
-    with mh.Server(slots=args.slots) as S:
+    with mh.Server(slots=args.slots, large_slots=args.large_slots) as S:
         tickets = [None] * n
         t0 = time.perf_counter()
 
@@ -492,6 +492,8 @@ def main(argv=None):
                          "served200: the served request trace")
     ap.add_argument("--requests", type=int, default=200, help="served200: requests replayed")
     ap.add_argument("--slots", type=int, default=8, help="served200: concurrent requests")
+    ap.add_argument("--large-slots", type=int, default=0,
+                    help="served200: large requests solved concurrently (0: the library default)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -196,6 +196,12 @@ typedef struct mh_server mh_server;
 typedef struct {
     int64_t hbm_budget_bytes; /* device memory for active requests; <= 0: 80% of the free memory */
     int32_t slots;            /* requests solved concurrently; <= 0: 8 */
+    int32_t large_slots;      /* "large" requests (more than 4e6 (h-1)-gene sets sharing a tumor, the
+                                 size at which one request keeps the whole GPU busy) solved
+                                 concurrently; <= 0: 1.  Large requests start in arrival order;
+                                 smaller ones queued behind a waiting large one may start first
+                                 (backfill), so a large request is not slowed by those that
+                                 arrive after it is admitted */
 } mh_server_opts;
 
 /* Starts a server on the current device.  opts may be NULL (defaults).

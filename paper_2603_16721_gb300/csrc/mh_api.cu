@@ -400,6 +400,11 @@ namespace {
 
 double work_estimate(const mh_handle *H, int d);
 
+// Expected search work (work_estimate with d = h - 1) above which one solve keeps
+// the whole GPU busy: such a solve runs the build with four blocks per SM, and the
+// served runtime limits how many of them share the GPU.
+constexpr double kLargeWork = 4.0e6;
+
 // Sizes the frontiers of depths 2..h-1 once per handle from a bound on their first
 // round: a non-empty depth-l prefix shares a tumor s, so it is one of the C(m_s, l)
 // l-sets of the genes mutated in s (m_s of them); at most sum_s C(m_s, l) records.
@@ -658,7 +663,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     ++launches;
     const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
     // large build for cohorts whose deepest frontier is expected to hold millions of prefixes
-    const bool large = work_estimate(H, h - 1) > 4.0e6;
+    const bool large = work_estimate(H, h - 1) > kLargeWork;
     const int pgrid = persistent_grid(H->num_sms, large);
     int rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
@@ -1138,11 +1143,13 @@ struct ServerReq {
     mh_result *res = nullptr;
     Solve s{};
     int maxr = 0;
+    double work = 0.0;   // expected search work (work_estimate with d = h - 1)
+    bool large = false;  // work above kLargeWork
 };
 
 // Device memory a request needs: its store, workspace and (for h >= 3) the
 // frontiers, estimated from the (h-1)-gene sets that share a tumor.
-int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h)
+int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, double *work)
 {
     const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64;
     std::vector<int> m(Nt, 0);
@@ -1152,15 +1159,17 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h)
     const int64_t gw = ((G + 63) / 64 + 2);
     int64_t bytes = (int64_t)G * (Wt + Wn + 4) * 8 + (int64_t)(Nt + Nn) * gw * 8;
     bytes += (int64_t)((G + kShards - 1) / kShards + 64) * kShards * (int64_t)sizeof(Rec);
-    if (h >= 3) {
-        double sets = 0;
-        for (int x : m) {
-            double comb = 1.0;
-            for (int i = 0; i < h - 1; ++i) comb = comb * (double)(x - i) / (double)(i + 1);
-            if (x >= h - 1) sets += comb;
+    // sets[d]: the d-gene sets sharing a tumor, summed over tumors
+    std::vector<double> sets(std::max(h, 1), 0.0);
+    for (int x : m) {
+        double comb = 1.0;
+        for (int d = 0; d < h; ++d) {
+            if (x >= d) sets[d] += comb;
+            comb = comb * (double)(x - d) / (double)(d + 1);
         }
-        bytes += (int64_t)(sets * 1.25 * (double)sizeof(Rec));
     }
+    for (int l = 2; l < h; ++l) bytes += (int64_t)(sets[l] * 1.25 * (double)sizeof(Rec));
+    *work = (double)G + sets[h - 1];  // as work_estimate(H, h - 1)
     return bytes + (64 << 20);
 }
 
@@ -1204,15 +1213,23 @@ struct mh_server {
         {
             std::lock_guard<std::mutex> lock(mu);
             if (queue.empty() || (int)(active.size() + ready.size()) >= o.slots) return false;
-            r = queue.front();
+            int large = 0;
+            for (ServerReq *a : active) large += a->large;
+            for (ServerReq *a : ready) large += a->large;
+            // the first request in arrival order that may start: a large one waits
+            // while large_slots are taken and the smaller ones behind it go first
+            auto it = queue.begin();
+            while (it != queue.end() && (*it)->large && large >= o.large_slots && (*it)->footprint <= budget) ++it;
+            if (it == queue.end()) return false;
+            r = *it;
             if (r->footprint > budget) {
-                queue.pop_front();
+                queue.erase(it);
                 finish(r, MH_EREJECT, "request needs more device memory than the server budget");
                 cv.notify_all();
                 return true;
             }
             if (in_use + r->footprint > budget && !(active.empty() && ready.empty())) return false;
-            queue.pop_front();
+            queue.erase(it);
             in_use += r->footprint;
         }
         int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st_up, &r->H);
@@ -1297,7 +1314,7 @@ struct mh_server {
     {
         const int n = (int)active.size();
         std::vector<double> work(n);
-        for (int i = 0; i < n; ++i) work[i] = work_estimate(active[i]->H, active[i]->opts.h - 1);
+        for (int i = 0; i < n; ++i) work[i] = active[i]->work;
         const std::vector<int> blocks = split_grid(work, 0.75, num_sms);
         if (items_cap < n) {
             cudaFree(d_items);
@@ -1372,6 +1389,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
     if (!S) return fail(MH_ENOMEM, "host allocation of the server failed");
     if (opts) S->o = *opts;
     if (S->o.slots <= 0) S->o.slots = 8;
+    if (S->o.large_slots <= 0) S->o.large_slots = 1;
     int dev = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     S->dev = dev;
@@ -1419,7 +1437,8 @@ MH_API int mh_submit(mh_server *S, const uint64_t *bitmaps, int32_t G, int32_t N
     r->opts.h = h;
     r->opts.alpha = alpha;
     r->opts.mode = MH_MODE_PERSISTENT;
-    r->footprint = estimate_footprint(bitmaps, G, Nt, Nn, h);
+    r->footprint = estimate_footprint(bitmaps, G, Nt, Nn, h, &r->work);
+    r->large = r->work > kLargeWork;
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->stop) {

@@ -278,14 +278,14 @@ def mh_solve_batch(handles, hs, alphas=None, blocks=None, prune: int = MH_PRUNE_
 
 
 class mh_server_opts(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("large_slots", ctypes.c_int32)]
 
 
 class Server:
     """Served runtime (continuous batching): mh_server_create / mh_submit /
     mh_poll / mh_wait / mh_server_destroy."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 0):
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 0, large_slots: int = 0):
         lib = load()
         if not hasattr(lib, "_server_typed"):
             lib.mh_server_create.restype = ctypes.c_int
@@ -304,7 +304,7 @@ class Server:
             lib.mh_server_destroy.argtypes = [_P]
             lib._server_typed = True
         self.ptr = _P()
-        o = mh_server_opts(hbm_budget_bytes, slots)
+        o = mh_server_opts(hbm_budget_bytes, slots, large_slots)
         _check(lib.mh_server_create(ctypes.byref(o), ctypes.byref(self.ptr)))
 
     def submit(self, bitmaps, G, Nt, Nn, h, alpha=(1, 10)) -> int:
