@@ -138,6 +138,25 @@ def algorithmic_ops(r, Nt, Nn):
     return visited_all * (wt + 1) + scored * per_scored, visited_leaf * (wt + 1) + scored * per_scored
 
 
+def _profiled_traffic(kernel_file="k_solve_c2.md"):
+    """DRAM bytes per launch of the solve kernel from the committed ncu summary, if
+    that summary was taken from the kernel source as it is now (else None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2603_16721_gb300", "csrc", "mh_kernels.cu")
+    try:
+        text = open(os.path.join(ROOT, "profiles", kernel_file)).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    fields = dict(ln.strip("- `").split(": ", 1) for ln in text.splitlines() if ln.startswith("- `") and ": " in ln)
+    if fields.get("kernel_source_sha256", "").strip("`") != sha:
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"].strip("`"))
+    except (KeyError, ValueError):
+        return None
+
+
 def solve_roofline(res_list, Nt, Nn, peaks, source):
     """Integer-pipe roofline of the persistent solve kernel (the dominant kernel:
     one cooperative launch runs every round of a solve).
@@ -164,7 +183,7 @@ def solve_roofline(res_list, Nt, Nn, peaks, source):
         leaf = {"achieved": round(la, 4), "frac": round(la / peak, 4), "ms_per_solve": round(leaf_s * 1e3 / len(res_list), 4),
                 "issued": round(issued, 4), "issued_frac": round(issued / peak, 5)}
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s (int32)",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(),
             "kernel": "k_solve (persistent solve, one launch per solve)", "launches": launches,
             "avg_launch_us": round(kernel_s / launches * 1e6, 2),
             "ops_per_launch": round(sum(o[0] for o in ops) / launches),

@@ -167,11 +167,14 @@ MH_API const char *mh_last_error(void);
  * launch ends at the others' next round boundary and the unfinished cohorts
  * share the whole grid again (one launch per finished cohort at most).  The paper
  * runs one cohort at a time; this is the GB300 batching of independent problems.
- * blocks: n block counts (each >= 1, summing to at most the co-resident grid; kept
- * fixed), or NULL to let the autotuner choose: blocks ~ work^gamma
- * with the per-cohort work estimated from the tumors' mutation counts (the gene
- * sets of size h-1, or of size h, that share a tumor), model and gamma
- * picked by timing each candidate once per batch shape and cached in the file
+ * Teams own whole SMs when the split allows it (blocks in multiples of the blocks
+ * one SM holds).  blocks: n block counts (each >= 1, summing to at most the
+ * co-resident grid of the three-blocks-per-SM build; kept fixed), or NULL to let
+ * the autotuner choose the kernel build (three or four blocks per SM) and the
+ * split: blocks ~ work^gamma with the per-cohort work estimated from the tumors'
+ * mutation counts (the gene sets of size h-1, or of size h, that share a tumor);
+ * build, model and gamma are picked by timing each candidate once per batch shape
+ * and cached in the file
  * named by MH_AUTOTUNE_CACHE (default ~/.cache/mh_autotune.txt; MH_AUTOTUNE=0
  * disables tuning).  Work runs on the first handle's stream; the call is
  * synchronous.  out: n result pointers, each as from mh_solve_ex (solve_ms is the

@@ -352,15 +352,16 @@ int ensure_workspace(mh_handle *H, int h)
 {
     const int rounds = H->Nt + 2;
     const int slots = std::max(std::max(level1_grid(H->c), leaf_grid(H)),
-                               std::max(persistent_grid(H->num_sms, true), batch_grid(H->num_sms)));
+                               std::max(persistent_grid(H->num_sms, true),
+                                        std::max(batch_grid(H->num_sms, 3), batch_grid(H->num_sms, 4))));
     int rc;
     const int dev = H->dev;
     cudaStream_t st = H->stream;
     if (!H->dU) {
         if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 1, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)kCountWords, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 2, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCounts, (size_t)kCountSets * kCountWords, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
@@ -380,7 +381,7 @@ int ensure_workspace(mh_handle *H, int h)
     if (slots > H->ws_slots) {
         dfree(H->dSlots, st);
         H->dSlots = nullptr;
-        if ((rc = dalloc(&H->dSlots, (size_t)slots, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dSlots, (size_t)2 * slots, &H->device_bytes, dev, st))) return rc;
         H->ws_slots = slots;
     }
     // depth 1: a warp appends its 32 genes to one of kShards regions
@@ -659,7 +660,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     u32 *counts = H->dCounts;
 
     MH_CUDA(cudaEventRecord(total.a, st));
-    launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, st);
+    launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, kCountSets, st);
     ++launches;
     const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
     // large build for cohorts whose deepest frontier is expected to hold millions of prefixes
@@ -685,8 +686,6 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
             MH_CUDA(cudaEventRecord(H->evk[1], st));
             ++launches;
             MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, st));
-            MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, counts, sizeof(u32) * kCountWords,
-                                    cudaMemcpyDeviceToHost, st));
             MH_CUDA(cudaStreamSynchronize(st));
             const int *hs = H->hState;
             const u32 *hc = (const u32 *)(H->hState + kStateWords);
@@ -698,13 +697,15 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 destroy_events();
                 return fail(MH_ETIMEOUT, "a grid barrier of the persistent solve timed out in round %d", rounds_done);
             }
-            if (hs[3]) {
+            if (hs[3]) {  // the frontier counters of the overflowed round (its parity's set)
+                MH_CUDA(cudaMemcpy(H->hState + kStateWords, counts + (size_t)(rounds_done & 1) * kCountWords,
+                                   sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost));
                 if ((rc = grow_overflowed(H, h, hc))) {
                     destroy_events();
                     return rc;
                 }
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
-                MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st));
+                MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountSets * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
                 continue;
             }
@@ -768,7 +769,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 return rc;
             }
             MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
-            MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st));
+            MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountSets * kCountWords, st));
             MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
             continue;
         }
@@ -913,17 +914,18 @@ size_t batch_ws_bytes(int n)
     return sizeof(BatchItem) * (size_t)n + 256 + sizeof(int) * kBatchTabInts + sizeof(GridSync);
 }
 
-BatchMap batch_map_at(BatchItem *items, int cap, int num_sms)
+BatchMap batch_map_at(BatchItem *items, int cap, int num_sms, int build)
 {
     char *base = (char *)items + sizeof(BatchItem) * (size_t)cap + 256;
-    return BatchMap{(int *)base, (GridSync *)(base + sizeof(int) * kBatchTabInts), batch_blocks_per_sm(), num_sms};
+    return BatchMap{(int *)base, (GridSync *)(base + sizeof(int) * kBatchTabInts), batch_blocks_per_sm(build), num_sms,
+                    build};
 }
 
 // Blocks per cohort of a batched launch: whole SMs (blocks ~ work^gamma rounded to
 // the blocks one SM holds) when there are no more cohorts than SMs.
-std::vector<int> split_grid(const std::vector<double> &work, double gamma, int num_sms)
+std::vector<int> split_grid(const std::vector<double> &work, double gamma, int num_sms, int build)
 {
-    const int per_sm = batch_blocks_per_sm();
+    const int per_sm = batch_blocks_per_sm(build);
     if ((int)work.size() > num_sms) return split_blocks(work, gamma, per_sm * num_sms);
     std::vector<int> b = split_blocks(work, gamma, num_sms);
     for (int &x : b) x *= per_sm;
@@ -935,7 +937,7 @@ std::vector<int> split_grid(const std::vector<double> &work, double gamma, int n
 // each time a cohort finishes, the launch ends and the remaining cohorts share
 // the whole grid again.  *ms receives the run's time (CUDA events).
 int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, double gamma,
-              const std::vector<int> *fixed, double *ms, int *sm_major = nullptr)
+              int build, const std::vector<int> *fixed, double *ms, int *sm_major = nullptr)
 {
     if (sm_major) *sm_major = 1;
     cudaStream_t st = hs[0]->stream;
@@ -949,7 +951,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
     MH_CUDA(cudaEventCreate(&a));
     MH_CUDA(cudaEventCreate(&b));
     MH_CUDA(cudaEventRecord(a, st));
-    for (int i = 0; i < n; ++i) launch_solve_init(hs[i]->c, ss[i], hs[i]->ws_rounds, maxr[i], hs[i]->dCounts, st);
+    for (int i = 0; i < n; ++i) launch_solve_init(hs[i]->c, ss[i], hs[i]->ws_rounds, maxr[i], hs[i]->dCounts, kCountSets, st);
     std::lock_guard<std::mutex> lock(g_items_mutex);
     if (g_items_cap < n) {
         cudaFree(g_items);
@@ -959,7 +961,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         g_items_cap = n;
     }
     int *d_yield = (int *)((char *)g_items + sizeof(BatchItem) * (size_t)g_items_cap);
-    const BatchMap map = batch_map_at(g_items, g_items_cap, hs[0]->num_sms);
+    const BatchMap map = batch_map_at(g_items, g_items_cap, hs[0]->num_sms, build);
     std::vector<char> finished(n, 0);
     for (int i = 0; i < n; ++i) finished[i] = hs[i]->Nt == 0;
     for (;;) {
@@ -973,7 +975,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         } else {
             std::vector<double> w;
             for (int i : act) w.push_back(work[i]);
-            blocks = split_grid(w, gamma, hs[0]->num_sms);
+            blocks = split_grid(w, gamma, hs[0]->num_sms, build);
         }
         std::vector<BatchItem> items(act.size());
         int first = 0;
@@ -1002,13 +1004,13 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
             if (H->hState[2]) return fail(MH_ETIMEOUT, "a team barrier of the batched solve timed out");
             if (H->hState[3]) {
-                MH_CUDA(cudaMemcpy(H->hState + kStateWords, H->dCounts, sizeof(u32) * kCountWords,
-                                   cudaMemcpyDeviceToHost));
                 const int r = H->hState[4];
+                MH_CUDA(cudaMemcpy(H->hState + kStateWords, H->dCounts + (size_t)(r & 1) * kCountWords,
+                                   sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost));
                 int rc = grow_overflowed(H, opts[i].h, (const u32 *)(H->hState + kStateWords));
                 if (rc) return rc;
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)r * opts[i].h * 2, 0, sizeof(u64) * 2 * opts[i].h, st));
-                MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountWords, st));
+                MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
             }
             finished[i] = H->hState[1] != 0;
@@ -1044,7 +1046,7 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         int rc = prepare_solve(handles[i], &opts[i], &tmp, &mr);
         if (rc) return rc;
     }
-    const int grid = batch_grid(H0->num_sms);
+    const int grid = batch_grid(H0->num_sms, 3);  // the smaller of the two builds' grids
     if (grid < n) return fail(MH_EINVAL, "mh_solve_batch: %d cohorts but only %d co-resident blocks", n, grid);
     std::vector<int> b(n);
     if (blocks) {
@@ -1064,37 +1066,44 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     }
     double ms = 0.0;
     int rc = MH_OK, smm = 0;
+    // a choice of the autotuner, encoded as 100 * (build == 4) + 10 * model + gamma
+    auto run_choice = [&](double choice, double *t, int *smm_out) {
+        const int build = choice >= 100.0 ? 4 : 3;
+        if (choice >= 100.0) choice -= 100.0;
+        const bool leaves = choice >= 10.0;
+        return run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), build, nullptr,
+                         t, smm_out);
+    };
     if (blocks) {
-        rc = run_batch(handles, opts, n, work_p, 1.0, &b, &ms, &smm);
+        rc = run_batch(handles, opts, n, work_p, 1.0, 3, &b, &ms, &smm);
     } else {
-        // autotuner: the work model and the split exponent gamma (blocks ~ work^gamma)
-        // are chosen by timing each candidate once per batch shape; the choice is
-        // cached on disk (encoded as 10 * model + gamma)
+        // autotuner: the kernel build (3 or 4 blocks per SM), the work model and the
+        // split exponent gamma (blocks ~ work^gamma) are chosen by timing each
+        // candidate once per batch shape; the choice is cached on disk
         const std::string sig = batch_signature(handles, opts, n, grid);
         double choice = 1.0;
         const char *off = getenv("MH_AUTOTUNE");
         if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
-            const bool leaves = choice >= 10.0;
-            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), nullptr, &ms,
-                           &smm);
+            rc = run_choice(choice, &ms, &smm);
         } else {
             const double gammas[] = {0.5, 0.75, 1.0};
             double best_ms = 1e300, best = 1.0;
-            for (int model = 0; model < 2; ++model) {
-                for (double g : gammas) {
-                    double t = 0.0;
-                    rc = run_batch(handles, opts, n, model ? work_l : work_p, g, nullptr, &t);
-                    if (rc) return rc;
-                    if (t < best_ms) {
-                        best_ms = t;
-                        best = 10.0 * model + g;
+            for (int build : kBatchBuilds) {
+                for (int model = 0; model < 2; ++model) {
+                    for (double g : gammas) {
+                        double t = 0.0;
+                        const double cand = (build == 4 ? 100.0 : 0.0) + 10.0 * model + g;
+                        rc = run_choice(cand, &t, nullptr);
+                        if (rc) return rc;
+                        if (t < best_ms) {
+                            best_ms = t;
+                            best = cand;
+                        }
                     }
                 }
             }
             tune_store(sig, best);
-            const bool leaves = best >= 10.0;
-            rc = run_batch(handles, opts, n, leaves ? work_l : work_p, best - (leaves ? 10.0 : 0.0), nullptr, &ms,
-                           &smm);
+            rc = run_choice(best, &ms, &smm);
         }
     }
     if (rc) return rc;
@@ -1174,6 +1183,10 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, dou
 }
 
 }  // namespace
+
+// The batched kernel's build used by the server (four blocks per SM: the faster one
+// on a stream of large requests with small ones backfilling).
+constexpr int kServerBuild = 4;
 
 struct mh_server {
     mh_server_opts o{};
@@ -1258,7 +1271,7 @@ struct mh_server {
     void start_ready()
     {
         for (ServerReq *r : ready) {
-            launch_solve_init(r->H->c, r->s, r->H->ws_rounds, r->maxr, r->H->dCounts, st);
+            launch_solve_init(r->H->c, r->s, r->H->ws_rounds, r->maxr, r->H->dCounts, kCountSets, st);
             if (r->Nt == 0) {
                 const int one = 1;
                 cudaMemcpyAsync(r->H->dState + 1, &one, sizeof(int), cudaMemcpyHostToDevice, st);
@@ -1282,11 +1295,12 @@ struct mh_server {
             if (st8[2]) rc = fail(MH_ETIMEOUT, "a team barrier of the served solve timed out");
             if (rc == MH_OK && st8[3]) {
                 std::vector<u32> hc(kCountWords);
-                cudaMemcpy(hc.data(), H->dCounts, sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost);
+                cudaMemcpy(hc.data(), H->dCounts + (size_t)(st8[4] & 1) * kCountWords, sizeof(u32) * kCountWords,
+                           cudaMemcpyDeviceToHost);
                 rc = grow_overflowed(H, r->opts.h, hc.data());
                 if (rc == MH_OK) {
                     cudaMemsetAsync(H->dCnt + (size_t)st8[4] * r->opts.h * 2, 0, sizeof(u64) * 2 * r->opts.h, st);
-                    cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountWords, st);
+                    cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st);
                     cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st);
                     cudaStreamSynchronize(st);
                     keep.push_back(r);
@@ -1315,7 +1329,7 @@ struct mh_server {
         const int n = (int)active.size();
         std::vector<double> work(n);
         for (int i = 0; i < n; ++i) work[i] = active[i]->work;
-        const std::vector<int> blocks = split_grid(work, 0.75, num_sms);
+        const std::vector<int> blocks = split_grid(work, 0.75, num_sms, kServerBuild);
         if (items_cap < n) {
             cudaFree(d_items);
             d_items = nullptr;
@@ -1342,7 +1356,8 @@ struct mh_server {
         cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
         cudaEvent_t ev;
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms), st) != cudaSuccess) {
+        if (launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms, kServerBuild), st) !=
+            cudaSuccess) {
             cudaEventDestroy(ev);
             return;
         }
@@ -1404,7 +1419,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
         delete S;
         return fail(MH_ECUDA, "mh_server_create: %s", cudaGetErrorString(e));
     }
-    S->grid = batch_grid(S->num_sms);
+    S->grid = batch_grid(S->num_sms, kServerBuild);
     if (S->o.slots > S->grid) S->o.slots = S->grid;
     if (S->o.hbm_budget_bytes > 0) {
         S->budget = S->o.hbm_budget_bytes;

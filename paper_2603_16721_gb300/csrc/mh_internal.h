@@ -80,11 +80,13 @@ struct Solve {
     int *state;         // kStateWords ints: k selected, done, error, overflow, round, round limit
     int *res;           // per round: h original indices, TP, FP
     u64 *cnt;           // per round, per level: visited, pruned
-    Key *slots;         // per-block best candidates of the current round
+    Key *slots;         // per-block best candidates of the current round (persistent solve:
+                        // two arrays of nslots, by round parity)
     int nslots;
     u64 *work;          // leaf-kernel work counters, see kWork*
     Key *cand;          // kCandidates best keys of the previous round (for the next threshold)
-    u64 *best_hint;     // best score (s field) known to exist in the round, for skipping hopeless scoring
+    u64 *best_hint;     // best score (s field) known to exist in the round, for skipping hopeless
+                        // scoring (persistent solve: two words, by round parity)
 };
 
 constexpr int kCandidates = 32;
@@ -102,6 +104,7 @@ enum {
     kWorkWarpMax = 11,   //   the longest warp of the current round,
     kWorkWarpMaxSum = 13,//   the longest warps summed over rounds,
     kWorkWarpN = 15,     //   warp count
+    kWorkWarpMaxOdd = 17,//   the longest warp of the current round when it is odd (persistent solve)
     kWorkCount = 20
 };
 
@@ -111,17 +114,25 @@ struct Frontiers {
     u32 cap[kMaxH];
 };
 
-// Grid-wide barrier state of the persistent solve (zeroed before each launch).
+// Grid-wide barrier state of the persistent solve (zeroed before each launch);
+// flag: a decision taken by the block that releases a barrier (the batch's yield).
 struct GridSync {
     unsigned count, gen;
+    int flag, pad;
 };
+
+// The persistent solve keeps the frontier counters (kCountWords) twice, by round
+// parity: round r appends into counts + (r & 1) * kCountWords.
+constexpr int kCountSets = 2;
 
 // Launchers (mh_kernels.cu).
 void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
 // Rounds run on the device: every kernel reads the round index and the done /
 // overflow flags from Solve::state, so the host can enqueue many rounds ahead.
 // counts: kCountWords u32 (see shard_slot); cap values are per shard.
-void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts,
+// sets: frontier counter sets (and slot arrays, threshold words) to clear: 1 for the
+// one-kernel-per-phase path, kCountSets for a persistent solve.
+void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts, int sets,
                        cudaStream_t st);
 void launch_level1(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, cudaStream_t st);
 void launch_expand(const Cohort &c, const Solve &s, int level, const Frontiers &f, u32 *counts, int grid,
@@ -135,7 +146,11 @@ void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t 
 // It returns when the solve is done, a frontier overflowed (state) or a grid
 // barrier timed out (state error = kErrTimeout).
 int persistent_grid(int num_sms, bool large);
-int batch_grid(int num_sms);
+// The batched kernel comes in two builds, 3 or 4 co-resident blocks per SM (more
+// registers per thread, or more warps); batch_grid / batch_blocks_per_sm take the build.
+int batch_grid(int num_sms, int build);
+int batch_blocks_per_sm(int build);
+constexpr int kBatchBuilds[2] = {3, 4};
 
 // One cohort of a batched solve: its device state and its share of the grid
 // (blocks [first_block, first_block + nblocks)).
@@ -158,6 +173,7 @@ struct BatchMap {
     int *tab;
     GridSync *sync;
     int per_sm, num_sms;
+    int build;  // 3 or 4 blocks per SM
 };
 // Runs the cohorts of d_items (device array of n items) in one cooperative launch
 // of the whole batch grid (per_sm x num_sms blocks; blocks beyond the items' ranges
@@ -165,7 +181,6 @@ struct BatchMap {
 // the launch ends as soon as one cohort finishes or overflows a frontier: every
 // other team stops at its next round boundary.
 cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, const BatchMap &map, cudaStream_t st);
-int batch_blocks_per_sm();
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
                                     u32 *counts, int grid, bool large, cudaStream_t st);
 int level1_grid(const Cohort &c);

@@ -45,6 +45,20 @@ struct Team {
 };
 __device__ __forceinline__ Team grid_team() { return Team{(int)blockIdx.x, (int)gridDim.x}; }
 
+// Where a phase of one round takes its inputs and leaves its results.  One kernel
+// per phase: depth-1 records from the frontier, bests merged into s.slots, the
+// threshold in s.best_hint.  Persistent solve: depth-1 nodes built from the gene
+// rows and the block's copy of U (Ush), bests stored into the round's slot array,
+// the round's threshold word, diagnostics by round parity.
+struct RoundIO {
+    const u64 *Ush;
+    Key *slots;
+    bool overwrite;
+    u64 *hint;
+    int par;
+};
+__device__ __forceinline__ RoundIO launch_io(const Solve &s) { return RoundIO{nullptr, s.slots, false, s.best_hint, 0}; }
+
 __device__ __forceinline__ int prefix_gene(const Prefix &p, int i)
 {
     const u64 w = i < 4 ? p.w0 : p.w1;
@@ -144,19 +158,21 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
     return v;
 }
 
-// Block-wide best key -> slots[rank] (merged with what an earlier launch of the
-// same round left there).  All threads of the block must call it.
-__device__ void block_commit_best(Key best, Key *slots, int rank)
+// Block-wide best key -> slots[rank]: stored (overwrite), or merged with what an
+// earlier launch of the same round left there.  All threads of the block must call it.
+__device__ void block_commit_best(Key best, Key *slots, int rank, bool overwrite)
 {
-    __shared__ Key wbest[kWarpsPerBlock];
+    __shared__ Key wbest[kMaxWarpsPerBlock];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     best = warp_max_key(best);
     if (lane == 0) wbest[warp] = best;
     __syncthreads();
     if (warp == 0) {
-        Key k = lane < kWarpsPerBlock ? wbest[lane] : key_empty();
+        Key k = lane < (int)(blockDim.x >> 5) ? wbest[lane] : key_empty();
         k = warp_max_key(k);
-        if (lane == 0 && k.s != 0) {
+        if (lane == 0 && overwrite) {
+            slots[rank] = k;
+        } else if (lane == 0 && k.s != 0) {
             const Key old = slots[rank];
             if (key_better(k, old)) slots[rank] = k;
         }
@@ -241,7 +257,7 @@ __device__ __forceinline__ int my_shard(const Team &t)
 
 // Block-wide accumulation of counters: warps add into shared memory, then one
 // global atomic per counter and block (not per warp) at the end of a phase.
-constexpr int kAccN = 8;
+constexpr int kAccN = 10;  // 8, 9: depth-1 visited / pruned of a persistent round
 __device__ __forceinline__ void acc_begin(u64 *acc)
 {
     if (threadIdx.x < kAccN) acc[threadIdx.x] = 0;
@@ -282,19 +298,103 @@ struct Batch {
     u16 po[kBatch][kMaxH - 1];      // leaves: ascending original indices of each record's prefix
 };
 
-// Lane j takes record first + j*stride (if < count) into the warp scratch with
+// Depth-1 node of gene g (search order) built from its rows and U: y_1 = U & x_g,
+// n_1 = x^N_g, their sizes and, when few, their samples.  Returns |y_1| > 0.
+__device__ __forceinline__ bool gene_record(const Cohort &c, const u64 *Ush, int g, Rec &r)
+{
+    const u64 *trow = c.T + (size_t)g * c.WTp;
+    const u64 *nrow = c.N + (size_t)g * c.WNp;
+    int ky = 0, kn = 0;
+    for (int w = 0; w < c.Wt; ++w) ky += __popcll(trow[w] & Ush[w]);
+    for (int w = 0; w < c.Wn; ++w) kn += __popcll(nrow[w]);
+    r.p.w0 = (u64)g;
+    r.p.w1 = 0;
+    r.ky = sat16(ky);
+    r.kn = sat16(kn);
+    if (!is_dense(ky, kn)) {
+        int k = 0;
+        for (int w = 0; w < c.Wt; ++w)
+            for (u64 y = trow[w] & Ush[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        k = kListT;
+        for (int w = 0; w < c.Wn; ++w)
+            for (u64 y = nrow[w]; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+    }
+    return ky > 0;
+}
+
+// Work assignment of a phase.  The phase's records are cut into batches of R <= 32
+// records, R = ceil(records / warps) capped at 32 so that every warp gets work even
+// when records are few: batch B holds records B % nw + (B / nw * R + j) * nw,
+// j = 0..R-1, for nw warps.  Warp gw first takes the batches gw, gw + nw, ... of
+// the first three quarters of the rounds (static, no atomics); the last quarter is
+// handed out by kDispensers counters (warp gw draws from counter gw % kDispensers),
+// so warps that finish early take over the batches of slow ones.
+constexpr int kDispensers = 4;
+constexpr int kSmallWarps = 16;  // warps per block of the one-block-per-SM persistent build
+struct Dispenser {
+    u32 nw, gw, it, it_static, R;
+    u32 *ctr;
+    __device__ Dispenser(u32 nw_, u32 gw_, u32 count, u32 *ctrs) : nw(nw_), gw(gw_), it(0)
+    {
+        const u64 per_warp = ((u64)count + nw - 1) / nw;
+        R = per_warp < (u64)kBatch ? (u32)(per_warp ? per_warp : 1) : (u32)kBatch;
+        const u64 iters = ((u64)count + (u64)R * nw - 1) / ((u64)R * nw);
+        it_static = (u32)(iters - iters / 4);
+        ctr = ctrs + (gw % kDispensers) * kShardStride;
+    }
+    // First record of the warp's next batch, or >= the record count when the phase is done.
+    __device__ u64 next(int lane)
+    {
+        u64 B;
+        if (it < it_static) {
+            B = (u64)it * nw + gw;
+            ++it;
+        } else {
+            u32 d = 0;
+            if (lane == 0) d = atomicAdd(ctr, 1u);
+            d = __shfl_sync(kFull, d, 0);
+            B = (u64)it_static * nw + (gw % kDispensers) + (u64)d * kDispensers;
+        }
+        return (B % nw) + (B / nw) * R * nw;
+    }
+};
+
+// The dispenser counters of phase p (p = level - 2 for an expansion, h - 2 for
+// the leaves) in the unused depth-0 slots of a counter set.
+__device__ __forceinline__ u32 *dispenser_counters(u32 *counts, int p)
+{
+    return counts + shard_slot(0, kDispensers * p);
+}
+
+// Depth-1 counters of the nodes built by gene_record.
+struct Depth1 {
+    u64 visited = 0, pruned = 0;
+};
+
+// Lane j < R takes record first + j*stride (if < count) into the warp scratch with
 // its child range [last gene + 1, hi_bound]; counts its children as visited.
-// Returns the number of column words of the batch's sparse records (those with
-// samples, or all of them with `all_children`) and the bit mask of dense records.
-__device__ __forceinline__ int batch_prepare(const Rec *Fin, u32 cap_s, u64 first, u64 stride, u32 count, int L,
-                                             int hi_bound, bool all_children, Batch &b, int lane,
-                                             unsigned &dense_mask, u64 &visited, const u16 *orig = nullptr)
+// With io.Ush the records are the depth-1 nodes of genes 0 .. count-1, built from
+// the rows (empty ones are counted as pruned and have no children, unless
+// all_children).  Returns the number of column words of the batch's sparse records
+// (those with samples, or all of them with `all_children`) and the bit mask of
+// dense records.
+__device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io, Depth1 &d1, const Rec *Fin,
+                                             u32 cap_s, u64 first, u64 stride, int R, u32 count, int L, int hi_bound,
+                                             bool all_children, Batch &b, int lane, unsigned &dense_mask,
+                                             u64 &visited, const u16 *orig = nullptr)
 {
     const u64 i = first + (u64)lane * stride;
-    const bool valid = i < count;
+    bool valid = lane < R && i < count;
     int lo = 1, hi = 0, ky = 0, kn = 0;
-    if (valid) {
+    if (valid && io.Ush) {
+        const bool nonempty = gene_record(c, io.Ush, (int)i, b.r[lane]);
+        ++d1.visited;
+        d1.pruned += nonempty ? 0 : 1;
+        valid = nonempty || all_children;
+    } else if (valid) {
         load_rec(&b.r[lane], front_rec(Fin, cap_s, b.soff, (u32)i));
+    }
+    if (valid) {
         lo = prefix_gene(b.r[lane].p, L - 1) + 1;
         hi = hi_bound;
         ky = b.r[lane].ky;
@@ -524,13 +624,13 @@ __device__ void rescore_candidates(const Cohort &c, const Solve &s, const Team &
 // the non-empty ones (all of them with pruning off) become depth-1 records.
 // Every thread of the block must call it.
 __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts,
-                             const Team &t)
+                             const Team &t, const RoundIO &io)
 {
     __shared__ u64 acc[kAccN];
     const int lane = threadIdx.x & 31;
     const int h = s.h;
     acc_begin(acc);
-    if (h > 1) rescore_candidates(c, s, t);
+    if (h > 1 && !io.Ush) rescore_candidates(c, s, t);
     const int last = c.G - h;  // 0-based inclusive bound of depth 1
     u32 *my_count = counts + shard_slot(1, my_shard(t));
     Rec *out = f.F[1] + (size_t)my_shard(t) * f.cap[1];
@@ -585,7 +685,7 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const F
         r.kn = sat16(kn);
         copy_rec(&out[pos], &r);
     }
-    if (h == 1) block_commit_best(best, s.slots, t.rank);
+    if (h == 1) block_commit_best(best, io.slots, t.rank, io.overwrite);
     __syncthreads();
     if (threadIdx.x < 2 && acc[threadIdx.x])
         atomicAdd(s.cnt + ((size_t)round * h) * 2 + threadIdx.x, acc[threadIdx.x]);
@@ -603,10 +703,10 @@ __device__ __forceinline__ void warp_cycles(u64 *acc, long long t0, int lane)
     }
 }
 
-__device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc, int k)
+__device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc, int k, int par)
 {
     if (threadIdx.x == 5 && acc[5]) atomicAdd(s.work + kWorkWarpSum + k, acc[5]);
-    if (threadIdx.x == 6 && acc[6]) atomicMax(s.work + kWorkWarpMax + k, acc[6]);
+    if (threadIdx.x == 6 && acc[6]) atomicMax(s.work + (par ? kWorkWarpMaxOdd : kWorkWarpMax) + k, acc[6]);
     if (threadIdx.x == 7 && acc[7]) atomicAdd(s.work + kWorkWarpN + k, acc[7]);
 }
 
@@ -615,20 +715,23 @@ __device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc
 // block must call it; returns false (for every thread) if the input frontier
 // overflowed.
 __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int level, const Frontiers &f, u32 *counts,
-                             Batch &b, const Team &t)
+                             Batch &b, const Team &t, const RoundIO &io_in)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = level - 1;
+    RoundIO io = io_in;
+    if (level != 2) io.Ush = nullptr;  // depth-1 nodes are built only as the parents of depth 2
     if (threadIdx.x == 0) overflow = 0;
     acc_begin(acc);
-    const long long n_in = front_open(counts, level - 1, f.cap[level - 1], b.soff, lane);
+    const long long n_in = io.Ush ? (long long)(c.G - s.h + 1) : front_open(counts, level - 1, f.cap[level - 1], b.soff, lane);
     if (n_in < 0 && lane == 0) overflow = 1;
     __syncthreads();
     if (overflow) return false;
     const u32 count = (u32)n_in;
+    Depth1 d1;
     const Rec *Fin = f.F[level - 1];
     const u32 cap_in = f.cap[level - 1];
     const u32 cap = f.cap[level];
@@ -638,10 +741,11 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     const bool all_children = s.prune != 0;
     const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
-    for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
+    Dispenser disp((u32)nw, (u32)gw, count, dispenser_counters(counts, level - 2));
+    for (u64 first = disp.next(lane); first < count; first = disp.next(lane)) {
         unsigned dense;
-        const int total = batch_prepare(Fin, cap_in, gw + kb * nw, nw, count, L, hi_bound, all_children, b, lane,
-                                        dense, visited);
+        const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, hi_bound, all_children, b,
+                                        lane, dense, visited);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
@@ -723,15 +827,21 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
+    d1.visited = warp_sum_u64(d1.visited);
+    d1.pruned = warp_sum_u64(d1.pruned);
     if (lane == 0) {
         acc_add(acc, 0, visited);
         acc_add(acc, 1, visited - alive);
+        acc_add(acc, 8, d1.visited);
+        acc_add(acc, 9, d1.pruned);
     }
     warp_cycles(acc, t0, lane);
     __syncthreads();
     if (threadIdx.x < 2 && acc[threadIdx.x])
         atomicAdd(s.cnt + ((size_t)round * s.h + (level - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
-    warp_cycles_flush(s, acc, 0);
+    if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
+        atomicAdd(s.cnt + ((size_t)round * s.h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
+    warp_cycles_flush(s, acc, 0, io.par);
     return true;
 }
 
@@ -742,7 +852,7 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
 // leaves are tested (and counted) but not scored.  Every thread of the block
 // must call it; returns false (for every thread) if the input frontier overflowed.
 __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Frontiers &f, u32 *counts, Batch &b,
-                           const Team &t)
+                           const Team &t, const RoundIO &io_in)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -750,26 +860,31 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = s.h, L = h - 1;
+    RoundIO io = io_in;
+    if (h != 2) io.Ush = nullptr;  // depth-1 nodes are built only as the parents of the leaves of h = 2
     if (threadIdx.x == 0) overflow = 0;
     acc_begin(acc);
-    const long long n_in = front_open(counts, h - 1, f.cap[h - 1], b.soff, lane);
+    const long long n_in = io.Ush ? (long long)(c.G - 1) : front_open(counts, h - 1, f.cap[h - 1], b.soff, lane);
     if (n_in < 0 && lane == 0) overflow = 1;
     __syncthreads();
     if (overflow) return false;
     const u32 count = (u32)n_in;
+    Depth1 d1;
     const Rec *Fin = f.F[h - 1];
     const u32 cap_in = f.cap[h - 1];
     u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
     const u64 nn_term = s.a_den * (u64)c.Nn + 1;
     const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
-    for (u64 kb = 0; gw + kb * nw < count; kb += kBatch) {
+    Dispenser disp((u32)nw, (u32)gw, count, dispenser_counters(counts, h - 2));
+    for (u64 first = disp.next(lane); first < count; first = disp.next(lane)) {
         unsigned dense;
-        const int total = batch_prepare(Fin, cap_in, gw + kb * nw, nw, count, L, c.G - 1, false, b, lane, dense,
-                                        visited, c.orig);
-        prefixes += (u64)(gw + (kb + lane) * nw < count);
+        // (with pruning off, the empty depth-1 nodes built here still have leaves)
+        const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, c.G - 1,
+                                        io.Ush != nullptr && s.prune != 0, b, lane, dense, visited, c.orig);
+        prefixes += (u64)(lane < (int)disp.R && first + (u64)lane * nw < count);
         // only candidates at least as good as the best score known to exist can win
         u64 thr = 0;
-        if (lane == 0) thr = *(volatile u64 *)s.best_hint;
+        if (lane == 0) thr = *(volatile u64 *)io.hint;
         thr = warp_max_u64(thr > best.s ? thr : best.s);
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
@@ -831,19 +946,23 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
         }
         // publish the warp's best score so that other warps can skip hopeless records
         const u64 wbest = warp_max_u64(best.s);
-        if (lane == 0 && wbest > thr) atomicMax(s.best_hint, wbest);
+        if (lane == 0 && wbest > thr) atomicMax(io.hint, wbest);
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
     words = warp_sum_u64(words);
     prefixes = warp_sum_u64(prefixes);
     scored = warp_sum_u64(scored);
+    d1.visited = warp_sum_u64(d1.visited);
+    d1.pruned = warp_sum_u64(d1.pruned);
     if (lane == 0) {
         acc_add(acc, 0, visited);
         acc_add(acc, 1, visited - alive);
         acc_add(acc, 2, words);
         acc_add(acc, 3, prefixes);
         acc_add(acc, 4, scored);
+        acc_add(acc, 8, d1.visited);
+        acc_add(acc, 9, d1.pruned);
     }
     warp_cycles(acc, t0, lane);
     // dense records counted through the block's slot 7 is taken: use an atomic per warp (rare)
@@ -854,8 +973,10 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     if (threadIdx.x == 2 && acc[2]) atomicAdd(s.work + kWorkColWords, acc[2]);
     if (threadIdx.x == 3 && acc[3]) atomicAdd(s.work + kWorkPrefixes, acc[3]);
     if (threadIdx.x == 4 && acc[4]) atomicAdd(s.work + kWorkScored, acc[4]);
-    warp_cycles_flush(s, acc, 1);
-    block_commit_best(best, s.slots, t.rank);
+    if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
+        atomicAdd(s.cnt + ((size_t)round * h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
+    warp_cycles_flush(s, acc, 1, io.par);
+    block_commit_best(best, io.slots, t.rank, io.overwrite);
     return true;
 }
 
@@ -979,14 +1100,15 @@ __global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
 __global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Frontiers f, u32 *counts)
 {
     if (halted(s)) return;
-    phase_level1(c, s, s.state[kStRound], f, counts, grid_team());
+    phase_level1(c, s, s.state[kStRound], f, counts, grid_team(), launch_io(s));
 }
 
 __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
-    if (!phase_expand(c, s, s.state[kStRound], level, f, counts, scratch[threadIdx.x >> 5], grid_team()) &&
+    if (!phase_expand(c, s, s.state[kStRound], level, f, counts, scratch[threadIdx.x >> 5], grid_team(),
+                      launch_io(s)) &&
         threadIdx.x == 0)
         s.state[kStOverflow] = 1;
 }
@@ -995,7 +1117,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, Frontie
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
-    if (!phase_leaf(c, s, s.state[kStRound], f, counts, scratch[threadIdx.x >> 5], grid_team()) && threadIdx.x == 0)
+    if (!phase_leaf(c, s, s.state[kStRound], f, counts, scratch[threadIdx.x >> 5], grid_team(), launch_io(s)) &&
+        threadIdx.x == 0)
         s.state[kStOverflow] = 1;
 }
 
@@ -1010,7 +1133,9 @@ __global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *c
 
 // Grid barrier with a bounded wait: a block that waits longer than about two
 // seconds records a timeout in the state and returns false instead of hanging.
-__device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks)
+// With `sample`, the block that releases the barrier copies *sample into g->flag
+// first, so every block reads the same value after the barrier.
+__device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, const int *sample = nullptr)
 {
     __shared__ int ok;
     __syncthreads();
@@ -1020,6 +1145,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks)
         __threadfence();
         const unsigned arrived = atomicAdd(&g->count, 1u) + 1u;
         if (arrived == (unsigned)nblocks) {
+            if (sample) *(volatile int *)&g->flag = *(volatile const int *)sample;
             atomicExch(&g->count, 0u);
             __threadfence();
             atomicAdd(&g->gen, 1u);
@@ -1047,13 +1173,163 @@ __device__ __forceinline__ u64 global_ns()
     return t;
 }
 
-// The greedy loop of one cohort run by a team of co-resident blocks, its phases
-// separated by the team's barrier.  Returns when the solve is done, a frontier
-// overflowed or a barrier timed out (recorded in the cohort's state).
-__device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts,
+// Re-scores keys[0 .. kCandidates) against U (the block's copy): the largest S + 1
+// of a key that still covers an uncovered tumor is a candidate score of the round,
+// a lower bound on its best; merged into *hint.  A warp takes 32 / lpk keys at a
+// time, lpk lanes each (one lane per row word), and issues the loads of all their
+// rows together.
+__device__ void block_rescore(const Cohort &c, const Solve &s, const Key *keys, const u64 *Ush, u64 *hint)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int h = s.h;
+    int lpk = 1;
+    while (lpk < c.Wt || lpk < c.Wn || lpk < h) lpk <<= 1;
+    const int kpp = 32 / lpk, sub = lane / lpk, w = lane % lpk, lead = lane - w;
+    u64 best = 0;
+    for (int base = warp * kpp; base < kCandidates; base += nwarps * kpp) {
+        const int i = base + sub;
+        const Key k = i < kCandidates ? keys[i] : key_empty();
+        const bool live = k.s != 0;
+        const int gq = (live && w < h) ? (int)c.inv[key_get(k, w)] : 0;
+        u64 y = (live && w < c.Wt) ? Ush[w] : 0ull;
+        u64 n = (live && w < c.Wn) ? ~0ull : 0ull;
+#pragma unroll
+        for (int q = 0; q < kMaxH; ++q) {
+            if (q >= h) break;
+            const int g = __shfl_sync(kFull, gq, lead + q);
+            if (live && w < c.Wt) y &= c.T[(size_t)g * c.WTp + w];
+            if (live && w < c.Wn) n &= c.N[(size_t)g * c.WNp + w];
+        }
+        int tp = __popcll(y), fp = __popcll(n);
+        for (int off = lpk >> 1; off; off >>= 1) {
+            tp += __shfl_xor_sync(kFull, tp, off);
+            fp += __shfl_xor_sync(kFull, fp, off);
+        }
+        if (live && tp > 0) {
+            const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+            best = s1 > best ? s1 : best;
+        }
+    }
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(hint, best);
+}
+
+// End of round r of the persistent solve, run by EVERY block of the team on the
+// same inputs, so that all of them reach the same decisions without another
+// barrier: the winner (largest key of the round's slots), its TP / FP, the next U
+// (DelCols on the block's copy Ush, then written to s.U: every block writes the
+// same words), the next round's candidates (cand_sh) and their rescored threshold
+// (merged into next_hint).  Rank 0 also records the selection, the round state and
+// the candidates (for a later launch).  Returns true when the solve is done.
+__device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots, const Team &t,
+                             u64 *Ush, Key *cand_sh, u64 *next_hint)
+{
+    __shared__ Key wbest[kMaxWarpsPerBlock];
+    __shared__ int gs[kMaxH], os[kMaxH];
+    __shared__ int done_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int h = s.h;
+    const bool lead = t.rank == 0;
+    Key best = key_empty();
+    for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
+        Key k;
+        k.s = __ldcg(&slots[i].s);
+        k.t0 = __ldcg(&slots[i].t0);
+        k.t1 = __ldcg(&slots[i].t1);
+        k.t2 = __ldcg(&slots[i].t2);
+        if (key_better(k, best)) best = k;
+    }
+    // the best kCandidates of the warps' lane bests become next round's candidates
+    Key mine = best;
+    const int per_warp = (kCandidates + nwarps - 1) / nwarps;
+    for (int r = 0; r < per_warp; ++r) {
+        const Key m = warp_max_key(mine);
+        const int idx = warp * per_warp + r;
+        if (lane == 0 && idx < kCandidates) {
+            cand_sh[idx] = m;
+            if (lead) s.cand[idx] = m;
+        }
+        if (m.s != 0 && mine.s == m.s && mine.t0 == m.t0 && mine.t1 == m.t1 && mine.t2 == m.t2) mine = key_empty();
+        if (r == 0 && lane == 0) wbest[warp] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        best = lane < nwarps ? wbest[lane] : key_empty();
+        best = warp_max_key(best);
+        const bool last_round = round + 1 >= *(volatile int *)&s.state[kStMaxRounds];
+        if (lead && lane < 2) {  // diagnostics: the round's longest warps
+            const int mx = ((round & 1) ? kWorkWarpMaxOdd : kWorkWarpMax) + lane;
+            s.work[kWorkWarpMaxSum + lane] += __ldcg(&s.work[mx]);
+            s.work[mx] = 0;
+        }
+        bool done = true;
+        if (best.s != 0) {
+            if (lane < h) {
+                const int o = key_get(best, lane);
+                os[lane] = o;
+                gs[lane] = (int)c.inv[o];
+            }
+            __syncwarp();
+            u64 y = 0, n = 0, u = 0;
+            if (lane < c.Wt) {
+                u = Ush[lane];
+                y = u;
+                for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+            }
+            if (lane < c.Wn) {
+                n = ~0ull;
+                for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
+            }
+            int tp = __popcll(y), fp = __popcll(n);
+            for (int off = 16; off; off >>= 1) {
+                tp += __shfl_xor_sync(kFull, tp, off);
+                fp += __shfl_xor_sync(kFull, fp, off);
+            }
+            __syncwarp();
+            if (lane < c.Wt) {
+                u &= ~y;
+                Ush[lane] = u;
+                s.U[lane] = u;
+            }
+            const unsigned left = __ballot_sync(kFull, u != 0);
+            done = !left || last_round;
+            if (lead && lane == 0) {
+                const int k = *(volatile int *)&s.state[kStK];
+                int *r = s.res + (size_t)k * (h + 2);
+                for (int i = 0; i < h; ++i) r[i] = os[i];
+                r[h] = tp;
+                r[h + 1] = fp;
+                s.state[kStK] = k + 1;
+            }
+        }
+        if (lane == 0) {
+            done_sh = done;
+            if (lead) {
+                s.state[kStRound] = round + 1;
+                if (done) s.state[kStDone] = 1;
+            }
+        }
+    }
+    __syncthreads();
+    const bool done = done_sh != 0;
+    if (!done && h > 1) block_rescore(c, s, cand_sh, Ush, next_hint);
+    return done;
+}
+
+// The greedy loop of one cohort run by a team of co-resident blocks.  A round is
+// the depth-2 .. h-1 expansions (depth 1 built on the fly from the gene rows), the
+// leaves, a barrier, and the end of round computed redundantly by every block, so
+// rounds are separated by h - 1 barriers.  Data indexed by round parity: the slots
+// the blocks' bests go to, the frontier counters and the threshold word; rank 0
+// clears the next round's set at the start of a round (all reads of it ended
+// before the previous round's last barrier).  Returns when the solve is done, a
+// frontier overflowed, a barrier timed out (recorded in the cohort's state) or,
+// in a batch, the barrier that ended a round carried a yield request.
+__device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts_base,
                            const Team &t, Batch &b, int *yield = nullptr)
 {
-    __shared__ int stop;
+    __shared__ u64 Ush[kMaxWords];
+    __shared__ Key cand_sh[kCandidates];
     const int h = s.h;
     const bool timer = t.rank == 0 && threadIdx.x == 0;
     u64 tm = timer ? global_ns() : 0;
@@ -1064,20 +1340,27 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
             tm = now;
         }
     };
+    if (*(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStError]) return;
+    int round = *(volatile int *)&s.state[kStRound];
+    // start of a launch: U and the candidates left by the previous round
+    for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x) Ush[i] = i < c.WTp ? __ldcg(&s.U[i]) : 0ull;
+    for (int i = threadIdx.x; i < kCandidates; i += blockDim.x) {
+        cand_sh[i].s = __ldcg(&s.cand[i].s);
+        cand_sh[i].t0 = __ldcg(&s.cand[i].t0);
+        cand_sh[i].t1 = __ldcg(&s.cand[i].t1);
+        cand_sh[i].t2 = __ldcg(&s.cand[i].t2);
+    }
+    __syncthreads();
+    if (h > 1) block_rescore(c, s, cand_sh, Ush, s.best_hint + (round & 1));
     for (;;) {
-        // the decision to stop is read from the cohort's state, written before the
-        // barrier that ended the previous round: every block of the team agrees
-        if (threadIdx.x == 0)
-            stop = *(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStOverflow] |
-                   *(volatile int *)&s.state[kStError] | *(volatile int *)&s.state[kStYield];
-        __syncthreads();
-        if (stop) return;
-        const int round = *(volatile int *)&s.state[kStRound];
-        phase_level1(c, s, round, f, counts, t);
-        if (!grid_sync(gsync, s.state, t.size)) return;
-        lap(0);
-        // every block reads the same shard counts after the same barrier, so an
-        // overflow is seen by all of them and they leave together
+        const int par = round & 1;
+        u32 *counts = counts_base + (size_t)par * kCountWords;
+        const RoundIO io{Ush, s.slots + (size_t)par * s.nslots, true, s.best_hint + par, par};
+        if (t.rank == 0) {  // the next round's counters and threshold start from zero
+            u32 *cn = counts_base + (size_t)(par ^ 1) * kCountWords;
+            for (int i = threadIdx.x; i < kMaxH * kShards; i += blockDim.x) cn[i * kShardStride] = 0;
+            if (threadIdx.x == 0) *(volatile u64 *)(s.best_hint + (par ^ 1)) = 0;
+        }
         // on an overflow the team stops; in a batch it also asks the other teams to
         // stop at their next round boundary, so that the host can grow the frontier
         // and relaunch without leaving the team's blocks idle
@@ -1090,48 +1373,57 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
         };
-        for (int l = 2; l <= h - 1; ++l) {
-            if (!phase_expand(c, s, round, l, f, counts, b, t)) {
+        if (h == 1) {
+            phase_level1(c, s, round, f, counts, t, io);
+            lap(0);
+        } else {
+            // every block reads the same shard counts after the same barrier, so an
+            // overflow is seen by all of them and they leave together
+            for (int l = 2; l <= h - 1; ++l) {
+                if (!phase_expand(c, s, round, l, f, counts, b, t, io)) {
+                    overflow();
+                    return;
+                }
+                if (!grid_sync(gsync, s.state, t.size)) return;
+            }
+            lap(1);
+            if (!phase_leaf(c, s, round, f, counts, b, t, io)) {
                 overflow();
                 return;
             }
-            if (!grid_sync(gsync, s.state, t.size)) return;
         }
-        lap(1);
-        if (h >= 2) {
-            if (!phase_leaf(c, s, round, f, counts, b, t)) {
-                overflow();
-                return;
-            }
-            if (!grid_sync(gsync, s.state, t.size)) return;
-        }
+        // the round's last barrier; in a batch its releasing block samples the yield
+        // request, so that every block of the team takes the same decision
+        if (!grid_sync(gsync, s.state, t.size, yield)) return;
+        const bool stop = yield && *(volatile int *)&gsync->flag;
         lap(2);
-        if (t.rank == 0) {
-            phase_finalize(c, s, counts, t.size);
+        const bool done = end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1));
+        lap(3);
+        if (done) {
             // batch: a team that finished asks the others to stop after their current
             // round, so that the host can hand its blocks to the unfinished cohorts
-            if (yield && threadIdx.x == 0) {
-                if (*(volatile int *)&s.state[kStDone]) {
-                    *(volatile int *)yield = 1;  // may be host memory: a plain store, made visible
-                    __threadfence_system();
-                } else if (*(volatile int *)yield) {
-                    s.state[kStYield] = 1;
-                }
+            if (yield && t.rank == 0 && threadIdx.x == 0) {
+                *(volatile int *)yield = 1;  // may be host memory: a plain store, made visible
+                __threadfence_system();
             }
+            return;
         }
-        if (!grid_sync(gsync, s.state, t.size)) return;
-        lap(3);
+        ++round;
+        if (stop) {
+            if (t.rank == 0 && threadIdx.x == 0) s.state[kStYield] = 1;
+            return;
+        }
     }
 }
 
-// Two builds of the persistent solve: one block per SM with registers to spare
-// (cheaper grid barriers: the small, latency-bound cohorts) and four blocks per SM
-// (more warps to hide memory latency: the large ones).
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+// Two builds of the persistent solve: one block per SM (a cheap grid barrier: the
+// small, latency-bound cohorts) and four blocks per SM (more warps to hide memory
+// latency: the large ones).
+template <int kMinBlocks, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
 {
-    __shared__ Batch scratch[kWarpsPerBlock];
+    __shared__ Batch scratch[kWarps];
     solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5]);
 }
 
@@ -1163,7 +1455,9 @@ __device__ int sm_major_block(const BatchMap &m)
 // Batched solve: block b (SM-major number, or blockIdx.x if that numbering failed
 // anywhere in the grid) works on the cohort whose block range holds b, with the
 // blocks of that range as its team; cohorts progress independently.
-__global__ void __launch_bounds__(kThreads, 4) k_solve_batch(const BatchItem *items, int n, int *yield, BatchMap map)
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_solve_batch(const BatchItem *items, int n, int *yield, BatchMap map)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     __shared__ int vb_s;
@@ -1212,15 +1506,15 @@ void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samp
     k_transpose<<<(unsigned)blocks, threads, 0, st>>>(c.G, rows, row_stride, samples, c.GW, cols);
 }
 
-void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts,
+void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int max_rounds, u32 *counts, int sets,
                        cudaStream_t st)
 {
     cudaMemsetAsync(s.cnt, 0, sizeof(u64) * 2 * (size_t)s.h * (size_t)counter_rounds, st);
-    cudaMemsetAsync(s.slots, 0, sizeof(Key) * (size_t)s.nslots, st);
+    cudaMemsetAsync(s.slots, 0, sizeof(Key) * (size_t)s.nslots * sets, st);
     cudaMemsetAsync(s.cand, 0, sizeof(Key) * (size_t)kCandidates, st);
     cudaMemsetAsync(s.work, 0, sizeof(u64) * kWorkCount, st);
-    cudaMemsetAsync(s.best_hint, 0, sizeof(u64), st);
-    cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords, st);
+    cudaMemsetAsync(s.best_hint, 0, sizeof(u64) * sets, st);
+    cudaMemsetAsync(counts, 0, sizeof(u32) * kCountWords * sets, st);
     k_solve_init<<<1, 64, 0, st>>>(c, s, max_rounds);
 }
 
@@ -1251,20 +1545,22 @@ int persistent_grid(int num_sms, bool large)
 {
     int per_sm = 0;
     const cudaError_t e = large
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<4>, kThreads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<1>, kThreads, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<4, kWarpsPerBlock>, kThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<1, kSmallWarps>, kSmallWarps * 32, 0);
     if (e != cudaSuccess || per_sm < 1) return 0;
     return (large ? per_sm : 1) * num_sms;
 }
 
-int batch_blocks_per_sm()
+int batch_blocks_per_sm(int build)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch, kThreads, 0) != cudaSuccess) return 0;
-    return per_sm;
+    const cudaError_t e = build == 3
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<3>, kThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<4>, kThreads, 0);
+    return e == cudaSuccess ? per_sm : 0;
 }
 
-int batch_grid(int num_sms) { return batch_blocks_per_sm() * num_sms; }
+int batch_grid(int num_sms, int build) { return batch_blocks_per_sm(build) * num_sms; }
 
 cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, const BatchMap &m, cudaStream_t st)
 {
@@ -1279,7 +1575,8 @@ cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, co
     if (e != cudaSuccess) return e;
     void *args[] = {&items, &nn, &yield, &map};
     const int grid = map.per_sm * map.num_sms;
-    return cudaLaunchCooperativeKernel((const void *)k_solve_batch, dim3(grid), dim3(kThreads), args, 0, st);
+    const void *fn = map.build == 3 ? (const void *)k_solve_batch<3> : (const void *)k_solve_batch<4>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
@@ -1289,8 +1586,8 @@ cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Front
     Solve ss = s;
     Frontiers ff = f;
     void *args[] = {&cc, &ss, &ff, &gsync, &counts};
-    const void *fn = large ? (const void *)k_solve<4> : (const void *)k_solve<1>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
+    const void *fn = large ? (const void *)k_solve<4, kWarpsPerBlock> : (const void *)k_solve<1, kSmallWarps>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(large ? kThreads : kSmallWarps * 32), args, 0, st);
 }
 
 }  // namespace mh

@@ -272,7 +272,7 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     NA_CUDA(cudaStreamSynchronize(st));
     if (hs[2]) return na_fail(MH_EINVAL, "mh_solve_noalloc: padding bits past Nt or Nn are set");
 
-    launch_solve_init(c, s, kNaRounds, Nt + 1, counts, st);
+    launch_solve_init(c, s, kNaRounds, Nt + 1, counts, 1, st);
     const int grid = leaf_blocks;
     // rounds run on the device; the host enqueues them in growing batches
     int batch = 4, rounds = 0;
