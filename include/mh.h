@@ -185,14 +185,17 @@ MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, 
 
 /* ---- Served runtime: continuous batching of solves ------------------------
  * A server owns a scheduler thread.  Submitted requests (a cohort in host
- * memory, h, alpha) wait in FIFO order until a slot and device memory are free:
- * admission uploads the cohort (as mh_create) when its estimated footprint
- * (store, workspace and, for h >= 3, the search frontiers estimated from the
- * (h-1)-gene sets sharing a tumor) fits the memory budget.  Active requests are
- * solved together, a team of blocks each, by the batched kernel; a launch ends at
- * a round boundary when a request finishes or a queued request can start, so new
- * requests join at the next round of the others (continuous batching) and every
- * cohort stays resident on the device between its rounds.  Results are those of
+ * memory, h, alpha) wait in arrival order until a slot and device memory are
+ * free: admission packs the cohort and uploads it (copies only, while a launch
+ * may be running) when its estimated footprint (store, workspace and, for h >= 3,
+ * the search frontiers estimated from the gene sets sharing a tumor) fits the
+ * memory budget.  A launch ends at a round boundary when a request finishes or an
+ * admitted one is ready, so new requests join at the next round of the others
+ * (continuous batching) and every cohort stays resident on the device between its
+ * rounds.  Small requests run batched (a team of whole SMs each, the batched
+ * kernel); while any is active, "large" requests (see large_slots) pause at
+ * their round boundary, and a large request runs on the whole GPU on the
+ * single-cohort kernel when no small one is active.  Results are those of
  * mh_solve (MH_MODE_PERSISTENT); a served result's solve_ms is the request's
  * latency from submission to completion. */
 typedef struct mh_server mh_server;
@@ -200,11 +203,10 @@ typedef struct {
     int64_t hbm_budget_bytes; /* device memory for active requests; <= 0: 80% of the free memory */
     int32_t slots;            /* requests solved concurrently; <= 0: 8 */
     int32_t large_slots;      /* "large" requests (more than 4e6 (h-1)-gene sets sharing a tumor, the
-                                 size at which one request keeps the whole GPU busy) solved
-                                 concurrently; <= 0: 1.  Large requests start in arrival order;
+                                 size at which one request keeps the whole GPU busy) admitted
+                                 at a time; <= 0: 1.  Large requests start in arrival order;
                                  smaller ones queued behind a waiting large one may start first
-                                 (backfill), so a large request is not slowed by those that
-                                 arrive after it is admitted */
+                                 (backfill) */
 } mh_server_opts;
 
 /* Starts a server on the current device.  opts may be NULL (defaults).

@@ -993,12 +993,23 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             MH_CUDA(cudaMemsetAsync(hs[i]->dState + 6, 0, sizeof(int), st));  // yield request
         }
         MH_CUDA(cudaMemsetAsync(d_yield, 0, sizeof(int), st));
-        MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st));
-        MH_CUDA(launch_solve_batch(g_items, (int)items.size(), act.size() > 1 ? d_yield : nullptr, map, st));
-        MH_CUDA(cudaStreamSynchronize(st));
-        int fell_back = 0;  // the launch numbered its blocks by blockIdx.x
-        MH_CUDA(cudaMemcpy(&fell_back, map.tab + 2 * kMaxSmid + 1, sizeof(int), cudaMemcpyDeviceToHost));
-        if (fell_back && sm_major) *sm_major = 0;
+        if (act.size() == 1 && !fixed) {
+            // one cohort left: the single-cohort persistent kernel (its fields are kernel
+            // parameters, which the compiler keeps out of registers)
+            mh_handle *H = hs[act[0]];
+            const bool large = work_estimate(H, opts[act[0]].h - 1) > kLargeWork;
+            MH_CUDA(launch_solve_persistent(H->c, ss[act[0]], frontiers_of(H), H->dSync, H->dCounts,
+                                            persistent_grid(H->num_sms, large), large, st));
+            MH_CUDA(cudaStreamSynchronize(st));
+        } else {
+            MH_CUDA(cudaMemcpyAsync(g_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                                    st));
+            MH_CUDA(launch_solve_batch(g_items, (int)items.size(), act.size() > 1 ? d_yield : nullptr, map, st));
+            MH_CUDA(cudaStreamSynchronize(st));
+            int fell_back = 0;  // the launch numbered its blocks by blockIdx.x
+            MH_CUDA(cudaMemcpy(&fell_back, map.tab + 2 * kMaxSmid + 1, sizeof(int), cudaMemcpyDeviceToHost));
+            if (fell_back && sm_major) *sm_major = 0;
+        }
         for (int i : act) {
             mh_handle *H = hs[i];
             MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
@@ -1324,11 +1335,21 @@ struct mh_server {
         return true;
     }
 
+    // One launch over the active requests.  Small requests go first: while any is
+    // active, the large ones pause at their round boundary (their state stays on the
+    // device) and the small ones run batched; a large request runs when no small one
+    // is active, alone on the single-cohort kernel (or batched with the other large
+    // ones when large_slots > 1).  A large solve keeps the whole GPU busy and runs
+    // fastest alone, while small solves are latency-bound and gain from sharing.
     void run_active()
     {
-        const int n = (int)active.size();
+        std::vector<ServerReq *> sel;
+        for (ServerReq *r : active)
+            if (!r->large) sel.push_back(r);
+        if (sel.empty()) sel = active;
+        const int n = (int)sel.size();
         std::vector<double> work(n);
-        for (int i = 0; i < n; ++i) work[i] = active[i]->work;
+        for (int i = 0; i < n; ++i) work[i] = sel[i]->work;
         const std::vector<int> blocks = split_grid(work, 0.75, num_sms, kServerBuild);
         if (items_cap < n) {
             cudaFree(d_items);
@@ -1340,9 +1361,9 @@ struct mh_server {
         std::vector<BatchItem> items(n);
         int first = 0;
         for (int i = 0; i < n; ++i) {
-            mh_handle *H = active[i]->H;
+            mh_handle *H = sel[i]->H;
             items[i].c = H->c;
-            items[i].s = active[i]->s;
+            items[i].s = sel[i]->s;
             items[i].f = frontiers_of(H);
             items[i].gsync = H->dSync;
             items[i].counts = H->dCounts;
@@ -1353,11 +1374,19 @@ struct mh_server {
             cudaMemsetAsync(H->dState + 6, 0, sizeof(int), st);
         }
         *(volatile int *)h_yield = 0;
-        cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
         cudaEvent_t ev;
         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms, kServerBuild), st) !=
-            cudaSuccess) {
+        cudaError_t e;
+        if (n == 1) {  // a lone request: the single-cohort persistent kernel, which yields the same way
+            ServerReq *r = sel[0];
+            mh_handle *H = r->H;
+            e = launch_solve_persistent(H->c, r->s, frontiers_of(H), H->dSync, H->dCounts,
+                                        persistent_grid(num_sms, r->large), r->large, st, d_yield);
+        } else {
+            cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
+            e = launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms, kServerBuild), st);
+        }
+        if (e != cudaSuccess) {
             cudaEventDestroy(ev);
             return;
         }

@@ -181,8 +181,9 @@ struct BatchMap {
 // the launch ends as soon as one cohort finishes or overflows a frontier: every
 // other team stops at its next round boundary.
 cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, const BatchMap &map, cudaStream_t st);
+// yield: as for launch_solve_batch (the server runs a lone request this way), or NULL.
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
-                                    u32 *counts, int grid, bool large, cudaStream_t st);
+                                    u32 *counts, int grid, bool large, cudaStream_t st, int *yield = nullptr);
 int level1_grid(const Cohort &c);
 
 // Message returned by mh_last_error() on the calling thread.

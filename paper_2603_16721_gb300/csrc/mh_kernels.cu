@@ -1421,10 +1421,10 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
 // latency: the large ones).
 template <int kMinBlocks, int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
-    k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts)
+    k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts, int *yield)
 {
     __shared__ Batch scratch[kWarps];
-    solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5]);
+    solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5], yield);
 }
 
 // SM-major number of the calling block (thread 0): SMs are ranked in the order
@@ -1580,12 +1580,12 @@ cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, co
 }
 
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
-                                    u32 *counts, int grid, bool large, cudaStream_t st)
+                                    u32 *counts, int grid, bool large, cudaStream_t st, int *yield)
 {
     Cohort cc = c;
     Solve ss = s;
     Frontiers ff = f;
-    void *args[] = {&cc, &ss, &ff, &gsync, &counts};
+    void *args[] = {&cc, &ss, &ff, &gsync, &counts, &yield};
     const void *fn = large ? (const void *)k_solve<4, kWarpsPerBlock> : (const void *)k_solve<1, kSmallWarps>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(large ? kThreads : kSmallWarps * 32), args, 0, st);
 }
