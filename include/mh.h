@@ -160,6 +160,15 @@ MH_API void mh_destroy(mh_handle *handle);
 /* Message of the last error on the calling thread ("" if none). */
 MH_API const char *mh_last_error(void);
 
+/* Diagnostic (no counterpart in the paper): checks the bounded device-side wait
+ * that every barrier of the persistent kernels uses.  One block enters a barrier
+ * that no other block reaches; the wait gives up after its bound (about two to
+ * five seconds), records the timeout and returns, and the CUDA context stays
+ * usable.  *status receives MH_ETIMEOUT when the wait ended by its bound (the
+ * expected outcome).  Returns MH_OK when the check ran, MH_EINVAL (NULL status)
+ * or MH_ECUDA otherwise. */
+MH_API int mh_check_bounded_wait(int32_t *status);
+
 /* Batched solve: n cohorts (distinct handles, one device) with their options are
  * solved by cooperative launches of one persistent kernel.  The co-resident grid
  * is split into teams of blocks, team i running the greedy loop of cohort i

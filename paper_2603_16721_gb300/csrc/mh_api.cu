@@ -559,6 +559,27 @@ extern "C" {
 
 MH_API const char *mh_last_error(void) { return g_last_error.c_str(); }
 
+MH_API int mh_check_bounded_wait(int32_t *status)
+{
+    if (!status) return fail(MH_EINVAL, "status is NULL");
+    *status = MH_OK;
+    GridSync *g = nullptr;
+    int *state = nullptr;
+    MH_CUDA(cudaMalloc((void **)&g, sizeof(GridSync)));
+    cudaError_t e = cudaMalloc((void **)&state, sizeof(int) * kStateWords);
+    if (e == cudaSuccess) e = cudaMemset(g, 0, sizeof(GridSync));
+    if (e == cudaSuccess) e = cudaMemset(state, 0, sizeof(int) * kStateWords);
+    if (e == cudaSuccess) e = launch_barrier_probe(g, state, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int hs[kStateWords] = {};
+    if (e == cudaSuccess) e = cudaMemcpy(hs, state, sizeof hs, cudaMemcpyDeviceToHost);
+    cudaFree(g);
+    cudaFree(state);
+    if (e != cudaSuccess) return fail(MH_ECUDA, "mh_check_bounded_wait: %s", cudaGetErrorString(e));
+    *status = hs[2] == kErrTimeout ? MH_ETIMEOUT : MH_OK;  // state word 2: error
+    return MH_OK;
+}
+
 MH_API int mh_create(const uint64_t *bitmaps, int32_t G, int32_t Nt, int32_t Nn, mh_handle **out)
 {
     if (!out) return fail(MH_EINVAL, "out is NULL");

@@ -185,6 +185,9 @@ cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, co
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
                                     u32 *counts, int grid, bool large, cudaStream_t st, int *yield = nullptr);
 int level1_grid(const Cohort &c);
+// One block waiting at a barrier that no other block reaches (the bounded wait's
+// timeout path); state: kStateWords zeroed ints.
+cudaError_t launch_barrier_probe(GridSync *g, int *state, cudaStream_t st);
 
 // Message returned by mh_last_error() on the calling thread.
 void set_error_text(const char *text);

@@ -1416,6 +1416,10 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     }
 }
 
+// Diagnostic: one block enters a team barrier sized for two blocks, so the wait
+// can only end by its bound; the timeout is recorded in state[kStError].
+__global__ void k_barrier_probe(GridSync *g, int *state) { grid_sync(g, state, 2); }
+
 // Two builds of the persistent solve: one block per SM (a cheap grid barrier: the
 // small, latency-bound cohorts) and four blocks per SM (more warps to hide memory
 // latency: the large ones).
@@ -1549,6 +1553,12 @@ int persistent_grid(int num_sms, bool large)
         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<1, kSmallWarps>, kSmallWarps * 32, 0);
     if (e != cudaSuccess || per_sm < 1) return 0;
     return (large ? per_sm : 1) * num_sms;
+}
+
+cudaError_t launch_barrier_probe(GridSync *g, int *state, cudaStream_t st)
+{
+    k_barrier_probe<<<1, 32, 0, st>>>(g, state);
+    return cudaGetLastError();
 }
 
 int batch_blocks_per_sm(int build)

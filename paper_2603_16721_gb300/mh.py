@@ -101,6 +101,16 @@ def load():
     return lib
 
 
+def mh_check_bounded_wait() -> int:
+    """Status of a barrier wait that only its bound can end (MH_ETIMEOUT expected)."""
+    lib = load()
+    lib.mh_check_bounded_wait.restype = ctypes.c_int
+    lib.mh_check_bounded_wait.argtypes = [ctypes.POINTER(ctypes.c_int32)]
+    st = ctypes.c_int32(0)
+    _check(lib.mh_check_bounded_wait(ctypes.byref(st)))
+    return int(st.value)
+
+
 def mh_last_error() -> str:
     return load().mh_last_error().decode()
 
