@@ -165,8 +165,9 @@ def solve_roofline(res_list, Nt, Nn, peaks, source):
     duration (CUDA events around its launch on the solving stream);
     peak = SMs x 64 int32 ops/clk x max SM clock.  The kernel tests 64 sibling
     leaves with one OR per sample column word (bit-sliced), so it issues far fewer
-    operations than the per-node count; `issued` gives the kernel's own count of
-    the integer operations of its leaf phase over that phase's time."""
+    operations than the per-node count; `issued` estimates the integer operations
+    the kernel itself executes in its leaf phase (from its own counters of column
+    words and exactly scored leaves) over that phase's time."""
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = SMS * INT32_OPS_PER_SM_CLK * clk / 1e12
     ops = [algorithmic_ops(r, Nt, Nn) for r in res_list]
@@ -179,7 +180,9 @@ def solve_roofline(res_list, Nt, Nn, peaks, source):
     leaf = None
     if leaf_s > 0:
         la = sum(o[1] for o in ops) / leaf_s / 1e12
-        issued = sum(r.leaf_alu_ops for r in res_list) / leaf_s / 1e12
+        # the kernel's own work in the leaf phase: 2 int32 ops per 64-bit column word
+        # OR-ed in a sibling test (counted by the kernel) + ~14 per leaf scored exactly
+        issued = sum(2 * r.leaf_words + 14 * r.leaf_scored for r in res_list) / leaf_s / 1e12
         leaf = {"achieved": round(la, 4), "frac": round(la / peak, 4), "ms_per_solve": round(leaf_s * 1e3 / len(res_list), 4),
                 "issued": round(issued, 4), "issued_frac": round(issued / peak, 5)}
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s (int32)",
