@@ -11,6 +11,7 @@
 #include <deque>
 #include <thread>
 #include <cmath>
+#include <cstdlib>
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -159,13 +160,15 @@ struct mh_handle {
     int64_t device_bytes = 0;
     // cohort store
     u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr, *dCN = nullptr;
-    u16 *dOrig = nullptr;
+    u16 *dOrig = nullptr, *dCC = nullptr, *dSL = nullptr, *dSLo = nullptr;
+    u32 *dSO = nullptr;
     u32 *dInv = nullptr;
     // solve workspace (grown on demand)
     int ws_h = 0, ws_rounds = 0, ws_slots = 0;
     u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr;
     int *dState = nullptr, *dRes = nullptr;
-    Key *dSlots = nullptr, *dCand = nullptr;
+    Key *dSlots = nullptr, *dCand = nullptr, *dChamp = nullptr;
+    int *dChampOk = nullptr;
     u32 *dCounts = nullptr;               // frontier sizes, one per depth, then work-distribution counters
     Rec *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
@@ -182,8 +185,8 @@ struct mh_handle {
     {
         for (int i = 0; i < 2; ++i)
             if (evk[i]) cudaEventDestroy(evk[i]);
-        for (void *p : {(void *)dT, (void *)dN, (void *)dCT, (void *)dCN, (void *)dOrig, (void *)dInv, (void *)dU,
-                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand,
+        for (void *p : {(void *)dT, (void *)dN, (void *)dCT, (void *)dCN, (void *)dCC, (void *)dSL, (void *)dSLo, (void *)dSO, (void *)dOrig, (void *)dInv, (void *)dU,
+                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk,
                         (void *)dCounts, (void *)dSync})
             dfree(p, stream);
         for (int l = 0; l < kMaxH; ++l) dfree(dF[l], stream);
@@ -262,21 +265,58 @@ int build_store(mh_handle *H, const uint64_t *bm)
             for (u64 x = N[(size_t)i * c.WNp + w]; x; x &= x - 1)
                 CN[(size_t)(w * 64 + __builtin_ctzll(x)) * c.GW + (i >> 6)] |= bit;
     }
+    // running counts of each column's set bits, word by word (closed-form counts of
+    // the subtrees whose tumor intersection is one sample)
+    std::vector<u16> CC((size_t)Nt * (c.GW + 1), 0);
+    std::vector<u32> SO((size_t)Nt + 1, 0);
+    for (int sm = 0; sm < Nt; ++sm) {
+        int run = 0;
+        for (int w = 0; w <= c.GW; ++w) {
+            CC[(size_t)sm * (c.GW + 1) + w] = (u16)run;
+            if (w < c.GW) run += __builtin_popcountll(CT[(size_t)sm * c.GW + w]);
+        }
+        SO[sm + 1] = SO[sm] + (u32)run;
+    }
+    // each sample's genes in ascending search order
+    std::vector<u16> SL(std::max<size_t>(SO[Nt], 1));
+    for (int sm = 0; sm < Nt; ++sm) {
+        u32 k = SO[sm];
+        for (int w = 0; w < c.GW; ++w)
+            for (u64 x = CT[(size_t)sm * c.GW + w]; x; x &= x - 1) SL[k++] = (u16)(w * 64 + __builtin_ctzll(x));
+    }
+    // and as original row indices, ascending (the order of the leaf keys' tuples)
+    std::vector<u16> SLo(SL.size());
+    for (int sm = 0; sm < Nt; ++sm) {
+        for (u32 k = SO[sm]; k < SO[sm + 1]; ++k) SLo[k] = orig[SL[k]];
+        std::sort(SLo.begin() + SO[sm], SLo.begin() + SO[sm + 1]);
+    }
     int rc;
     cudaStream_t st = H->stream;
     if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes, H->dev, st))) return rc;
     if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes, H->dev, st))) return rc;
     if ((rc = dalloc(&H->dCT, CT.size(), &H->device_bytes, H->dev, st))) return rc;
     if ((rc = dalloc(&H->dCN, CN.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dCC, CC.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dSL, SL.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dSLo, SLo.size(), &H->device_bytes, H->dev, st))) return rc;
+    if ((rc = dalloc(&H->dSO, SO.size(), &H->device_bytes, H->dev, st))) return rc;
     if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
     if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
     MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
     MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
     if (!CT.empty()) MH_CUDA(cudaMemcpyAsync(H->dCT, CT.data(), CT.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
     if (!CN.empty()) MH_CUDA(cudaMemcpyAsync(H->dCN, CN.data(), CN.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
+    if (!CC.empty()) MH_CUDA(cudaMemcpyAsync(H->dCC, CC.data(), CC.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dSL, SL.data(), SL.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dSLo, SLo.data(), SLo.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dSO, SO.data(), SO.size() * sizeof(u32), cudaMemcpyHostToDevice, st));
     MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, st));
     MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, st));
     c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.CN = H->dCN; c.orig = H->dOrig; c.inv = H->dInv;
+    c.CC = Nt ? H->dCC : nullptr;
+    c.SL = H->dSL;
+    c.SO = H->dSO;
+    c.SLo = H->dSLo;
     MH_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
     return MH_OK;
 }
@@ -310,7 +350,11 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
 int ensure_frontier(mh_handle *H, int l, u64 n, bool exact = false)
 {
     if (n <= H->cap[l]) return MH_OK;
-    u64 want = std::max<u64>(exact ? n : n + n / 4, 1u << 11);
+    // smallest region: 2048 records per shard, or MH_FRONTIER_MIN_RECORDS
+    u64 least = 1u << 11;
+    const char *mn = getenv("MH_FRONTIER_MIN_RECORDS");
+    if (mn && *mn && atoll(mn) > 0) least = (u64)atoll(mn);
+    u64 want = std::max<u64>(exact ? n : n + n / 4, least);
     if (want > 0xffffffffull / kShards) want = 0xffffffffull / kShards;
     const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)sizeof(Rec);
     const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
@@ -363,6 +407,8 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 2, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dCounts, (size_t)kCountSets * kCountWords, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dChamp, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dChampOk, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
         if (!(H->hState = pinned_state_get())) return fail(MH_ENOMEM, "pinned host allocation failed");
@@ -459,6 +505,8 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     s->slots = H->dSlots;
     s->nslots = H->ws_slots;
     s->cand = H->dCand;
+    s->champ = H->dChamp;
+    s->champ_ok = H->dChampOk;
     s->work = H->dWork;
     s->best_hint = H->dWork + kWorkCount;
     *max_rounds = H->Nt + 1;
@@ -738,6 +786,8 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     // the host reads the state; an overflowed frontier is grown and its round rerun.
     int batch = 4;
     Frontiers fl;
+    s.champ = nullptr;  // the per-sample champions are computed by the persistent kernels only
+    s.champ_ok = nullptr;
     while (!done) {
         for (int l = 0; l < kMaxH; ++l) {
             fl.F[l] = H->dF[l];

@@ -42,6 +42,16 @@ struct Cohort {
     const u64 *CN;  // Nn x GW   normal bits, sample-major
     const u16 *orig;  // G: search position -> original row index
     const u32 *inv;   // G: original row index -> search position
+    // Nt x (GW + 1) running counts of CT: CC[s][w] = set bits of column s in words
+    // below w (CC[s][GW]: genes mutated in sample s).  nullptr: single-sample
+    // subtrees are searched like any other (no closed-form counts).
+    const u16 *CC;
+    // Genes of each tumor sample, ascending search positions: sample s's list is
+    // SL[SO[s] .. SO[s + 1]) (the set bits of column s of CT, listed).
+    const u16 *SL;
+    const u32 *SO;
+    // The same genes as original row indices, ascending: SLo[SO[s] .. SO[s + 1]).
+    const u16 *SLo;
 };
 
 // Best candidate of a search, compared as (score desc, original tuple asc).
@@ -87,6 +97,12 @@ struct Solve {
     Key *cand;          // kCandidates best keys of the previous round (for the next threshold)
     u64 *best_hint;     // best score (s field) known to exist in the round, for skipping hopeless
                         // scoring (persistent solve: two words, by round parity)
+    // Per tumor sample s (Nt entries), computed once per solve by the persistent
+    // kernels: champ[s] = the best key, valued with TP = 1, over the h-subsets of
+    // the genes of s; champ_ok[s] = 1 once known (champ[s].s = 0: fewer than h
+    // genes), 0 if its search exceeded its budget.  nullptr: not computed.
+    Key *champ;
+    int *champ_ok;
 };
 
 constexpr int kCandidates = 32;

@@ -257,7 +257,10 @@ __device__ __forceinline__ int my_shard(const Team &t)
 
 // Block-wide accumulation of counters: warps add into shared memory, then one
 // global atomic per counter and block (not per warp) at the end of a phase.
-constexpr int kAccN = 10;  // 8, 9: depth-1 visited / pruned of a persistent round
+// 8, 9: depth-1 visited / pruned of a persistent round; from kAccDeep: visited and
+// surviving nodes of every depth counted in closed form (single-sample subtrees)
+constexpr int kAccDeep = 10;
+constexpr int kAccN = kAccDeep + 2 * (kMaxH + 1);
 __device__ __forceinline__ void acc_begin(u64 *acc)
 {
     if (threadIdx.x < kAccN) acc[threadIdx.x] = 0;
@@ -266,6 +269,20 @@ __device__ __forceinline__ void acc_begin(u64 *acc)
 __device__ __forceinline__ void acc_add(u64 *acc, int i, u64 v)
 {
     if (v) atomicAdd(&acc[i], v);
+}
+
+// Closed-form counters of the block (depths 1 .. h) into the round's counters.
+// Every thread of the block calls it after the block's last update of acc.
+__device__ __forceinline__ void acc_flush_deep(const Solve &s, int round, const u64 *acc)
+{
+    const int e = (int)threadIdx.x - 32;
+    if (e >= 1 && e <= s.h) {
+        const u64 v = acc[kAccDeep + 2 * e], a = acc[kAccDeep + 2 * e + 1];
+        if (v) {
+            atomicAdd(s.cnt + ((size_t)round * s.h + (e - 1)) * 2, v);
+            if (v - a) atomicAdd(s.cnt + ((size_t)round * s.h + (e - 1)) * 2 + 1, v - a);
+        }
+    }
 }
 
 __device__ __forceinline__ void copy_rec(Rec *dst, const Rec *src)
@@ -284,6 +301,96 @@ __device__ __forceinline__ void load_rec(Rec *dst, const Rec *src)
     uint4 *b = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
     for (int i = 0; i < (int)(sizeof(Rec) / 16); ++i) b[i] = __ldcg(a + i);
+}
+
+// ---------------------------------------------------------------------------
+// Single-sample subtrees.  Below a node whose tumor intersection is one sample
+// smp, every node's intersection is {smp} or empty, so the tree there is fixed by
+// the genes of smp after the node's last gene g: with b_1 < b_2 < ... those genes,
+// a depth-(d+k) descendant survives iff its last k genes are k of the b's, each
+// within its depth's bound hi(e) = G - h + e - 1 (0-based, inclusive).  Its
+// counters -- visited and pruned per depth, exactly those of Algorithm 2's loops
+// over this subtree -- follow from one pass over the bits of column smp, and none
+// of its leaves scores above a_num + a_den * Nn (TP = 1).  So when a candidate of
+// the round is known to score more than that, the subtree is counted in closed
+// form instead of being searched.
+
+// Which single-sample subtrees a phase may count in closed form:
+//   2: all of them -- a candidate of the round is known to score above
+//      a_num * 1 + a_den * Nn (thr, as S + 1), which no TP = 1 leaf reaches;
+//   1: those of the samples whose champion is known (Solve::champ): the
+//      champions stand for every TP = 1 leaf (see phase_champions);
+//   0: none.  Paper pruning only (with pruning off the empty nodes have children too).
+__device__ __forceinline__ int single_sample_mode(const Cohort &c, const Solve &s, u64 thr)
+{
+    if (s.prune != 0 || c.CC == nullptr) return 0;
+    if (s.a_num + s.a_den * (u64)c.Nn + 1ull < thr) return 2;
+    return s.champ ? 1 : 0;
+}
+
+__device__ __forceinline__ bool single_sample_closed(int mode, const int *champ_ok, int smp)
+{
+    return mode == 2 || (mode == 1 && __ldcg(champ_ok + smp) != 0);
+}
+
+// Position in sample smp's gene list of its first gene after g.
+__device__ __forceinline__ int single_sample_rank(const Cohort &c, int g, int smp)
+{
+    const int w = g >> 6, bt = g & 63;
+    const u64 upto = bt == 63 ? ~0ull : ((2ull << bt) - 1ull);
+    return (int)__ldg(c.CC + (size_t)smp * (c.GW + 1) + w) + __popcll(__ldg(c.CT + (size_t)smp * c.GW + w) & upto);
+}
+
+// Counters of the subtree below a depth-d node (d <= h - 2) with y = {smp} and last
+// gene g, added to the block's per-depth sums deep[2e] (visited) and deep[2e + 1]
+// (surviving) for e = d+1 .. h.  f_k(b) = number of surviving depth-(d+k) nodes
+// whose last gene is b: f_1(b) = [b <= hi(d+1)], f_k(b) = [b <= hi(d+k)] * (sum of
+// f_{k-1} over the earlier genes); each such node has hi(d+k+1) - b children.
+// genes: the n genes of smp after g, ascending; G: the cohort's gene count.
+__device__ __noinline__ void single_sample_subtree(const u16 *genes, int n, int G, int h, int d, int g, u64 *deep)
+{
+    const int K = h - d;            // levels below the node, 2 .. kMaxH - 1
+    const int hi0 = G - h + d - 1;  // hi(d + k) = hi0 + k
+    u64 S[kMaxH], av[kMaxH], vi[kMaxH];
+#pragma unroll
+    for (int k = 0; k < kMaxH; ++k) S[k] = av[k] = vi[k] = 0;
+    vi[1] = (u64)(hi0 + 1 - g);
+    for (int i = 0; i < n; ++i) {
+        const int b = (int)__ldg(genes + i);
+        // descending k: f_k reads the sum of f_{k-1} before this gene's update
+#pragma unroll
+        for (int k = kMaxH - 1; k >= 1; --k) {
+            if (k > K || b > hi0 + k) continue;
+            const u64 f = k == 1 ? 1ull : S[k - 1];
+            av[k] += f;
+            if (k < K) {
+                vi[k + 1] += f * (u64)(hi0 + k + 1 - b);
+                S[k] += f;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 1; k < kMaxH; ++k) {
+        if (k > K) break;
+        if (vi[k]) atomicAdd(&deep[2 * (d + k)], vi[k]);
+        if (av[k]) atomicAdd(&deep[2 * (d + k) + 1], av[k]);
+    }
+}
+
+// Closed-form counters of the subtree below a depth-d node (d < h) with y = {smp}
+// and last gene g: the leaves of a leaf parent into vis_h / alive_h, a deeper
+// subtree into deep.
+__device__ __forceinline__ void single_sample_count(const Cohort &c, int h, int d, int g, int smp, u64 &vis_h,
+                                                    u64 &alive_h, u64 *deep)
+{
+    const int r = single_sample_rank(c, g, smp);
+    const int m = (int)__ldg(c.CC + (size_t)smp * (c.GW + 1) + c.GW);
+    if (d == h - 1) {
+        vis_h += (u64)(c.G - 1 - g);
+        alive_h += (u64)(m - r);
+    } else {
+        single_sample_subtree(c.SL + __ldg(c.SO + smp) + r, m - r, c.G, h, d, g, deep);
+    }
 }
 
 // Per-warp scratch: one batch of frontier records and their child ranges.
@@ -375,13 +482,17 @@ struct Depth1 {
 // its child range [last gene + 1, hi_bound]; counts its children as visited.
 // With io.Ush the records are the depth-1 nodes of genes 0 .. count-1, built from
 // the rows (empty ones are counted as pruned and have no children, unless
-// all_children).  Returns the number of column words of the batch's sparse records
-// (those with samples, or all of them with `all_children`) and the bit mask of
-// dense records.
+// all_children).  With `single` (single_sample_mode), a listed record whose tumor
+// intersection is one sample is counted in closed form and left with no children
+// to search: a leaf parent (L = h - 1) adds its surviving leaves to alive_cf, a
+// shallower record adds its whole subtree to deep.  Returns the number of column
+// words of the batch's sparse records (those with samples, or all of them with
+// `all_children`) and the bit mask of dense records.
 __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io, Depth1 &d1, const Rec *Fin,
                                              u32 cap_s, u64 first, u64 stride, int R, u32 count, int L, int hi_bound,
                                              bool all_children, Batch &b, int lane, unsigned &dense_mask,
-                                             u64 &visited, const u16 *orig = nullptr)
+                                             u64 &visited, int h, int single, const int *champ_ok, u64 &alive_cf,
+                                             u64 *deep, const u16 *orig = nullptr)
 {
     const u64 i = first + (u64)lane * stride;
     bool valid = lane < R && i < count;
@@ -399,8 +510,14 @@ __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io,
         hi = hi_bound;
         ky = b.r[lane].ky;
         kn = b.r[lane].kn;
-        if (hi >= lo) visited += (u64)(hi - lo + 1);
-        if (orig) {  // ascending original indices of the prefix genes (leaf keys)
+        if (single && ky == 1 && !is_dense(ky, kn) && hi >= lo &&
+            single_sample_closed(single, champ_ok, b.r[lane].ids[0])) {
+            single_sample_count(c, h, L, lo - 1, b.r[lane].ids[0], visited, alive_cf, deep);
+            hi = lo - 1;  // nothing left to search below this record
+        } else if (hi >= lo) {
+            visited += (u64)(hi - lo + 1);
+        }
+        if (orig && hi >= lo) {  // ascending original indices of the prefix genes (leaf keys)
             for (int q = 0; q < L; ++q) {
                 const u16 v = orig[prefix_gene(b.r[lane].p, q)];
                 int k = q - 1;
@@ -741,11 +858,20 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     const bool all_children = s.prune != 0;
     const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
+    u64 leaf_vis = 0, leaf_alive = 0;  // closed-form leaves of single-sample children (level = h - 1)
+    u64 *deep = acc + kAccDeep;
+    const int h = s.h;
     Dispenser disp((u32)nw, (u32)gw, count, dispenser_counters(counts, level - 2));
     for (u64 first = disp.next(lane); first < count; first = disp.next(lane)) {
         unsigned dense;
+        // the best score known to exist in the round decides whether single-sample
+        // subtrees may be counted in closed form
+        u64 thr = 0;
+        if (lane == 0) thr = *(volatile u64 *)io.hint;
+        const int single = single_sample_mode(c, s, __shfl_sync(kFull, thr, 0));
+        u64 alive_cf = 0;
         const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, hi_bound, all_children, b,
-                                        lane, dense, visited);
+                                        lane, dense, visited, h, single, s.champ_ok, alive_cf, deep);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
@@ -769,26 +895,32 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
                 b.ns[lane] = ((u64)(u32)jj[u] << 32) | (u32)wi[u];
                 b.cx[lane] = incl - n;
                 if (lane == 31) b.cx[32] = incl;
-                u32 base = 0;
-                if (lane == 0) base = atomicAdd(my_count, (u32)tot);
-                base = __shfl_sync(kFull, base, 0);
                 __syncwarp();
-                for (int k = lane; k < tot; k += 32) {
-                    int lo = 0, hi = 31;  // source lane: last with cx <= k
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (b.cx[mid] <= k) lo = mid; else hi = mid - 1;
-                    }
-                    u64 x = b.ys[lo];
-                    for (int r = k - b.cx[lo]; r > 0; --r) x &= x - 1;
-                    const u32 pos = base + (u32)k;
-                    if (pos < cap) {
+                for (int k0 = 0; k0 < tot; k0 += 32) {
+                    const int k = k0 + lane;
+                    Rec child;
+                    bool emit = false;
+                    if (k < tot) {
+                        int lo = 0, hi = 31;  // source lane: last with cx <= k
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (b.cx[mid] <= k) lo = mid; else hi = mid - 1;
+                        }
+                        u64 x = b.ys[lo];
+                        for (int r = k - b.cx[lo]; r > 0; --r) x &= x - 1;
                         const u64 jw = b.ns[lo];
-                        Rec child;
+                        const int g = (int)(u32)jw * 64 + __ffsll((long long)x) - 1;
                         child.pad[0] = child.pad[1] = child.pad[2] = 0;
-                        child_from_lists(c, b.r[(int)(jw >> 32)], L, (int)(u32)jw, __ffsll((long long)x) - 1, child);
-                        copy_rec(&Fout[pos], &child);
+                        child_from_lists(c, b.r[(int)(jw >> 32)], L, (int)(u32)jw, g & 63, child);
+                        emit = true;
+                        // a child of a listed parent is listed: one sample -> closed form
+                        if (single && child.ky == 1 && single_sample_closed(single, s.champ_ok, child.ids[0])) {
+                            single_sample_count(c, h, level, g, child.ids[0], leaf_vis, leaf_alive, deep);
+                            emit = false;
+                        }
                     }
+                    const u32 pos = warp_reserve(emit ? 1 : 0, my_count, lane);
+                    if (emit && pos < cap) copy_rec(&Fout[pos], &child);
                 }
                 __syncwarp();
             }
@@ -804,16 +936,23 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
             dense_setup(c, s, p, L, b, by, bn, lane);
             for (int gb = lo; gb <= hi; gb += 32) {
                 const int g = gb + lane;
-                int kyc = 0;
+                int kyc = 0, smp = 0;
                 if (g <= hi) {
                     const u64 *trow = c.T + (size_t)g * c.WTp;
                     for (unsigned bits = by; bits; bits &= bits - 1) {
                         const int w = __ffs(bits) - 1;
-                        kyc += __popcll(b.ys[w] & trow[w]);
+                        const u64 yw = b.ys[w] & trow[w];
+                        if (yw) smp = w * 64 + __ffsll((long long)yw) - 1;
+                        kyc += __popcll(yw);
                     }
                 }
                 alive += (u64)(kyc > 0);
-                const bool emit = g <= hi && (all_children || kyc > 0);
+                bool closed = false;
+                if (single && kyc == 1 && g <= hi && single_sample_closed(single, s.champ_ok, smp)) {
+                    single_sample_count(c, h, level, g, smp, leaf_vis, leaf_alive, deep);
+                    closed = true;
+                }
+                const bool emit = g <= hi && (all_children || kyc > 0) && !closed;
                 const u32 pos = warp_reserve(emit ? 1 : 0, my_count, lane);
                 if (emit && pos < cap) {
                     Rec child;
@@ -827,6 +966,8 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
+    leaf_vis = warp_sum_u64(leaf_vis);
+    leaf_alive = warp_sum_u64(leaf_alive);
     d1.visited = warp_sum_u64(d1.visited);
     d1.pruned = warp_sum_u64(d1.pruned);
     if (lane == 0) {
@@ -834,6 +975,8 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
         acc_add(acc, 1, visited - alive);
         acc_add(acc, 8, d1.visited);
         acc_add(acc, 9, d1.pruned);
+        acc_add(deep, 2 * h, leaf_vis);
+        acc_add(deep, 2 * h + 1, leaf_alive);
     }
     warp_cycles(acc, t0, lane);
     __syncthreads();
@@ -841,6 +984,7 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
         atomicAdd(s.cnt + ((size_t)round * s.h + (level - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
     if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
         atomicAdd(s.cnt + ((size_t)round * s.h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
+    acc_flush_deep(s, round, acc);
     warp_cycles_flush(s, acc, 0, io.par);
     return true;
 }
@@ -860,6 +1004,19 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     Key best = key_empty();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = s.h, L = h - 1;
+    // the champions of the uncovered tumors (a share of them per block) are
+    // candidates of the round and stand for its TP = 1 leaves
+    if (s.champ && io_in.Ush) {
+        for (int smp = t.rank * (int)blockDim.x + (int)threadIdx.x; smp < c.Nt; smp += t.size * (int)blockDim.x) {
+            if (!((io_in.Ush[smp >> 6] >> (smp & 63)) & 1ull) || !__ldcg(s.champ_ok + smp)) continue;
+            Key k;
+            k.s = __ldcg(&s.champ[smp].s);
+            k.t0 = __ldcg(&s.champ[smp].t0);
+            k.t1 = __ldcg(&s.champ[smp].t1);
+            k.t2 = __ldcg(&s.champ[smp].t2);
+            if (k.s && key_better(k, best)) best = k;
+        }
+    }
     RoundIO io = io_in;
     if (h != 2) io.Ush = nullptr;  // depth-1 nodes are built only as the parents of the leaves of h = 2
     if (threadIdx.x == 0) overflow = 0;
@@ -878,14 +1035,18 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     Dispenser disp((u32)nw, (u32)gw, count, dispenser_counters(counts, h - 2));
     for (u64 first = disp.next(lane); first < count; first = disp.next(lane)) {
         unsigned dense;
-        // (with pruning off, the empty depth-1 nodes built here still have leaves)
-        const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, c.G - 1,
-                                        io.Ush != nullptr && s.prune != 0, b, lane, dense, visited, c.orig);
-        prefixes += (u64)(lane < (int)disp.R && first + (u64)lane * nw < count);
         // only candidates at least as good as the best score known to exist can win
         u64 thr = 0;
         if (lane == 0) thr = *(volatile u64 *)io.hint;
         thr = warp_max_u64(thr > best.s ? thr : best.s);
+        u64 alive_cf = 0;
+        // (with pruning off, the empty depth-1 nodes built here still have leaves)
+        const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, c.G - 1,
+                                        io.Ush != nullptr && s.prune != 0, b, lane, dense, visited, h,
+                                        single_sample_mode(c, s, thr), s.champ_ok, alive_cf, acc + kAccDeep,
+                                        c.orig);
+        alive += alive_cf;
+        prefixes += (u64)(lane < (int)disp.R && first + (u64)lane * nw < count);
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
@@ -975,6 +1136,7 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     if (threadIdx.x == 4 && acc[4]) atomicAdd(s.work + kWorkScored, acc[4]);
     if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
         atomicAdd(s.cnt + ((size_t)round * h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
+    acc_flush_deep(s, round, acc);
     warp_cycles_flush(s, acc, 1, io.par);
     block_commit_best(best, io.slots, t.rank, io.overwrite);
     return true;
@@ -1214,6 +1376,140 @@ __device__ void block_rescore(const Cohort &c, const Solve &s, const Key *keys, 
     if (lane == 0 && best) atomicMax(hint, best);
 }
 
+// Per-sample champions, computed once per solve before its first round.  For a
+// tumor sample s every h-subset of its genes is a leaf whose tumor intersection
+// holds s; valued with TP = 1 it scores a_num + a_den * (Nn - FP).  champ[s] is the
+// largest key among them (least FP, then the smallest tuple of original indices).
+// In any round with s uncovered, the h-subsets of s's genes that no other
+// uncovered tumor carries are exactly the leaves of s's single-sample subtrees
+// and score their TP = 1 value; the others are leaves of the multi-sample part of
+// the tree (TP >= 2) and score at least that value there.  Hence the round's best
+// key is the larger of the best multi-sample leaf and the best champion of an
+// uncovered tumor, and single-sample subtrees need no scoring: this is the same
+// argmax, evaluated without visiting the TP = 1 leaves one by one.
+//
+// Search: one warp per sample over the subsets in lexicographic order of original
+// indices (each sample's genes listed ascending by original index), the last gene
+// spread over the lanes; the first subset with FP = 0 is the champion.  A sample
+// whose search passes kChampBudget subsets is left unknown (champ_ok = 0): its
+// single-sample subtrees are then searched and scored like the rest.
+constexpr int kChampBudget = 1 << 15;
+
+__device__ void phase_champions(const Cohort &c, const Solve &s, const Team &t, Batch &b)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int h = s.h;
+    for (int smp = t.rank * nwarps + warp; smp < c.Nt; smp += t.size * nwarps) {
+        const u32 off = __ldg(c.SO + smp);
+        const int m = (int)(__ldg(c.SO + smp + 1) - off);
+        const u16 *go = c.SLo + off;
+        Key best = key_empty();
+        int ok = 1;
+        if (m >= h) {
+            int idx[kMaxH];  // positions of the prefix genes 0 .. h-2 (the same in every lane)
+            for (int q = 0; q < h - 1; ++q) idx[q] = q;
+            int best_fp = 0x7fffffff, best_j = 0, evaluated = 0;
+            int best_idx[kMaxH];
+            for (int q = 0; q < kMaxH; ++q) best_idx[q] = 0;
+            for (;;) {
+                // normal intersection of the prefix, word `lane`
+                u64 pn = 0;
+                if (lane < c.Wn) {
+                    pn = ~0ull;
+                    for (int q = 0; q < h - 1; ++q) pn &= c.N[(size_t)c.inv[go[idx[q]]] * c.WNp + lane];
+                }
+                b.ns[lane] = pn;
+                __syncwarp();
+                bool zero = false;
+                for (int j0 = idx[h - 2] + 1; j0 < m; j0 += 32) {
+                    const int j = j0 + lane;
+                    unsigned v = 0xffffffffu;  // (FP, lane): least FP, then the first in order
+                    if (j < m) {
+                        const u64 *nrow = c.N + (size_t)c.inv[go[j]] * c.WNp;
+                        int fp = 0;
+                        for (int w = 0; w < c.Wn; ++w) fp += __popcll(b.ns[w] & nrow[w]);
+                        v = ((unsigned)fp << 5) | (unsigned)lane;
+                    }
+                    const unsigned mv = __reduce_min_sync(kFull, v);
+                    evaluated += m - j0 < 32 ? m - j0 : 32;
+                    if ((int)(mv >> 5) < best_fp) {
+                        best_fp = (int)(mv >> 5);
+                        best_j = j0 + (int)(mv & 31u);
+                        for (int q = 0; q < h - 1; ++q) best_idx[q] = idx[q];
+                    }
+                    if (best_fp == 0) {
+                        zero = true;
+                        break;
+                    }
+                }
+                __syncwarp();
+                if (zero) break;
+                if (evaluated > kChampBudget) {
+                    ok = 0;
+                    break;
+                }
+                // next prefix in lexicographic order (position q is at most m - h + q)
+                int q = h - 2;
+                while (q >= 0 && idx[q] == m - h + q) --q;
+                if (q < 0) break;
+                ++idx[q];
+                for (int r = q + 1; r < h - 1; ++r) idx[r] = idx[r - 1] + 1;
+            }
+            if (ok) {
+                best.s = s.a_num + s.a_den * (u64)(c.Nn - best_fp) + 1;
+                for (int q = 0; q < h - 1; ++q) key_put(best, q, go[best_idx[q]]);
+                key_put(best, h - 1, go[best_j]);
+            }
+        }
+        if (lane == 0) {
+            s.champ[smp] = best;
+            s.champ_ok[smp] = ok;
+        }
+        __syncwarp();
+    }
+}
+
+// First round of a solve: no candidate of an earlier round bounds the round's best
+// score yet.  Every uncovered tumor is covered by the combination of its h last
+// genes in search order (its most frequently mutated ones); the best of their
+// scores is a lower bound on the round's best, merged into *hint, so that the
+// first round can already skip what cannot win.
+__device__ void block_seed(const Cohort &c, const Solve &s, const Team &t, const u64 *Ush, u64 *hint)
+{
+    const int h = s.h;
+    u64 best = 0;
+    for (int smp = t.rank * (int)blockDim.x + (int)threadIdx.x; smp < c.Nt; smp += t.size * (int)blockDim.x) {
+        if (!((Ush[smp >> 6] >> (smp & 63)) & 1ull)) continue;
+        const u64 *col = c.CT + (size_t)smp * c.GW;
+        int gs[kMaxH];
+        int n = 0;
+        for (int w = (c.G - 1) >> 6; w >= 0 && n < h; --w) {
+            u64 x = __ldg(col + w);
+            while (x && n < h) {
+                const int bt = 63 - __clzll((long long)x);
+                gs[n++] = w * 64 + bt;
+                x &= ~(1ull << bt);
+            }
+        }
+        if (n < h) continue;
+        int tp = 0, fp = 0;
+        for (int w = 0; w < c.Wt; ++w) {
+            u64 y = Ush[w];
+            for (int q = 0; q < h; ++q) y &= c.T[(size_t)gs[q] * c.WTp + w];
+            tp += __popcll(y);
+        }
+        for (int w = 0; w < c.Wn; ++w) {
+            u64 y = ~0ull;
+            for (int q = 0; q < h; ++q) y &= c.N[(size_t)gs[q] * c.WNp + w];
+            fp += __popcll(y);
+        }
+        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+        best = s1 > best ? s1 : best;
+    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(hint, best);
+}
+
 // End of round r of the persistent solve, run by EVERY block of the team on the
 // same inputs, so that all of them reach the same decisions without another
 // barrier: the winner (largest key of the round's slots), its TP / FP, the next U
@@ -1352,6 +1648,13 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     }
     __syncthreads();
     if (h > 1) block_rescore(c, s, cand_sh, Ush, s.best_hint + (round & 1));
+    if (h > 1 && round == 0 && s.prune == 0 && c.CC) {
+        // the champions and the first round's threshold, complete before any block
+        // starts searching
+        if (s.champ) phase_champions(c, s, t, b);
+        block_seed(c, s, t, Ush, s.best_hint);
+        if (!grid_sync(gsync, s.state, t.size)) return;
+    }
     for (;;) {
         const int par = round & 1;
         u32 *counts = counts_base + (size_t)par * kCountWords;

@@ -226,6 +226,10 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     u16 *orig = (u16 *)(base + kOffOrig);
     u32 *inv = (u32 *)(base + kOffInv);
     c.T = T; c.N = N; c.CT = CT; c.CN = CN; c.orig = orig; c.inv = inv;
+    c.CC = nullptr;  // no running-count table here: every subtree is searched
+    c.SL = nullptr;
+    c.SO = nullptr;
+    c.SLo = nullptr;
 
     Solve s;
     s.h = h;
@@ -240,6 +244,8 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.work = (u64 *)(base + kOffWork);
     s.best_hint = s.work + kWorkCount;
     s.cand = (Key *)(base + kOffCand);
+    s.champ = nullptr;  // one kernel per phase: no per-sample champions
+    s.champ_ok = nullptr;
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);

@@ -184,9 +184,11 @@ def test_invalid_inputs_rejected(mh):
 
 
 def test_frontier_growth_on_overflow(mh, monkeypatch):
-    """Frontiers sized only by growth: the first rounds overflow the initial regions,
-    the host grows them and reruns the round; results and counters are unchanged."""
+    """Frontiers sized only by growth from small initial regions (16 records per
+    shard): the first rounds overflow them, the host grows them and reruns the
+    round; results and counters are unchanged."""
     monkeypatch.setenv("MH_FRONTIER_PRESIZE", "0")
+    monkeypatch.setenv("MH_FRONTIER_MIN_RECORDS", "16")
     c = synth.generate(synth.c2_law(1500, 300, 200, seed=4, h=4))
     ref = oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, 4)
     for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
