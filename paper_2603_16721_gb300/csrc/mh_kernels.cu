@@ -615,21 +615,27 @@ __device__ __forceinline__ u32 warp_reserve(int n, u32 *shard_count, int lane)
 }
 
 // Child record of a sparse parent: its samples are the parent's samples whose
-// column word wi has bit bt set.
-__device__ __forceinline__ void child_from_lists(const Cohort &c, const Rec &parent, int L, int wi, int bt,
-                                                 Rec &out)
+// column word wi has bit bt set.  child_tumors fills the prefix and the tumor
+// samples, child_normals the normal samples (not needed when the child is
+// counted in closed form).
+__device__ __forceinline__ void child_tumors(const Cohort &c, const Rec &parent, int L, int wi, int bt, Rec &out)
 {
     out.p = prefix_with(parent.p, L, wi * 64 + bt);
-    int ky = 0, kn = 0;
+    int ky = 0;
     for (int q = 0; q < parent.ky; ++q) {
         const int sm = parent.ids[q];
         if ((c.CT[(size_t)sm * c.GW + wi] >> bt) & 1ull) out.ids[ky++] = (u16)sm;
     }
+    out.ky = (u16)ky;
+}
+
+__device__ __forceinline__ void child_normals(const Cohort &c, const Rec &parent, int wi, int bt, Rec &out)
+{
+    int kn = 0;
     for (int q = 0; q < parent.kn; ++q) {
         const int sm = parent.ids[kListT + q];
         if ((c.CN[(size_t)sm * c.GW + wi] >> bt) & 1ull) out.ids[kListT + kn++] = (u16)sm;
     }
-    out.ky = (u16)ky;
     out.kn = (u16)kn;
 }
 
@@ -910,13 +916,16 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
                         for (int r = k - b.cx[lo]; r > 0; --r) x &= x - 1;
                         const u64 jw = b.ns[lo];
                         const int g = (int)(u32)jw * 64 + __ffsll((long long)x) - 1;
+                        const Rec &parent = b.r[(int)(jw >> 32)];
                         child.pad[0] = child.pad[1] = child.pad[2] = 0;
-                        child_from_lists(c, b.r[(int)(jw >> 32)], L, (int)(u32)jw, g & 63, child);
+                        child_tumors(c, parent, L, (int)(u32)jw, g & 63, child);
                         emit = true;
                         // a child of a listed parent is listed: one sample -> closed form
                         if (single && child.ky == 1 && single_sample_closed(single, s.champ_ok, child.ids[0])) {
                             single_sample_count(c, h, level, g, child.ids[0], leaf_vis, leaf_alive, deep);
                             emit = false;
+                        } else {
+                            child_normals(c, parent, (int)(u32)jw, g & 63, child);
                         }
                     }
                     const u32 pos = warp_reserve(emit ? 1 : 0, my_count, lane);
