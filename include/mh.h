@@ -203,19 +203,18 @@ MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, 
  * (continuous batching) and every cohort stays resident on the device between its
  * rounds.  Small requests run batched (a team of whole SMs each, the batched
  * kernel); while any is active, "large" requests (see large_slots) pause at
- * their round boundary, and a large request runs on the whole GPU on the
- * single-cohort kernel when no small one is active.  Results are those of
+ * their round boundary, and the large requests run when no small one is active
+ * (a lone one on the single-cohort kernel, several batched).  Results are those of
  * mh_solve (MH_MODE_PERSISTENT); a served result's solve_ms is the request's
  * latency from submission to completion. */
 typedef struct mh_server mh_server;
 typedef struct {
     int64_t hbm_budget_bytes; /* device memory for active requests; <= 0: 80% of the free memory */
     int32_t slots;            /* requests solved concurrently; <= 0: 8 */
-    int32_t large_slots;      /* "large" requests (more than 4e6 (h-1)-gene sets sharing a tumor, the
-                                 size at which one request keeps the whole GPU busy) admitted
-                                 at a time; <= 0: 1.  Large requests start in arrival order;
-                                 smaller ones queued behind a waiting large one may start first
-                                 (backfill) */
+    int32_t large_slots;      /* "large" requests (more than 4e6 (h-1)-gene sets sharing a tumor)
+                                 admitted at a time, run batched together; <= 0: 2.  Large
+                                 requests start in arrival order; smaller ones queued behind a
+                                 waiting large one may start first (backfill) */
 } mh_server_opts;
 
 /* Starts a server on the current device.  opts may be NULL (defaults).

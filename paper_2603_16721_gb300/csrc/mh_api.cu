@@ -452,12 +452,29 @@ double work_estimate(const mh_handle *H, int d);
 // served runtime limits how many of them share the GPU.
 constexpr double kLargeWork = 4.0e6;
 
-// Sizes the frontiers of depths 2..h-1 once per handle from a bound on their first
-// round: a non-empty depth-l prefix shares a tumor s, so it is one of the C(m_s, l)
-// l-sets of the genes mutated in s (m_s of them); at most sum_s C(m_s, l) records.
-// The shards fill unevenly, hence 15% more per shard.  A bound above half the
-// frontier budget is skipped (the frontier then grows when it overflows), and so is
-// everything with MH_FRONTIER_PRESIZE=0 (frontiers grown on overflow only).
+// Build of the single-cohort persistent kernel for a solve: one block of 16 warps
+// per SM (the cheaper grid barrier; with single-sample subtrees counted in closed
+// form it is the faster build for every cohort measured, c1-c3 and the served
+// cohorts), or four blocks of 8 warps per SM with MH_PERSISTENT_BUILD=large.
+bool use_large_build(const mh_handle *, int)
+{
+    const char *v = getenv("MH_PERSISTENT_BUILD");
+    return v && !strcmp(v, "large");
+}
+
+// Expected depth-l frontier records from sets = sum_s C(m_s, l), the l-gene sets
+// that share a tumor (m_s: genes mutated in tumor s).  Nodes with one uncovered
+// tumor are counted in closed form and never stored, so a frontier holds the
+// l-sets that two or more tumors share: in the first round of the synthetic
+// cohorts (c2, c3) 7-9% of `sets` at l = 2 and under 1% at l = 3.  The estimate
+// takes 1/8 and 1/64; a frontier that outgrows it grows and its round reruns.
+double frontier_records_estimate(double sets, int l) { return sets / (l == 2 ? 8.0 : 64.0); }
+
+// Sizes the frontiers of depths 2..h-1 once per handle from the first-round
+// estimate above.  The shards fill unevenly, hence 15% more per shard.  An
+// estimate above half the frontier budget is skipped (the frontier then grows when
+// it overflows), and so is everything with MH_FRONTIER_PRESIZE=0 (frontiers grown
+// on overflow only).
 int presize_frontiers(mh_handle *H, int h)
 {
     const char *v = getenv("MH_FRONTIER_PRESIZE");
@@ -471,7 +488,7 @@ int presize_frontiers(mh_handle *H, int h)
             for (int i = 0; i < l; ++i) comb = comb * (double)(m - i) / (double)(i + 1);
             if (m >= l) e += comb;
         }
-        const double per_shard = e * 1.15 / kShards + 64.0;
+        const double per_shard = frontier_records_estimate(e, l) * 1.15 / kShards + 64.0;
         if (per_shard * kShards * sizeof(Rec) > 0.5 * (double)frontier_budget(H->dev)) continue;
         const int rc = ensure_frontier(H, l, (u64)per_shard, true);
         if (rc) return rc;
@@ -733,7 +750,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     ++launches;
     const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
     // large build for cohorts whose deepest frontier is expected to hold millions of prefixes
-    const bool large = work_estimate(H, h - 1) > kLargeWork;
+    const bool large = use_large_build(H, h);
     const int pgrid = persistent_grid(H->num_sms, large);
     int rounds_done = 0;
     bool done = H->Nt == 0;  // every tumor covered from the start
@@ -1068,7 +1085,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             // one cohort left: the single-cohort persistent kernel (its fields are kernel
             // parameters, which the compiler keeps out of registers)
             mh_handle *H = hs[act[0]];
-            const bool large = work_estimate(H, opts[act[0]].h - 1) > kLargeWork;
+            const bool large = use_large_build(H, opts[act[0]].h);
             MH_CUDA(launch_solve_persistent(H->c, ss[act[0]], frontiers_of(H), H->dSync, H->dCounts,
                                             persistent_grid(H->num_sms, large), large, st));
             MH_CUDA(cudaStreamSynchronize(st));
@@ -1239,7 +1256,8 @@ struct ServerReq {
 };
 
 // Device memory a request needs: its store, workspace and (for h >= 3) the
-// frontiers, estimated from the (h-1)-gene sets that share a tumor.
+// frontiers, estimated from the l-gene sets that share a tumor
+// (frontier_records_estimate).
 int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, double *work)
 {
     const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64;
@@ -1259,7 +1277,9 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, dou
             comb = comb * (double)(x - d) / (double)(d + 1);
         }
     }
-    for (int l = 2; l < h; ++l) bytes += (int64_t)(sets[l] * 1.25 * (double)sizeof(Rec));
+    for (int l = 2; l < h; ++l)
+        bytes += (int64_t)(frontier_records_estimate(sets[l], l) * 1.25 * (double)sizeof(Rec)) +
+                 (int64_t)(2048 * kShards) * (int64_t)sizeof(Rec);
     *work = (double)G + sets[h - 1];  // as work_estimate(H, h - 1)
     return bytes + (64 << 20);
 }
@@ -1408,10 +1428,10 @@ struct mh_server {
 
     // One launch over the active requests.  Small requests go first: while any is
     // active, the large ones pause at their round boundary (their state stays on the
-    // device) and the small ones run batched; a large request runs when no small one
-    // is active, alone on the single-cohort kernel (or batched with the other large
-    // ones when large_slots > 1).  A large solve keeps the whole GPU busy and runs
-    // fastest alone, while small solves are latency-bound and gain from sharing.
+    // device) and the small ones run batched; the large requests run when no small
+    // one is active, a lone one on the single-cohort kernel, several (large_slots >
+    // 1) batched together.  Rounds are latency-bound, so solves that share the GPU
+    // lose little speed each and gain throughput together.
     void run_active()
     {
         std::vector<ServerReq *> sel;
@@ -1452,7 +1472,8 @@ struct mh_server {
             ServerReq *r = sel[0];
             mh_handle *H = r->H;
             e = launch_solve_persistent(H->c, r->s, frontiers_of(H), H->dSync, H->dCounts,
-                                        persistent_grid(num_sms, r->large), r->large, st, d_yield);
+                                        persistent_grid(num_sms, use_large_build(H, r->opts.h)),
+                                        use_large_build(H, r->opts.h), st, d_yield);
         } else {
             cudaMemcpyAsync(d_items, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st);
             e = launch_solve_batch(d_items, n, d_yield, batch_map_at(d_items, items_cap, num_sms, kServerBuild), st);
@@ -1504,7 +1525,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
     if (!S) return fail(MH_ENOMEM, "host allocation of the server failed");
     if (opts) S->o = *opts;
     if (S->o.slots <= 0) S->o.slots = 8;
-    if (S->o.large_slots <= 0) S->o.large_slots = 1;
+    if (S->o.large_slots <= 0) S->o.large_slots = 2;
     int dev = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     S->dev = dev;
