@@ -138,21 +138,25 @@ def algorithmic_ops(r, Nt, Nn):
     return visited_all * (wt + 1) + scored * per_scored, visited_leaf * (wt + 1) + scored * per_scored
 
 
-def _profiled_traffic(kernel_file="k_solve_c2.md"):
-    """DRAM bytes per launch of the solve kernel from the committed ncu summary, if
-    that summary was taken from the kernel source as it is now (else None)."""
+def _profiled_fields(kernel_file="k_solve_c2.md"):
+    """Fields of the committed ncu summary of the solve kernel ("- `key`: `value`"
+    lines), if that summary was taken from the kernel source as it is now (else {})."""
     import hashlib
     src = os.path.join(ROOT, "paper_2603_16721_gb300", "csrc", "mh_kernels.cu")
     try:
         text = open(os.path.join(ROOT, "profiles", kernel_file)).read()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
-        return None
-    fields = dict(ln.strip("- `").split(": ", 1) for ln in text.splitlines() if ln.startswith("- `") and ": " in ln)
-    if fields.get("kernel_source_sha256", "").strip("`") != sha:
-        return None
+        return {}
+    fields = {k: v.strip("`") for k, v in (ln.strip("- `").split(": ", 1) for ln in text.splitlines()
+                                             if ln.startswith("- `") and ": " in ln)}
+    return fields if fields.get("kernel_source_sha256") == sha else {}
+
+
+def _profiled_traffic(kernel_file="k_solve_c2.md"):
+    """DRAM bytes per launch of the solve kernel from the committed ncu summary (or None)."""
     try:
-        return int(fields["dram_bytes_per_launch"].strip("`"))
+        return int(_profiled_fields(kernel_file)["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
 
@@ -161,13 +165,15 @@ def solve_roofline(res_list, Nt, Nn, peaks, source):
     """Integer-pipe roofline of the persistent solve kernel (the dominant kernel:
     one cooperative launch runs every round of a solve).
 
-    achieved = algorithmic 32-bit ops of a solve (algorithmic_ops) / the kernel's
-    duration (CUDA events around its launch on the solving stream);
-    peak = SMs x 64 int32 ops/clk x max SM clock.  The kernel tests 64 sibling
-    leaves with one OR per sample column word (bit-sliced), so it issues far fewer
-    operations than the per-node count; `issued` estimates the integer operations
-    the kernel itself executes in its leaf phase (from its own counters of column
-    words and exactly scored leaves) over that phase's time."""
+    achieved = algorithmic 32-bit ops of a solve (algorithmic_ops: the per-node and
+    per-leaf cost of the paper's search, applied to the solve's exact counters) /
+    the kernel's duration (CUDA events around its launch on the solving stream);
+    peak = SMs x 64 int32 ops/clk x max SM clock.  The kernel reaches the same
+    counters and argmax with far fewer operations (64 siblings per OR of a sample
+    column word; single-sample subtrees counted in closed form; TP = 1 leaves
+    represented by per-sample champions), so `achieved` is a work-equivalent rate.
+    What the hardware did is in `ncu` (from the committed profile of this kernel
+    source): integer-pipe and issue utilisation over the launch."""
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak = SMS * INT32_OPS_PER_SM_CLK * clk / 1e12
     ops = [algorithmic_ops(r, Nt, Nn) for r in res_list]
@@ -179,18 +185,20 @@ def solve_roofline(res_list, Nt, Nn, peaks, source):
     leaf_s = sum(r.leaf_ms for r in res_list) / 1e3
     leaf = None
     if leaf_s > 0:
-        la = sum(o[1] for o in ops) / leaf_s / 1e12
         # the kernel's own work in the leaf phase: 2 int32 ops per 64-bit column word
         # OR-ed in a sibling test (counted by the kernel) + ~14 per leaf scored exactly
         issued = sum(2 * r.leaf_words + 14 * r.leaf_scored for r in res_list) / leaf_s / 1e12
-        leaf = {"achieved": round(la, 4), "frac": round(la / peak, 4), "ms_per_solve": round(leaf_s * 1e3 / len(res_list), 4),
+        leaf = {"ms_per_solve": round(leaf_s * 1e3 / len(res_list), 4),
                 "issued": round(issued, 4), "issued_frac": round(issued / peak, 5)}
+    prof = _profiled_fields()
+    ncu = {k: float(prof[k]) for k in ("alu_pipe_active_pct", "issue_active_pct", "warps_active_pct",
+                                       "barrier_stall_per_issue") if k in prof} or None
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s (int32)",
             "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(),
             "kernel": "k_solve (persistent solve, one launch per solve)", "launches": launches,
             "avg_launch_us": round(kernel_s / launches * 1e6, 2),
             "ops_per_launch": round(sum(o[0] for o in ops) / launches),
-            "leaf_phase": leaf,
+            "leaf_phase": leaf, "ncu": ncu,
             "peak_source": f"derived: {SMS} SMs x {INT32_OPS_PER_SM_CLK} int32/clk x {clk / 1e6:.0f} MHz "
                            f"({source} max SM clock); no measured integer peak exists"}
 
@@ -355,6 +363,14 @@ def run_ours(args):
             "gpu_launches": int(sum(r.kernel_launches for r in results)),
             "clocks": clocks,
         }
+        if world == 1 and not args.no_extras:
+            # the other two parts of the metric, after the timed c2 steps: batched
+            # (16 uneven cohorts in one launch vs one after another) and served
+            # (request trace: continuous batching vs a plain loop)
+            b16 = batch16_comparison(argparse.Namespace(steps=3, warmup=1))
+            line["batched"] = {k: b16[k] for k in ("value", "unit", "sequential_value", "speedup_vs_sequential",
+                                                   "identical_to_sequential", "config")}
+            line["served"] = served_comparison(argparse.Namespace(requests=200, slots=8, large_slots=0))
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -372,6 +388,11 @@ MODES = {"persistent": 0, "launches": 1}
 
 
 def run_batch16(args):
+    print(json.dumps(batch16_comparison(args)))
+    return 0
+
+
+def batch16_comparison(args):
     """Batched workload: 16 cohorts of uneven size (seeds 100-115, h=3 for 12, h=4 for 4)
     solved in one persistent launch, against the same 16 solved one after another."""
     import torch
@@ -408,7 +429,7 @@ def run_batch16(args):
         bat.append(time.perf_counter() - t0)
     bat_t = statistics.median(bat[args.warmup:])
     same = all(a.records() == b.records() for a, b in zip(rs, rb))
-    print(json.dumps({
+    out = ({
         "metric": "batched_wsc_solves_per_s", "value": len(handles) / bat_t, "unit": "solves/s",
         "sequential_value": len(handles) / seq_t, "speedup_vs_sequential": seq_t / bat_t,
         "identical_to_sequential": same, "steps": args.steps, "warmup": args.warmup,
@@ -416,17 +437,23 @@ def run_batch16(args):
                                "Nn~U[50,500], h=3 x12 and h=4 x4, alpha=1/10"},
         "per_cohort": [{"G": c.G, "Nt": c.Nt, "Nn": c.Nn, "h": sp.h, "k": r.k, "rounds": r.rounds,
                         "solo_ms": round(r.solve_ms, 3)} for c, sp, r in zip(cohorts, specs, rs)],
-    }))
+    })
     for H in handles:
         H.close()
-    return 0
+    return out
 
 
 def run_served(args):
+    print(json.dumps(served_comparison(args)))
+    return 0
+
+
+def served_comparison(args):
     """Served workload: a trace of requests (c3-law cohorts, Poisson arrivals at 5/s,
     h from {2: .3, 3: .5, 4: .2}) replayed in real time against (i) the served
     runtime (continuous batching) and (ii) a plain FIFO loop of one solve (one
-    persistent launch) per request; latency = arrival to result."""
+    persistent launch) per request; latency = arrival to result.  Then the same
+    requests all at once (saturated), for throughput at full load."""
     import threading
     import numpy as np
     import torch
@@ -494,7 +521,7 @@ def run_served(args):
     same = same and all(a.records() == b.records() for a, b in zip(plain_res, burst_res))
     mean_service = sum(service) / n
     plain_done = np.cumsum(service)  # the plain loop fed all requests at once
-    print(json.dumps({
+    return ({
         "metric": "served_wsc_solves_per_s", "value": n / served_span, "unit": "solves/s",
         "p50_ms": 1e3 * pct(served_lat, 0.50), "p99_ms": 1e3 * pct(served_lat, 0.99),
         "plain": {"value": n / plain_span, "p50_ms": 1e3 * pct(plain_lat, 0.50), "p99_ms": 1e3 * pct(plain_lat, 0.99),
@@ -508,8 +535,7 @@ def run_served(args):
         "identical_to_plain": same, "server_launches": stats["launches"],
         "config": {"workload": f"served: first {n} of 200 requests, c3-law cohorts (G=19000, Nt=800, Nn=400), "
                                "seeds 1000-1199, Poisson 5 req/s, h from {2:.3,3:.5,4:.2}, trace seed 5000"},
-    }))
-    return 0
+    })
 
 
 def main(argv=None):
@@ -520,6 +546,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--max-rounds", type=int, default=0, help="stop each solve after R rounds (profiling)")
     ap.add_argument("--kernels-only", action="store_true", help="time the solves only (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="c2: leave out the batched and served comparisons appended to the line")
     ap.add_argument("--mode", choices=["persistent", "launches"], default="persistent",
                     help="one persistent kernel per solve, or one launch per phase")
     ap.add_argument("--workload", choices=["c2", "batch16", "served200"], default="c2",

@@ -114,7 +114,8 @@ typedef struct {
     int32_t mode;            /* the mode that ran (MH_MODE_*) */
     uint64_t diag[8];        /* diagnostics, [expansion, leaf]: summed warp cycles, summed per-round
                                 longest warp cycles, warp count (indices 0-1, 2-3, 4-5); a batched
-                                result's diag[6] is 1 if every launch numbered its blocks SM-major */
+                                result's diag[6] is 1 if every launch numbered its blocks SM-major,
+                                diag[7] is 1 if its first launch ran from a captured CUDA graph */
     double kernel_ms;        /* persistent mode: the solve kernel's own duration (CUDA events around
                                 each cooperative launch, summed over relaunches); launch mode with
                                 time_kernels: the four phase times summed; else 0 */

@@ -534,6 +534,7 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
 Frontiers frontiers_of(const mh_handle *H)
 {
     Frontiers f;
+    memset(&f, 0, sizeof f);  // padding included: batch items are compared byte by byte
     for (int l = 0; l < kMaxH; ++l) {
         f.F[l] = H->dF[l];
         f.cap[l] = H->cap[l];
@@ -1024,10 +1025,37 @@ std::vector<int> split_grid(const std::vector<double> &work, double gamma, int n
 // between the unfinished cohorts (blocks ~ work^gamma, or the fixed split) and,
 // each time a cohort finishes, the launch ends and the remaining cohorts share
 // the whole grid again.  *ms receives the run's time (CUDA events).
+// The start of a batched solve -- every cohort's round-state initialisation and the
+// first cooperative launch over all of them -- is captured into a CUDA graph once
+// per launch signature (the items' bytes, which hold every device pointer and size,
+// the round limits, the stream and the launch buffers) and replayed when the same
+// cohorts are solved again, so a repeated batch costs one graph launch instead of
+// some 10 API calls per cohort.  Streams that cannot be captured (the legacy
+// default stream, or one already capturing) take the direct launches.
+struct StartGraph {
+    std::vector<char> key;
+    cudaGraphExec_t exec = nullptr;
+    BatchItem *h_items = nullptr;  // pinned copy of the items the graph uploads
+    int h_cap = 0;
+};
+StartGraph g_start;  // guarded by g_items_mutex
+
+bool capturable(cudaStream_t st)
+{
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
 int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, double gamma,
-              int build, const std::vector<int> *fixed, double *ms, int *sm_major = nullptr)
+              int build, const std::vector<int> *fixed, double *ms, int *sm_major = nullptr, int *graphed = nullptr)
 {
     if (sm_major) *sm_major = 1;
+    if (graphed) *graphed = 0;
     cudaStream_t st = hs[0]->stream;
     std::vector<Solve> ss(n);
     std::vector<int> maxr(n);
@@ -1039,7 +1067,12 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
     MH_CUDA(cudaEventCreate(&a));
     MH_CUDA(cudaEventCreate(&b));
     MH_CUDA(cudaEventRecord(a, st));
-    for (int i = 0; i < n; ++i) launch_solve_init(hs[i]->c, ss[i], hs[i]->ws_rounds, maxr[i], hs[i]->dCounts, kCountSets, st);
+    // every cohort's round state starts from scratch: issued with the first launch
+    bool init_pending = true;
+    auto issue_init = [&]() {
+        for (int i = 0; i < n; ++i)
+            launch_solve_init(hs[i]->c, ss[i], hs[i]->ws_rounds, maxr[i], hs[i]->dCounts, kCountSets, st);
+    };
     std::lock_guard<std::mutex> lock(g_items_mutex);
     if (g_items_cap < n) {
         cudaFree(g_items);
@@ -1066,6 +1099,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             blocks = split_grid(w, gamma, hs[0]->num_sms, build);
         }
         std::vector<BatchItem> items(act.size());
+        memset(items.data(), 0, sizeof(BatchItem) * items.size());  // padding too: the bytes are a graph key
         int first = 0;
         for (size_t k = 0; k < act.size(); ++k) {
             const int i = act[k];
@@ -1077,11 +1111,71 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
             items[k].first_block = first;
             items[k].nblocks = blocks[k];
             first += blocks[k];
-            MH_CUDA(cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st));
-            MH_CUDA(cudaMemsetAsync(hs[i]->dState + 6, 0, sizeof(int), st));  // yield request
         }
-        MH_CUDA(cudaMemsetAsync(d_yield, 0, sizeof(int), st));
-        if (act.size() == 1 && !fixed) {
+        auto issue_prep = [&]() {
+            for (int i : act) {
+                cudaMemsetAsync(hs[i]->dSync, 0, sizeof(GridSync), st);
+                cudaMemsetAsync(hs[i]->dState + 6, 0, sizeof(int), st);  // yield request
+            }
+            return cudaMemsetAsync(d_yield, 0, sizeof(int), st);
+        };
+        // the start of the solve from a captured graph (see StartGraph)
+        bool started = false;
+        if (init_pending && act.size() > 1 && capturable(st)) {
+            std::vector<char> key(sizeof(BatchItem) * items.size());
+            memcpy(key.data(), items.data(), key.size());
+            auto put = [&](const void *p, size_t bytes) {
+                key.insert(key.end(), (const char *)p, (const char *)p + bytes);
+            };
+            for (int i = 0; i < n; ++i) {
+                put(&hs[i]->ws_rounds, sizeof(int));
+                put(&maxr[i], sizeof(int));
+            }
+            put(&st, sizeof st);
+            put(&g_items, sizeof g_items);
+            put(&map, sizeof map);
+            if (g_start.exec && g_start.key == key) {
+                started = cudaGraphLaunch(g_start.exec, st) == cudaSuccess;
+            } else {
+                if (g_start.h_cap < (int)items.size()) {
+                    if (g_start.h_items) cudaFreeHost(g_start.h_items);
+                    g_start.h_items = nullptr;
+                    g_start.h_cap = 0;
+                    if (cudaMallocHost((void **)&g_start.h_items, sizeof(BatchItem) * items.size()) == cudaSuccess)
+                        g_start.h_cap = (int)items.size();
+                }
+                cudaGraph_t g = nullptr;
+                if (g_start.h_cap >= (int)items.size() &&
+                    cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    memcpy(g_start.h_items, items.data(), sizeof(BatchItem) * items.size());
+                    issue_init();
+                    issue_prep();
+                    cudaMemcpyAsync(g_items, g_start.h_items, sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                                    st);
+                    launch_solve_batch(g_items, (int)items.size(), d_yield, map, st);
+                    cudaGraphExec_t ex = nullptr;
+                    if (cudaStreamEndCapture(st, &g) == cudaSuccess && g &&
+                        cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                        if (g_start.exec) cudaGraphExecDestroy(g_start.exec);
+                        g_start.exec = ex;
+                        g_start.key.swap(key);
+                        started = cudaGraphLaunch(ex, st) == cudaSuccess;
+                    }
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaGetLastError();  // a stream that could not be captured: launch directly
+            }
+            if (started && graphed) *graphed = 1;
+        }
+        if (init_pending && !started) issue_init();
+        init_pending = false;
+        if (!started) MH_CUDA(issue_prep());
+        if (started) {
+            MH_CUDA(cudaStreamSynchronize(st));
+            int fell_back = 0;
+            MH_CUDA(cudaMemcpy(&fell_back, map.tab + 2 * kMaxSmid + 1, sizeof(int), cudaMemcpyDeviceToHost));
+            if (fell_back && sm_major) *sm_major = 0;
+        } else if (act.size() == 1 && !fixed) {
             // one cohort left: the single-cohort persistent kernel (its fields are kernel
             // parameters, which the compiler keeps out of registers)
             mh_handle *H = hs[act[0]];
@@ -1164,17 +1258,17 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         work_l[i] = work_estimate(handles[i], opts[i].h);
     }
     double ms = 0.0;
-    int rc = MH_OK, smm = 0;
+    int rc = MH_OK, smm = 0, graphed = 0;
     // a choice of the autotuner, encoded as 100 * (build == 4) + 10 * model + gamma
     auto run_choice = [&](double choice, double *t, int *smm_out) {
         const int build = choice >= 100.0 ? 4 : 3;
         if (choice >= 100.0) choice -= 100.0;
         const bool leaves = choice >= 10.0;
         return run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), build, nullptr,
-                         t, smm_out);
+                         t, smm_out, smm_out ? &graphed : nullptr);
     };
     if (blocks) {
-        rc = run_batch(handles, opts, n, work_p, 1.0, 3, &b, &ms, &smm);
+        rc = run_batch(handles, opts, n, work_p, 1.0, 3, &b, &ms, &smm, &graphed);
     } else {
         // autotuner: the kernel build (3 or 4 blocks per SM), the work model and the
         // split exponent gamma (blocks ~ work^gamma) are chosen by timing each
@@ -1208,7 +1302,10 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
         rc = collect_result(handles[i], opts[i].h, true, ms, nullptr, 1, 0, &out[i], ms);
-        if (rc == MH_OK) out[i]->diag[6] = (uint64_t)smm;
+        if (rc == MH_OK) {
+            out[i]->diag[6] = (uint64_t)smm;
+            out[i]->diag[7] = (uint64_t)graphed;
+        }
         if (rc) {
             for (int j = 0; j < i; ++j) {
                 mh_result_free(out[j]);

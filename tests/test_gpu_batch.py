@@ -89,3 +89,28 @@ def test_batch_blocks_numbered_sm_major(mh):
     assert all(r.diag[6] == 1 for r in got)
     for H in handles:
         H.close()
+
+
+def test_batch_start_replays_a_captured_graph(mh, tmp_path, monkeypatch):
+    """On a non-default stream the start of a batched solve (every cohort's round
+    state and the first cooperative launch) runs from a captured CUDA graph; solving
+    the same cohorts again replays it, with the results of solving each alone."""
+    import torch
+    monkeypatch.setenv("MH_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    monkeypatch.setenv("MH_AUTOTUNE", "0")
+    cohorts = _mixed_cohorts()
+    stream = torch.cuda.Stream()
+    handles = [mh.mh_create(bm, G, Nt, Nn) for bm, G, Nt, Nn, h in cohorts]
+    try:
+        for H in handles:
+            mh.mh_set_stream(H, stream.cuda_stream)
+        hs = [h for *_, h in cohorts]
+        alone = [mh.mh_solve(H, h) for H, h in zip(handles, hs)]
+        for _ in range(3):
+            rs = mh.mh_solve_batch(handles, hs)
+            for r, a in zip(rs, alone):
+                _same(r, a)
+                assert r.diag[7] == 1
+    finally:
+        for H in handles:
+            H.close()
