@@ -377,6 +377,36 @@ __device__ __noinline__ void single_sample_subtree(const u16 *genes, int n, int 
     }
 }
 
+// The same recurrence for a compile-time number of levels K = h - d (2 or 3: the
+// subtrees of depth-1 and depth-2 nodes for h <= 5), with every sum in registers.
+template <int K>
+__device__ __noinline__ void single_sample_subtree_k(const u16 *genes, int n, int G, int h, int d, int g, u64 *deep)
+{
+    const int hi0 = G - h + d - 1;
+    u64 S[K + 1], av[K + 1], vi[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) S[k] = av[k] = vi[k] = 0;
+    vi[1] = (u64)(hi0 + 1 - g);
+    for (int i = 0; i < n; ++i) {
+        const int b = (int)__ldg(genes + i);
+#pragma unroll
+        for (int k = K; k >= 1; --k) {
+            if (b > hi0 + k) continue;
+            const u64 f = k == 1 ? 1ull : S[k - 1];
+            av[k] += f;
+            if (k < K) {
+                vi[k + 1] += f * (u64)(hi0 + k + 1 - b);
+                S[k] += f;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 1; k <= K; ++k) {
+        if (vi[k]) atomicAdd(&deep[2 * (d + k)], vi[k]);
+        if (av[k]) atomicAdd(&deep[2 * (d + k) + 1], av[k]);
+    }
+}
+
 // Closed-form counters of the subtree below a depth-d node (d < h) with y = {smp}
 // and last gene g: the leaves of a leaf parent into vis_h / alive_h, a deeper
 // subtree into deep.
@@ -389,7 +419,10 @@ __device__ __forceinline__ void single_sample_count(const Cohort &c, int h, int 
         vis_h += (u64)(c.G - 1 - g);
         alive_h += (u64)(m - r);
     } else {
-        single_sample_subtree(c.SL + __ldg(c.SO + smp) + r, m - r, c.G, h, d, g, deep);
+        const u16 *genes = c.SL + __ldg(c.SO + smp) + r;
+        if (h - d == 2) single_sample_subtree_k<2>(genes, m - r, c.G, h, d, g, deep);
+        else if (h - d == 3) single_sample_subtree_k<3>(genes, m - r, c.G, h, d, g, deep);
+        else single_sample_subtree(genes, m - r, c.G, h, d, g, deep);
     }
 }
 
@@ -437,7 +470,10 @@ __device__ __forceinline__ bool gene_record(const Cohort &c, const u64 *Ush, int
 // handed out by kDispensers counters (warp gw draws from counter gw % kDispensers),
 // so warps that finish early take over the batches of slow ones.
 constexpr int kDispensers = 4;
-constexpr int kSmallWarps = 16;  // warps per block of the one-block-per-SM persistent build
+#ifndef MH_SMALL_WARPS
+#define MH_SMALL_WARPS 16
+#endif
+constexpr int kSmallWarps = MH_SMALL_WARPS;  // warps per block of the one-block-per-SM persistent build
 struct Dispenser {
     u32 nw, gw, it, it_static, R;
     u32 *ctr;
