@@ -1304,13 +1304,15 @@ __global__ void k_solve_init(Cohort c, Solve s, int max_rounds)
     if (w < kStateWords) s.state[w] = w == kStMaxRounds ? max_rounds : 0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_level1(Cohort c, Solve s, Frontiers f, u32 *counts)
+__global__ void __launch_bounds__(kThreads) k_level1(const __grid_constant__ Cohort c, const __grid_constant__ Solve s,
+                                                     const __grid_constant__ Frontiers f, u32 *counts)
 {
     if (halted(s)) return;
     phase_level1(c, s, s.state[kStRound], f, counts, grid_team(), launch_io(s));
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int level, Frontiers f, u32 *counts)
+__global__ void __launch_bounds__(kThreads, 4) k_expand(const __grid_constant__ Cohort c, const __grid_constant__ Solve s,
+                                                        int level, const __grid_constant__ Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
@@ -1320,7 +1322,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_expand(Cohort c, Solve s, int l
         s.state[kStOverflow] = 1;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, Frontiers f, u32 *counts)
+__global__ void __launch_bounds__(kThreads, 3) k_leaf(const __grid_constant__ Cohort c, const __grid_constant__ Solve s,
+                                                      const __grid_constant__ Frontiers f, u32 *counts)
 {
     __shared__ Batch scratch[kWarpsPerBlock];
     if (halted(s)) return;
@@ -1329,7 +1332,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_leaf(Cohort c, Solve s, Frontie
         s.state[kStOverflow] = 1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(Cohort c, Solve s, u32 *counts)
+__global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ Cohort c, const __grid_constant__ Solve s,
+                                                       u32 *counts)
 {
     if (halted(s)) return;
     phase_finalize(c, s, counts, s.nslots);
@@ -1773,7 +1777,8 @@ __global__ void k_barrier_probe(GridSync *g, int *state) { grid_sync(g, state, 2
 // latency: the large ones).
 template <int kMinBlocks, int kWarps>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
-    k_solve(Cohort c, Solve s, Frontiers f, GridSync *gsync, u32 *counts, int *yield)
+    k_solve(const __grid_constant__ Cohort c, const __grid_constant__ Solve s, const __grid_constant__ Frontiers f,
+            GridSync *gsync, u32 *counts, int *yield)
 {
     __shared__ Batch scratch[kWarps];
     solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5], yield);
