@@ -328,9 +328,11 @@ __device__ __forceinline__ int single_sample_mode(const Cohort &c, const Solve &
     return s.champ ? 1 : 0;
 }
 
+// champ_ok is written once per solve, before the grid barrier that precedes its
+// first read, so plain (L1-cached) loads see the final values.
 __device__ __forceinline__ bool single_sample_closed(int mode, const int *champ_ok, int smp)
 {
-    return mode == 2 || (mode == 1 && __ldcg(champ_ok + smp) != 0);
+    return mode == 2 || (mode == 1 && champ_ok[smp] != 0);
 }
 
 // Position in sample smp's gene list of its first gene after g.
@@ -908,9 +910,14 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
         unsigned dense;
         // the best score known to exist in the round decides whether single-sample
         // subtrees may be counted in closed form
-        u64 thr = 0;
-        if (lane == 0) thr = *(volatile u64 *)io.hint;
-        const int single = single_sample_mode(c, s, __shfl_sync(kFull, thr, 0));
+        // (with champions known, every sample whose champion is known qualifies: no
+        // threshold needed)
+        int single = 1;
+        if (!(s.champ && s.prune == 0 && c.CC)) {
+            u64 thr = 0;
+            if (lane == 0) thr = *(volatile u64 *)io.hint;
+            single = single_sample_mode(c, s, __shfl_sync(kFull, thr, 0));
+        }
         u64 alive_cf = 0;
         const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, hi_bound, all_children, b,
                                         lane, dense, visited, h, single, s.champ_ok, alive_cf, deep);
