@@ -1570,9 +1570,9 @@ __device__ void block_seed(const Cohort &c, const Solve &s, const Team &t, const
 // same inputs, so that all of them reach the same decisions without another
 // barrier: the winner (largest key of the round's slots), its TP / FP, the next U
 // (DelCols on the block's copy Ush, then written to s.U: every block writes the
-// same words), the next round's candidates (cand_sh) and their rescored threshold
-// (merged into next_hint).  Rank 0 also records the selection, the round state and
-// the candidates (for a later launch).  Returns true when the solve is done.
+// same words).  Rank 0 also picks the next round's candidates (cand_sh, and s.cand
+// for a later launch), rescores them into the next threshold (next_hint), and
+// records the selection and the round state.  Returns true when the solve is done.
 __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots, const Team &t,
                              u64 *Ush, Key *cand_sh, u64 *next_hint)
 {
@@ -1592,9 +1592,11 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
         if (key_better(k, best)) best = k;
     }
     // the best kCandidates of the warps' lane bests become next round's candidates
+    // (rank 0 keeps them and rescores them into the next threshold; the other blocks
+    // need only each warp's best)
     Key mine = best;
     const int per_warp = (kCandidates + nwarps - 1) / nwarps;
-    for (int r = 0; r < per_warp; ++r) {
+    for (int r = 0; r < (lead ? per_warp : 1); ++r) {
         const Key m = warp_max_key(mine);
         const int idx = warp * per_warp + r;
         if (lane == 0 && idx < kCandidates) {
@@ -1664,7 +1666,9 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
     }
     __syncthreads();
     const bool done = done_sh != 0;
-    if (!done && h > 1) block_rescore(c, s, cand_sh, Ush, next_hint);
+    // one block suffices: the threshold is a lower bound whichever blocks have merged
+    // into it, and it is first read after the next round's first barrier (h >= 3)
+    if (!done && h > 1 && lead) block_rescore(c, s, cand_sh, Ush, next_hint);
     return done;
 }
 
@@ -1703,7 +1707,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         cand_sh[i].t2 = __ldcg(&s.cand[i].t2);
     }
     __syncthreads();
-    if (h > 1) block_rescore(c, s, cand_sh, Ush, s.best_hint + (round & 1));
+    if (h > 1 && t.rank == 0) block_rescore(c, s, cand_sh, Ush, s.best_hint + (round & 1));
     if (h > 1 && round == 0 && s.prune == 0 && c.CC) {
         // the champions and the first round's threshold, complete before any block
         // starts searching
