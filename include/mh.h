@@ -187,7 +187,9 @@ MH_API int mh_check_bounded_wait(int32_t *status);
  * and cached in the file
  * named by MH_AUTOTUNE_CACHE (default ~/.cache/mh_autotune.txt; MH_AUTOTUNE=0
  * disables tuning).  Work runs on the first handle's stream; the call is
- * synchronous.  out: n result pointers, each as from mh_solve_ex (solve_ms is the
+ * synchronous.  On a stream other than the legacy default one, the start of the
+ * batch (every cohort's round state and the first launch) is captured as a CUDA
+ * graph and replayed when the same cohorts are solved again (diag[7]).  out: n result pointers, each as from mh_solve_ex (solve_ms is the
  * batch's time).  Errors: MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT; on error no
  * result is returned. */
 MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n, const int32_t *blocks,

@@ -159,6 +159,7 @@ struct mh_handle {
     int num_sms = 0, dev = 0;
     int64_t device_bytes = 0;
     // cohort store
+    unsigned char *dStore = nullptr;      // one block holding every piece below
     u64 *dT = nullptr, *dN = nullptr, *dCT = nullptr, *dCN = nullptr;
     u16 *dOrig = nullptr, *dCC = nullptr, *dSL = nullptr, *dSLo = nullptr;
     u32 *dSO = nullptr;
@@ -185,7 +186,7 @@ struct mh_handle {
     {
         for (int i = 0; i < 2; ++i)
             if (evk[i]) cudaEventDestroy(evk[i]);
-        for (void *p : {(void *)dT, (void *)dN, (void *)dCT, (void *)dCN, (void *)dCC, (void *)dSL, (void *)dSLo, (void *)dSO, (void *)dOrig, (void *)dInv, (void *)dU,
+        for (void *p : {(void *)dStore, (void *)dU,
                         (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk,
                         (void *)dCounts, (void *)dSync})
             dfree(p, stream);
@@ -292,26 +293,44 @@ int build_store(mh_handle *H, const uint64_t *bm)
     }
     int rc;
     cudaStream_t st = H->stream;
-    if ((rc = dalloc(&H->dT, T.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dN, N.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dCT, CT.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dCN, CN.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dCC, CC.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dSL, SL.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dSLo, SLo.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dSO, SO.size(), &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dOrig, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
-    if ((rc = dalloc(&H->dInv, (size_t)G, &H->device_bytes, H->dev, st))) return rc;
-    MH_CUDA(cudaMemcpyAsync(H->dT, T.data(), T.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dN, N.data(), N.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
-    if (!CT.empty()) MH_CUDA(cudaMemcpyAsync(H->dCT, CT.data(), CT.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
-    if (!CN.empty()) MH_CUDA(cudaMemcpyAsync(H->dCN, CN.data(), CN.size() * sizeof(u64), cudaMemcpyHostToDevice, st));
-    if (!CC.empty()) MH_CUDA(cudaMemcpyAsync(H->dCC, CC.data(), CC.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dSL, SL.data(), SL.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dSLo, SLo.data(), SLo.size() * sizeof(u16), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dSO, SO.data(), SO.size() * sizeof(u32), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dOrig, orig.data(), G * sizeof(u16), cudaMemcpyHostToDevice, st));
-    MH_CUDA(cudaMemcpyAsync(H->dInv, inv.data(), G * sizeof(u32), cudaMemcpyHostToDevice, st));
+    // the whole store in one device block, filled by one copy (256-byte aligned pieces)
+    size_t off = 0;
+    auto piece = [&](size_t bytes) {
+        const size_t o = off;
+        off += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t oT = piece(T.size() * sizeof(u64)), oN = piece(N.size() * sizeof(u64));
+    const size_t oCT = piece(CT.size() * sizeof(u64)), oCN = piece(CN.size() * sizeof(u64));
+    const size_t oCC = piece(CC.size() * sizeof(u16)), oSL = piece(SL.size() * sizeof(u16));
+    const size_t oSLo = piece(SLo.size() * sizeof(u16)), oSO = piece(SO.size() * sizeof(u32));
+    const size_t oOrig = piece((size_t)G * sizeof(u16)), oInv = piece((size_t)G * sizeof(u32));
+    std::vector<unsigned char> host(off, 0);
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+        if (bytes) memcpy(host.data() + o, src, bytes);
+    };
+    put(oT, T.data(), T.size() * sizeof(u64));
+    put(oN, N.data(), N.size() * sizeof(u64));
+    put(oCT, CT.data(), CT.size() * sizeof(u64));
+    put(oCN, CN.data(), CN.size() * sizeof(u64));
+    put(oCC, CC.data(), CC.size() * sizeof(u16));
+    put(oSL, SL.data(), SL.size() * sizeof(u16));
+    put(oSLo, SLo.data(), SLo.size() * sizeof(u16));
+    put(oSO, SO.data(), SO.size() * sizeof(u32));
+    put(oOrig, orig.data(), (size_t)G * sizeof(u16));
+    put(oInv, inv.data(), (size_t)G * sizeof(u32));
+    if ((rc = dalloc(&H->dStore, off, &H->device_bytes, H->dev, st))) return rc;
+    MH_CUDA(cudaMemcpyAsync(H->dStore, host.data(), off, cudaMemcpyHostToDevice, st));
+    H->dT = (u64 *)(H->dStore + oT);
+    H->dN = (u64 *)(H->dStore + oN);
+    H->dCT = (u64 *)(H->dStore + oCT);
+    H->dCN = (u64 *)(H->dStore + oCN);
+    H->dCC = (u16 *)(H->dStore + oCC);
+    H->dSL = (u16 *)(H->dStore + oSL);
+    H->dSLo = (u16 *)(H->dStore + oSLo);
+    H->dSO = (u32 *)(H->dStore + oSO);
+    H->dOrig = (u16 *)(H->dStore + oOrig);
+    H->dInv = (u32 *)(H->dStore + oInv);
     c.T = H->dT; c.N = H->dN; c.CT = H->dCT; c.CN = H->dCN; c.orig = H->dOrig; c.inv = H->dInv;
     c.CC = Nt ? H->dCC : nullptr;
     c.SL = H->dSL;
