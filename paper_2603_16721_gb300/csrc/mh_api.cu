@@ -466,9 +466,9 @@ namespace {
 
 double work_estimate(const mh_handle *H, int d);
 
-// Expected search work (work_estimate with d = h - 1) above which one solve keeps
-// the whole GPU busy: such a solve runs the build with four blocks per SM, and the
-// served runtime limits how many of them share the GPU.
+// Expected search work (work_estimate with d = h - 1) above which the served
+// runtime treats a request as "large" (it pauses for small ones and at most
+// large_slots of them share the GPU).
 constexpr double kLargeWork = 4.0e6;
 
 // Build of the single-cohort persistent kernel for a solve: one block of 16 warps
@@ -769,7 +769,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     launch_solve_init(c, s, H->ws_rounds, max_rounds, counts, kCountSets, st);
     ++launches;
     const bool persistent = opts->mode == MH_MODE_PERSISTENT && H->pgrid > 0 && H->pgrid <= H->ws_slots;
-    // large build for cohorts whose deepest frontier is expected to hold millions of prefixes
+    // one block of 16 warps per SM unless MH_PERSISTENT_BUILD=large
     const bool large = use_large_build(H, h);
     const int pgrid = persistent_grid(H->num_sms, large);
     int rounds_done = 0;

@@ -157,8 +157,9 @@ void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *count
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
 
 // Persistent solve: all rounds in one cooperative launch of `grid` blocks
-// (persistent_grid(): one block per SM for a small cohort, the co-resident
-// maximum of the large build otherwise; 0 if it cannot be determined).
+// (persistent_grid(): one block per SM for the default build, the co-resident
+// maximum of the four-blocks-per-SM build with `large`; 0 if it cannot be
+// determined).
 // It returns when the solve is done, a frontier overflowed (state) or a grid
 // barrier timed out (state error = kErrTimeout).
 int persistent_grid(int num_sms, bool large);
