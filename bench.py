@@ -6,6 +6,9 @@ seed 1; see synth/), with the cohort already resident on the device.  Between
 timed steps a 256 MiB buffer is written to flush L2 (the cohort is far smaller
 than L2).  Each step is timed with CUDA events on the solving stream; the timed
 region is bracketed by barrier + synchronize; the result is the max over ranks.
+On one GPU the line also carries the batched workload (16 uneven cohorts in one
+launch against one after another) and the served one (a request trace replayed
+against the continuous-batching server and against a plain loop).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -70,10 +73,15 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # the timed region starts once nvidia-smi is sampling (at most 3 s)
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.lines.clear()
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -541,7 +549,7 @@ def served_comparison(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--max-rounds", type=int, default=0, help="stop each solve after R rounds (profiling)")
