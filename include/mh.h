@@ -51,7 +51,7 @@ extern "C" {
 
 typedef struct mh_handle mh_handle;
 
-/* alpha = num / den of the weight function F (§II-B; "often set to 0.1", i.e. {1, 10}).
+/* alpha = num / den of the weight function F (§II-B; the paper's usual 0.1 is {1, 10}).
  * Requires 0 <= num and 0 < den, both below 2^31. */
 typedef struct {
     int32_t num;
@@ -262,9 +262,10 @@ MH_API void mh_server_destroy(mh_server *server);
  *   stream    : cudaStream_t (NULL = legacy default stream); the call is synchronous.
  * Limits: G <= 8192, Nt <= 1024, Nn <= 1024, 1 <= h <= 4, and at most 2^17
  * prefixes per intermediate depth of the search; larger inputs return MH_EINVAL,
- * a larger frontier MH_ENOMEM, each with a message naming the limit.  The first
- * call on a device looks up the array's device address (once per device); make
- * that first call before any CUDA stream capture.  All calls share the array and
+ * a larger frontier MH_ENOMEM, each with a message naming the limit.  Every call
+ * looks up the array's device address on the current device (cudaGetSymbolAddress,
+ * so calls may span a device reset); the first call on a device also loads the
+ * library's device code there, so make it before any CUDA stream capture.  All calls share the array and
  * each leaves its contents behind (every call clears what must start at zero):
  * calls whose GPU work overlaps, on different streams or host threads, race on
  * it and must be serialised by the caller.  No cudaMalloc, cudaFree or

@@ -16,7 +16,7 @@ Functions (all results use original gene indices, ascending inside a tuple):
 
 Readings of the paper that these functions fix (each is pinned by a test):
   * F = (alpha T+ + T-) / (Nt + Nn) with T- = Nn - FP, FP the normals that
-    carry all genes of the combination (the "all" of Eq. 1); with
+    carry all genes of the combination (coverage in Eq. 1 needs every gene); with
     alpha = a_num / a_den the integer S = a_num TP + a_den (Nn - FP) orders
     candidates exactly as F does.
   * A combination with TP = 0 is never a candidate (§III-D scores only leaves

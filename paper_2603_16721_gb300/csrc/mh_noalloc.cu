@@ -20,7 +20,6 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "mh.h"
 #include "mh_internal.h"
@@ -36,7 +35,6 @@ constexpr int kNaMaxNn = 1024;
 constexpr int kNaMaxH = 4;
 constexpr u32 kNaFrontierCap = 1u << 17;  // entries per intermediate depth
 constexpr int kNaMaxSlots = 4096;
-constexpr int kNaMaxDevices = 64;
 
 constexpr int kNaWTp = kNaMaxNt / 64;  // 16 words
 constexpr int kNaWNp = kNaMaxNn / 64;
@@ -139,10 +137,6 @@ __global__ void k_na_unpack(const int *res, const int *state, int h, int capacit
     }
 }
 
-std::mutex g_setup_mutex;
-unsigned char *g_scratch_ptr[kNaMaxDevices] = {};
-int g_num_sms[kNaMaxDevices] = {};
-
 int na_fail(int code, const char *fmt, ...)
 {
     char buf[384];
@@ -160,27 +154,22 @@ int na_fail(int code, const char *fmt, ...)
         if (e_ != cudaSuccess) return na_fail(MH_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
     } while (0)
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device, looked up on every
+// call: an address kept from an earlier call would be stale after a device reset
+// or with a new primary context, and the lookup costs little next to a solve.
 int scratch_for_current_device(unsigned char **ptr, int *num_sms)
 {
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNaMaxDevices) return na_fail(MH_EINVAL, "device %d beyond the supported %d", dev,
-                                                         kNaMaxDevices);
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return na_fail(MH_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return na_fail(MH_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-        g_num_sms[dev] = sms;
-        g_scratch_ptr[dev] = (unsigned char *)p;
-    }
-    *ptr = g_scratch_ptr[dev];
-    *num_sms = g_num_sms[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return na_fail(MH_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return na_fail(MH_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    *ptr = (unsigned char *)p;
+    *num_sms = sms;
     return MH_OK;
 }
 

@@ -2,7 +2,8 @@
 
 The paper's cohorts (TCGA somatic mutations, §IV-B) are not available, so these
 stand in for them: binary gene x sample matrices with very sparse, heavy-tailed
-per-gene rates (the "few mountains, many hills" profile of §III-A) and a few
+per-gene rates (a few very frequently mutated genes and a long tail of rare
+ones, the profile of §III-A) and a few
 planted co-mutated gene combinations.  The generator is plain C
 (``cohort_gen.c``), loaded through ctypes, so that cohorts with ~20k genes are
 drawn in well under a second.  Both the oracle and the CUDA library take the

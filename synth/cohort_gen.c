@@ -3,7 +3,8 @@
  *
  * This module only draws inputs: binary gene x sample mutation matrices shaped
  * like the somatic-mutation cohorts of the paper's experiments (§IV-B: very
- * sparse rows, "few mountains, many hills", §III-A), packed in the layout the
+ * sparse rows, a few frequent genes and a long tail of rare ones, §III-A), packed
+ * in the layout the
  * solver library and the oracle both accept.  It contains none of the method's
  * arithmetic (no covers, no scores, no search).
  *
