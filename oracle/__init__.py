@@ -13,6 +13,14 @@ Functions (all results use original gene indices, ascending inside a tuple):
   sparsity_order(...)  -- the §III-C gene order (ascending tumor mutation count,
                           ties by original index).
   cover_counts(...)    -- TP / FP of given combinations against a mask U.
+  pdfs_mt(...)         -- the same P-DFS on several threads (``pdfs_mt.c``: the
+                          depth-1 subtrees handed out by an atomic counter, the
+                          paper's master-worker scheme of §III-E on host cores),
+                          optionally with the score-bound cut; the multi-core
+                          CPU baseline.
+  mt_round(...)        -- one round of that search over a given U, optionally on
+                          one shard of the depth-1 genes (the per-round unit of a
+                          multi-process solve); ``delcols(...)`` applies a winner.
 
 Readings of the paper that these functions fix (each is pinned by a test):
   * F = (alpha T+ + T-) / (Nt + Nn) with T- = Nn - FP, FP the normals that
@@ -36,17 +44,18 @@ from dataclasses import dataclass, field
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "pdfs_mt.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, EINVAL, ENOMEM, ECAP = 0, 1, 3, 8
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``oracle/liboracle.so``."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    """Compile ``oracle.c`` and ``pdfs_mt.c`` into ``oracle/liboracle.so``."""
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -71,6 +80,14 @@ def _load():
         lib.oracle_sparsity_order.argtypes = [_P, _I32, _I32, _I32, _P]
         lib.oracle_cover_counts.restype = ctypes.c_int
         lib.oracle_cover_counts.argtypes = [_P, _I32, _I32, _I32, _I32, _P, _I32, _P, _P, _P]
+        lib.pdfs_mt_round.restype = ctypes.c_int
+        lib.pdfs_mt_round.argtypes = [_P, _I32, _I32, _I32, _I32, _I64, _I64, _I32, _P, _P, _I32, _I32, _I32,
+                                      _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.pdfs_mt_delcols.restype = ctypes.c_int
+        lib.pdfs_mt_delcols.argtypes = [_P, _I32, _I32, _I32, _I32, _P, _P]
+        lib.pdfs_mt_solve.restype = ctypes.c_int
+        lib.pdfs_mt_solve.argtypes = [_P, _I32, _I32, _I32, _I32, _I64, _I64, _I32, _I32, _I32, _I32,
+                                      _P, _P, _P, _P, _I32, _P, _P, _P, _P]
         _lib = lib
     return _lib
 
@@ -176,3 +193,80 @@ def full_tumor_mask(Nt: int) -> np.ndarray:
         rem = Nt - 64 * w
         U[w] = np.uint64(0xFFFFFFFFFFFFFFFF) if rem >= 64 else np.uint64((1 << rem) - 1)
     return U[:Wt]
+
+
+# Pruning modes of the threaded P-DFS.
+MT_PRUNE_OFF, MT_PRUNE_PAPER, MT_PRUNE_BOUND = 0, 1, 2
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+
+
+def pdfs_mt(bitmaps, G, Nt, Nn, h, alpha=(1, 10), prune=MT_PRUNE_PAPER, max_rounds=-1, threads=None) -> Solution:
+    """Threaded P-DFS (``pdfs_mt.c``); ``Solution.cut`` holds the bound-mode cuts."""
+    bm = _prep(bitmaps, G, Nt, Nn)
+    threads = default_threads() if threads is None else threads
+    cap = Nt + 1
+    genes = np.zeros((cap, h), dtype=np.int32)
+    tp = np.zeros(cap, dtype=np.int32)
+    fp = np.zeros(cap, dtype=np.int32)
+    visited = np.zeros((cap + 1, h), dtype=np.uint64)
+    pruned = np.zeros((cap + 1, h), dtype=np.uint64)
+    cut = np.zeros((cap + 1, h), dtype=np.uint64)
+    k = ctypes.c_int32()
+    rounds = ctypes.c_int32()
+    rc = _load().pdfs_mt_solve(bm.ctypes.data, G, Nt, Nn, h, alpha[0], alpha[1], int(prune), max_rounds,
+                               int(threads), cap, genes.ctypes.data, tp.ctypes.data, fp.ctypes.data,
+                               ctypes.byref(k), cap + 1, visited.ctypes.data, pruned.ctypes.data,
+                               cut.ctypes.data, ctypes.byref(rounds))
+    _check(rc, "pdfs_mt_solve")
+    n, r = k.value, rounds.value
+    sol = Solution(genes[:n].copy(), tp[:n].copy(), fp[:n].copy(), visited[:r].copy(), pruned[:r].copy())
+    sol.cut = cut[:r].copy()
+    return sol
+
+
+@dataclass
+class RoundResult:
+    """One round's search on one shard: best candidate (or none) and counters."""
+    have: bool
+    score: int
+    genes: tuple
+    tp: int
+    fp: int
+    visited: np.ndarray
+    pruned: np.ndarray
+    cut: np.ndarray
+
+
+def mt_round(bitmaps, G, Nt, Nn, h, U, alpha=(1, 10), prune=MT_PRUNE_PAPER, order=None, threads=1, shard=0,
+             nshards=1) -> RoundResult:
+    bm = _prep(bitmaps, G, Nt, Nn)
+    order = sparsity_order(bm, G, Nt, Nn) if order is None else np.ascontiguousarray(order, dtype=np.int32)
+    U = np.ascontiguousarray(U, dtype=np.uint64)
+    have = ctypes.c_int32()
+    score = ctypes.c_int64()
+    tup = np.zeros(h, dtype=np.int32)
+    tp = ctypes.c_int32()
+    fp = ctypes.c_int32()
+    visited = np.zeros(h, dtype=np.uint64)
+    pruned = np.zeros(h, dtype=np.uint64)
+    cut = np.zeros(h, dtype=np.uint64)
+    rc = _load().pdfs_mt_round(bm.ctypes.data, G, Nt, Nn, h, alpha[0], alpha[1], int(prune), order.ctypes.data,
+                               U.ctypes.data, int(threads), int(shard), int(nshards), ctypes.byref(have),
+                               ctypes.byref(score), tup.ctypes.data, ctypes.byref(tp), ctypes.byref(fp),
+                               visited.ctypes.data, pruned.ctypes.data, cut.ctypes.data)
+    _check(rc, "pdfs_mt_round")
+    return RoundResult(bool(have.value), int(score.value), tuple(int(x) for x in tup), int(tp.value),
+                       int(fp.value), visited, pruned, cut)
+
+
+def delcols(bitmaps, G, Nt, Nn, genes, U) -> np.ndarray:
+    """U with the tumors covered by ``genes`` cleared (Algorithm 1's DelCols)."""
+    bm = _prep(bitmaps, G, Nt, Nn)
+    out = np.ascontiguousarray(U, dtype=np.uint64).copy()
+    t = np.ascontiguousarray(genes, dtype=np.int32)
+    _check(_load().pdfs_mt_delcols(bm.ctypes.data, G, Nt, Nn, t.size, t.ctypes.data, out.ctypes.data),
+           "pdfs_mt_delcols")
+    return out
