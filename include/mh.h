@@ -274,6 +274,16 @@ MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, in
                             mh_rational alpha, void *stream, int32_t *d_genes, int32_t *d_tp, int32_t *d_fp,
                             int32_t capacity, int32_t *k_out, int32_t *rounds_out);
 
+/* Diagnostic (no counterpart in the paper): measured integer throughput of the
+ * current GPU, the denominator of the search kernels' integer roofline.  One
+ * kernel keeps every SM busy with one 32-bit operation in independent chains:
+ * op 0 = LOP3 (three-input logic), 1 = POPC, 2 = IADD.  *ops_per_s receives the
+ * thread operations retired per second (best of three timed launches after one
+ * warm-up, CUDA events on the legacy default stream); *kernel_ms (may be NULL)
+ * the duration of that launch.  Allocates a small output buffer with cudaMalloc.
+ * Errors: MH_EINVAL (bad op or NULL ops_per_s), MH_ECUDA. */
+MH_API int mh_int_peak(int32_t op, double *ops_per_s, double *kernel_ms);
+
 /* Cohort dimensions of a handle (any pointer may be NULL). */
 MH_API int mh_handle_info(const mh_handle *handle, int32_t *G, int32_t *Nt, int32_t *Nn,
                           int64_t *device_bytes);

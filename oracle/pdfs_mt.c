@@ -113,20 +113,21 @@ static void mt_level(mt_worker *wk, int level, int first)
     for (int g = first; g <= last; ++g) {
         if (level == 1 && g != first) break; /* depth 1: one unit (one gene) per call */
         const uint64_t *row = rc->bm + (size_t)rc->order[g] * rc->W;
-        int ky = 0;
+        uint64_t any = 0;
         for (int w = 0; w < Wt; ++w) {
             yc[w] = yp[w] & row[w];
-            ky += __builtin_popcountll(yc[w]);
+            any |= yc[w];
         }
         for (int w = 0; w < Wn; ++w) nc[w] = np[w] & row[Wt + w];
         wk->path[level - 1] = g;
         wk->visited[level - 1] += 1;
-        if (ky == 0) {
+        if (!any) {
             wk->pruned[level - 1] += 1;
             if (rc->prune != MT_PRUNE_OFF) continue;
         }
         if (level < h) {
             if (rc->prune == MT_PRUNE_BOUND) {
+                const int ky = mt_popcount_words(yc, Wt);
                 const int64_t ub = rc->a_num * (int64_t)ky + rc->a_den * (int64_t)rc->Nn;
                 if (ub < (int64_t)atomic_load(&rc->best_known)) {
                     wk->cut[level - 1] += 1;
@@ -136,7 +137,8 @@ static void mt_level(mt_worker *wk, int level, int first)
             mt_level(wk, level + 1, g + 1);
             continue;
         }
-        if (ky == 0) continue; /* TP = 0: not a candidate */
+        if (!any) continue; /* TP = 0: not a candidate */
+        const int ky = mt_popcount_words(yc, Wt);
         const int FP = mt_popcount_words(nc, Wn);
         const int64_t S = rc->a_num * (int64_t)ky + rc->a_den * (int64_t)(rc->Nn - FP);
         if (wk->have && S < wk->best_s) continue;

@@ -1,6 +1,6 @@
 """Build of libmh.so (CUDA, sm_103a) in the package directory.
 
-Two translation units are compiled in parallel with nvcc and linked into one
+The translation units are compiled in parallel with nvcc and linked into one
 shared library with the CUDA runtime linked statically, so that loading the
 library needs no GPU and no particular libcudart on the search path.
 """
@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmh.so")
 
-SOURCES = ["mh_kernels.cu", "mh_api.cu", "mh_noalloc.cu"]
+SOURCES = ["mh_kernels.cu", "mh_api.cu", "mh_noalloc.cu", "mh_diag.cu"]
 HEADERS = ["mh_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

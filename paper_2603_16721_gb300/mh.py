@@ -111,6 +111,18 @@ def mh_check_bounded_wait() -> int:
     return int(st.value)
 
 
+def mh_int_peak(op: int = 0):
+    """Measured integer throughput of the current GPU: (thread ops/s, kernel ms) of
+    op 0 = LOP3, 1 = POPC, 2 = IADD."""
+    lib = load()
+    lib.mh_int_peak.restype = ctypes.c_int
+    lib.mh_int_peak.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    _check(lib.mh_int_peak(op, ctypes.byref(v), ctypes.byref(ms)))
+    return float(v.value), float(ms.value)
+
+
 def mh_last_error() -> str:
     return load().mh_last_error().decode()
 
