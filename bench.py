@@ -13,9 +13,14 @@ against the continuous-batching server and against a plain loop).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs under torchrun: every rank solves its own copy of the workload (weak
-scaling, no collective on the data path).  --impl reference times the CPU oracle
-(the paper's P-DFS restated in plain C, single-threaded) on a bounded sample of
-the same workload.
+scaling, no collective on the data path).  --impl reference times the CPU P-DFS
+of oracle/ (threaded over every host core, checked against the single-threaded
+oracle) solving the same workload, one whole solve per step.
+
+The line's roofline compares the solve kernel's executed integer work (from the
+committed ncu capture of the same kernel source) with this GPU's measured LOP3
+rate; cpu_baseline is measured on this host without extrapolation; plain_configs
+adds the c1 and c3 single-cohort solves.
 """
 from __future__ import annotations
 
@@ -116,19 +121,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except (OSError, ValueError):
-        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
-# Integer pipe of one SM per clock (32-bit results): logical / add ops and popcount.
-INT32_OPS_PER_SM_CLK = 64
-SMS = 152
-
-
 def algorithmic_ops(r, Nt, Nn):
     """32-bit integer operations the P-DFS of §III-D performs for a solve's counters.
 
@@ -161,115 +153,124 @@ def _profiled_fields(kernel_file="k_solve_c2.md"):
     return fields if fields.get("kernel_source_sha256") == sha else {}
 
 
-def _profiled_traffic(kernel_file="k_solve_c2.md"):
-    """DRAM bytes per launch of the solve kernel from the committed ncu summary (or None)."""
+def _profiled_int(key, kernel_file="k_solve_c2.md"):
     try:
-        return int(_profiled_fields(kernel_file)["dram_bytes_per_launch"])
+        return int(float(_profiled_fields(kernel_file)[key]))
     except (KeyError, ValueError):
         return None
 
 
-def solve_roofline(res_list, Nt, Nn, peaks, source):
+def int_peaks():
+    """Measured integer throughput of this GPU (thread ops/s): LOP3 and POPC."""
+    from paper_2603_16721_gb300 import mh
+    lop3, _ = mh.mh_int_peak(0)
+    popc, _ = mh.mh_int_peak(1)
+    return {"lop3_tops": lop3 / 1e12, "popc_tops": popc / 1e12}
+
+
+def solve_roofline(res_list, Nt, Nn, peaks_int, kernel_file="k_solve_c2.md"):
     """Integer-pipe roofline of the persistent solve kernel (the dominant kernel:
     one cooperative launch runs every round of a solve).
 
-    achieved = algorithmic 32-bit ops of a solve (algorithmic_ops: the per-node and
-    per-leaf cost of the paper's search, applied to the solve's exact counters) /
-    the kernel's duration (CUDA events around its launch on the solving stream);
-    peak = SMs x 64 int32 ops/clk x max SM clock.  The kernel reaches the same
-    counters and argmax with far fewer operations (64 siblings per OR of a sample
-    column word; single-sample subtrees counted in closed form; TP = 1 leaves
-    represented by per-sample champions), so `achieved` is a work-equivalent rate.
-    What the hardware did is in `ncu` (from the committed profile of this kernel
-    source): integer-pipe and issue utilisation over the launch."""
-    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak = SMS * INT32_OPS_PER_SM_CLK * clk / 1e12
+    achieved = the integer and logic thread instructions one launch executes
+    (sm__sass_thread_inst_executed_op_integer_pred_on + ..._op_bit_pred_on, from
+    the committed ncu capture of this kernel source on the same workload) / the
+    launch's duration measured here (CUDA events around each cooperative launch on
+    the solving stream); peak = the measured LOP3 rate of this GPU (mh_int_peak).
+    work_equiv = the paper's per-node cost of the same search (algorithmic_ops,
+    SURVEY-style units: every visited node and scored leaf of the exact counters)
+    over the same duration: the rate a kernel doing the paper's work would need;
+    the kernel reaches the same counters with far fewer operations, so this is not
+    pipe utilisation."""
     ops = [algorithmic_ops(r, Nt, Nn) for r in res_list]
     kernel_s = sum(r.kernel_ms for r in res_list) / 1e3
     launches = sum(max(1, r.kernel_launches - 1) for r in res_list)  # minus the init kernel
     if kernel_s <= 0:
         return None
-    achieved = sum(o[0] for o in ops) / kernel_s / 1e12
-    leaf_s = sum(r.leaf_ms for r in res_list) / 1e3
-    leaf = None
-    if leaf_s > 0:
-        # the kernel's own work in the leaf phase: 2 int32 ops per 64-bit column word
-        # OR-ed in a sibling test (counted by the kernel) + ~14 per leaf scored exactly
-        issued = sum(2 * r.leaf_words + 14 * r.leaf_scored for r in res_list) / leaf_s / 1e12
-        leaf = {"ms_per_solve": round(leaf_s * 1e3 / len(res_list), 4),
-                "issued": round(issued, 4), "issued_frac": round(issued / peak, 5)}
-    prof = _profiled_fields()
+    avg_s = kernel_s / launches
+    peak = peaks_int["lop3_tops"]
+    executed = _profiled_int("int_thread_ops_per_launch", kernel_file)
+    achieved = executed / avg_s / 1e12 if executed else None
+    wequiv = sum(o[0] for o in ops) / launches / avg_s / 1e12
+    prof = _profiled_fields(kernel_file)
     ncu = {k: float(prof[k]) for k in ("alu_pipe_active_pct", "issue_active_pct", "warps_active_pct",
-                                       "barrier_stall_per_issue") if k in prof} or None
-    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2), "unit": "Tops/s (int32)",
-            "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(),
+                                       "barrier_stall_per_issue", "duration_ms") if k in prof} or None
+    return {"bound": "alu", "achieved": round(achieved, 4) if achieved else None, "peak": round(peak, 3),
+            "unit": "Tops/s (int32 thread ops)", "frac": round(achieved / peak, 4) if achieved else None,
+            "traffic": _profiled_int("dram_bytes_per_launch", kernel_file),
             "kernel": "k_solve (persistent solve, one launch per solve)", "launches": launches,
-            "avg_launch_us": round(kernel_s / launches * 1e6, 2),
-            "ops_per_launch": round(sum(o[0] for o in ops) / launches),
-            "leaf_phase": leaf, "ncu": ncu,
-            "peak_source": f"derived: {SMS} SMs x {INT32_OPS_PER_SM_CLK} int32/clk x {clk / 1e6:.0f} MHz "
-                           f"({source} max SM clock); no measured integer peak exists"}
+            "avg_launch_us": round(avg_s * 1e6, 2), "executed_int_ops_per_launch": executed,
+            "peak_source": "measured: mh_int_peak LOP3 rate on this GPU (popc rate in int_peaks)",
+            "int_peaks": {k: round(v, 3) for k, v in peaks_int.items()},
+            "work_equiv": {"ops_per_launch": round(sum(o[0] for o in ops) / launches),
+                           "achieved": round(wequiv, 4), "work_equiv_frac": round(wequiv / peak, 4)},
+            "ncu": ncu}
 
 
-def cpu_baseline_sample(c, full_visited_total, seconds_target=10.0):
-    """Oracle P-DFS on the first rounds of the workload, scaled to solves/s by visited nodes."""
+def cpu_threads():
     import oracle
-    rounds = 1
+    return oracle.default_threads()
+
+
+def cpu_baseline_measure(c):
+    """CPU baselines on this host, measured (no extrapolation): the threaded CPU
+    P-DFS (oracle/pdfs_mt.c, every host core, the paper's master-worker scheme on
+    threads) solving the whole workload once; the single-threaded oracle P-DFS on
+    its first two greedy rounds; the brute-force oracle on the whole c1 solve."""
+    import oracle
+    import synth
+    th = cpu_threads()
     t0 = time.perf_counter()
-    sol = oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA, max_rounds=rounds)
+    sol = oracle.pdfs_mt(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA, threads=th)
     dt = time.perf_counter() - t0
-    while dt < seconds_target / 3 and rounds < 8:
-        rounds *= 2
-        t0 = time.perf_counter()
-        sol = oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA, max_rounds=rounds)
-        dt = time.perf_counter() - t0
-    vis = int(sol.visited.sum())
-    frac = vis / full_visited_total
-    solves_per_s = frac / dt
-    return {"value": solves_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle P-DFS (single-threaded C) on the first {rounds} greedy rounds of {WORKLOAD} "
-                      f"({vis} of {full_visited_total} visited nodes of the solve, {100 * frac:.1f}%), "
-                      f"{dt:.2f} s, scaled to whole solves by visited nodes"}, dt
+    t0 = time.perf_counter()
+    one = oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA, max_rounds=2)
+    dt1 = time.perf_counter() - t0
+    c1 = synth.generate(synth.c1())
+    t0 = time.perf_counter()
+    bf = oracle.bruteforce(c1.bitmaps, c1.G, c1.Nt, c1.Nn, 2, ALPHA)
+    dtb = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": th, "kind": "oracle",
+            "sample": f"threaded CPU P-DFS (oracle/pdfs_mt.c, {th} threads) solving the whole {WORKLOAD} workload "
+                      f"once ({sol.k} selections, {sol.visited.shape[0]} rounds): {dt:.2f} s",
+            "single_thread_oracle": {"rounds": int(one.visited.shape[0]), "seconds": round(dt1, 3),
+                                     "visited_nodes": int(one.visited.sum()), "cores": 1,
+                                     "what": f"oracle P-DFS (plain C), first 2 greedy rounds of {WORKLOAD}"},
+            "bruteforce_c1": {"seconds": round(dtb, 3), "selections": bf.k, "cores": 1,
+                              "what": "brute-force oracle (every 2-subset, no pruning), whole c1 solve"}}
 
 
 def run_reference(args):
+    """Reference arm: the CPU P-DFS of oracle/ (threaded over every host core) solving
+    the whole c2 workload once per step; ms_per_step is what each step took."""
     rank, world, _ = _dist_env()
     if world > 1 and rank != 0:
         return 0
+    import oracle
     import synth
     c = synth.generate(synth.c2())
-    total = _full_visited_total(c)
-    if total is None:  # stored oracle result does not match this machine's cohort: count once
-        import oracle
-        total = int(oracle.pdfs(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA).visited.sum())
-    vals = []
+    th = cpu_threads()
+    times = []
+    k = rounds = 0
     for i in range(args.warmup + args.steps):
-        cb, dt = cpu_baseline_sample(c, total, seconds_target=3.0)
+        t0 = time.perf_counter()
+        sol = oracle.pdfs_mt(c.bitmaps, c.G, c.Nt, c.Nn, H, ALPHA, threads=th)
+        dt = time.perf_counter() - t0
+        k, rounds = sol.k, int(sol.visited.shape[0])
         if i >= args.warmup:
-            vals.append((cb, dt))
-    value = statistics.median(v[0]["value"] for v in vals)
-    ms = 1e3 / value
+            times.append(dt)
+    total = sum(times)
+    value = len(times) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "c2: h=3, G=5000, Nt=500, Nn=300, seed 1, alpha=1/10"},
-            "cpu_baseline": vals[-1][0], "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                                                  "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle",
+                             "sample": f"threaded CPU P-DFS (oracle/pdfs_mt.c, {th} threads), one whole c2 solve "
+                                       f"per step ({k} selections, {rounds} rounds)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
-
-
-def _full_visited_total(c):
-    """Visited nodes of the whole c2 solve (from the stored oracle result when it matches)."""
-    import hashlib
-    path = os.path.join(ROOT, "tests", "golden", "c2_pdfs.json")
-    try:
-        g = json.load(open(path))
-        if g["cohort_sha256"] == hashlib.sha256(c.bitmaps.tobytes()).hexdigest():
-            return int(sum(sum(r) for r in g["visited"]))
-    except (OSError, ValueError, KeyError):
-        pass
-    return None
 
 
 def run_ours(args):
@@ -338,15 +339,11 @@ def run_ours(args):
     H.close()
 
     if rank == 0:
-        peaks, src = _peaks()
         r0 = results[-1]
         scored = int((r0.visited[:, -1] - r0.pruned[:, -1]).sum())
         vis_leaves = int(r0.visited[:, -1].sum())
         pruned_prefixes = int(r0.pruned[:, :-1].sum())
-        cb = None
-        total_vis = _full_visited_total(c) or int(r0.visited.sum())
-        if world == 1:
-            cb, _ = cpu_baseline_sample(c, total_vis)
+        cb = cpu_baseline_measure(c) if world == 1 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -364,7 +361,7 @@ def run_ours(args):
                       "combos_scored_per_s": scored * value / world, "leaves_tested_per_s": vis_leaves * value / world,
                       "prefixes_pruned_per_s": pruned_prefixes * value / world,
                       "visited_fraction": vis_leaves / (r0.rounds * _comb(c.G, H_HITS))},
-            "roofline": solve_roofline(results, c.Nt, c.Nn, peaks, src),
+            "roofline": solve_roofline(results, c.Nt, c.Nn, int_peaks()),
             "cpu_baseline": cb,
             "e2e": {"value": world / (e2e_max / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(c.bitmaps.nbytes), "d2h_bytes_per_step": int(d2h)},
@@ -372,6 +369,9 @@ def run_ours(args):
             "clocks": clocks,
         }
         if world == 1 and not args.no_extras:
+            # the other plain single-cohort configurations (c1: h=2, G=1,000; c3: h=4,
+            # G=19,000, 128-bit rows): CUDA events on the solving stream, L2 flushed
+            line["plain_configs"] = {"c1": plain_config("c1", 5), "c3": plain_config("c3", 3)}
             # the other two parts of the metric, after the timed c2 steps: batched
             # (16 uneven cohorts in one launch vs one after another) and served
             # (request trace: continuous batching vs a plain loop)
@@ -384,6 +384,41 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def plain_config(name, runs):
+    """One plain single-cohort configuration: the median of `runs` solves (after one
+    warm-up) of its synthetic cohort, timed with CUDA events, L2 flushed between."""
+    import torch
+    import synth
+    from paper_2603_16721_gb300 import mh
+    spec = synth.COHORTS[name]()
+    c = synth.generate(spec)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms, kms = [], []
+    with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as Hc:
+        mh.mh_set_stream(Hc, stream.cuda_stream)
+        r = mh.mh_solve(Hc, spec.h, ALPHA)
+        for _ in range(runs):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            r = mh.mh_solve(Hc, spec.h, ALPHA)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            kms.append(r.kernel_ms)
+    t = statistics.median(ms) / 1e3
+    scored = int((r.visited[:, -1] - r.pruned[:, -1]).sum())
+    return {"workload": f"{name}: h={spec.h}, G={c.G}, Nt={c.Nt}, Nn={c.Nn}, seed {spec.seed}, alpha=1/10",
+            "ms_per_solve": round(1e3 * t, 3), "kernel_ms_per_solve": round(statistics.median(kms), 3),
+            "solves_per_s": round(1.0 / t, 3), "rounds": r.rounds, "selected": r.k,
+            "combos_scored_per_s": scored / t, "leaves_tested_per_s": int(r.visited[:, -1].sum()) / t,
+            "prefixes_pruned_per_s": int(r.pruned[:, :-1].sum()) / t,
+            "visited_fraction": int(r.visited[:, -1].sum()) / (r.rounds * _comb(c.G, spec.h)), "runs": runs}
 
 
 def _comb(n, k):
@@ -460,8 +495,10 @@ def served_comparison(args):
     """Served workload: a trace of requests (c3-law cohorts, Poisson arrivals at 5/s,
     h from {2: .3, 3: .5, 4: .2}) replayed in real time against (i) the served
     runtime (continuous batching) and (ii) a plain FIFO loop of one solve (one
-    persistent launch) per request; latency = arrival to result.  Then the same
-    requests all at once (saturated), for throughput at full load."""
+    persistent launch) per request; latency = arrival to result.  The same trace is
+    replayed again with its arrival times compressed so that the offered load is
+    0.8x the plain loop's measured capacity, and finally every request arrives at
+    once (saturated): each of the three is run on both paths."""
     import threading
     import numpy as np
     import torch
@@ -485,64 +522,72 @@ def served_comparison(args):
         xs = sorted(xs)
         return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
 
-    # (ii) plain FIFO loop
-    plain_res, plain_lat, service = [], [], []
-    t0 = time.perf_counter()
-    for i, (c, sp) in enumerate(zip(cohorts, specs)):
-        now = time.perf_counter() - t0
-        if now < arrivals[i]:
-            time.sleep(arrivals[i] - now)
-        ts = time.perf_counter()
-        with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
-            plain_res.append(mh.mh_solve(H, sp.h))
-        te = time.perf_counter()
-        service.append(te - ts)
-        plain_lat.append(te - t0 - arrivals[i])
-    plain_span = time.perf_counter() - t0
+    def plain(arr):
+        """Plain FIFO loop: returns results, latencies, service times, span."""
+        res, lat, service = [], [], []
+        t0 = time.perf_counter()
+        for i, (c, sp) in enumerate(zip(cohorts, specs)):
+            now = time.perf_counter() - t0
+            if now < arr[i]:
+                time.sleep(arr[i] - now)
+            ts = time.perf_counter()
+            with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
+                res.append(mh.mh_solve(H, sp.h))
+            te = time.perf_counter()
+            service.append(te - ts)
+            lat.append(te - t0 - arr[i])
+        return res, lat, service, time.perf_counter() - t0
 
-    # (i) served: requests submitted at their arrival times
-    with mh.Server(slots=args.slots, large_slots=args.large_slots) as S:
+    def served(S, arr):
+        """Requests submitted at their arrival times; returns results, latencies, span."""
         tickets = [None] * n
         t0 = time.perf_counter()
 
         def submitter():
             for i, (c, sp) in enumerate(zip(cohorts, specs)):
                 now = time.perf_counter() - t0
-                if now < arrivals[i]:
-                    time.sleep(arrivals[i] - now)
+                if now < arr[i]:
+                    time.sleep(arr[i] - now)
                 tickets[i] = S.submit(c.bitmaps, c.G, c.Nt, c.Nn, sp.h)
 
         th = threading.Thread(target=submitter)
         th.start()
         th.join()
-        served_res = [S.wait(t) for t in tickets]
-        served_span = time.perf_counter() - t0
-        stats = S.stats()
-        # saturated: every request submitted at once (throughput at full load; the
-        # plain loop's is 1 / mean service time)
-        t0 = time.perf_counter()
-        burst_tickets = [S.submit(c.bitmaps, c.G, c.Nt, c.Nn, sp.h) for c, sp in zip(cohorts, specs)]
-        burst_res = [S.wait(t) for t in burst_tickets]
-        burst_span = time.perf_counter() - t0
-    served_lat = [r.solve_ms / 1e3 for r in served_res]
-    same = all(a.records() == b.records() for a, b in zip(plain_res, served_res))
-    same = same and all(a.records() == b.records() for a, b in zip(plain_res, burst_res))
+        res = [S.wait(t) for t in tickets]
+        return res, [r.solve_ms / 1e3 for r in res], time.perf_counter() - t0
+
+    def summary(lat, span):
+        return {"solves_per_s": n / span, "p50_ms": 1e3 * pct(lat, 0.50), "p99_ms": 1e3 * pct(lat, 0.99)}
+
+    plain_res, plain_lat, service, plain_span = plain(arrivals)
     mean_service = sum(service) / n
-    plain_done = np.cumsum(service)  # the plain loop fed all requests at once
+    capacity = 1.0 / mean_service
+    scale = (n / max(arrivals[-1], 1e-9)) / (0.8 * capacity)  # 5 req/s -> 0.8x capacity
+    fast = arrivals * scale
+    zero = np.zeros(n)
+    pl_fast_res, pl_fast_lat, _, pl_fast_span = plain(fast)
+    pl_burst_res, pl_burst_lat, _, pl_burst_span = plain(zero)
+    with mh.Server(slots=args.slots, large_slots=args.large_slots) as S:
+        served_res, served_lat, served_span = served(S, arrivals)
+        fast_res, fast_lat, fast_span = served(S, fast)
+        burst_res, burst_lat, burst_span = served(S, zero)
+        stats = S.stats()
+    same = all(a.records() == b.records() for a, b in zip(plain_res, served_res))
+    for other in (fast_res, burst_res, pl_fast_res, pl_burst_res):
+        same = same and all(a.records() == b.records() for a, b in zip(plain_res, other))
     return ({
         "metric": "served_wsc_solves_per_s", "value": n / served_span, "unit": "solves/s",
         "p50_ms": 1e3 * pct(served_lat, 0.50), "p99_ms": 1e3 * pct(served_lat, 0.99),
         "plain": {"value": n / plain_span, "p50_ms": 1e3 * pct(plain_lat, 0.50), "p99_ms": 1e3 * pct(plain_lat, 0.99),
-                  "mean_service_ms": 1e3 * mean_service, "capacity_solves_per_s": 1.0 / mean_service},
-        "saturated": {"served_solves_per_s": n / burst_span, "plain_solves_per_s": 1.0 / mean_service,
-                      "served_p50_ms": 1e3 * pct([r.solve_ms / 1e3 for r in burst_res], 0.50),
-                      "served_p99_ms": 1e3 * pct([r.solve_ms / 1e3 for r in burst_res], 0.99),
-                      "plain_p50_ms": 1e3 * pct(list(plain_done), 0.50),
-                      "plain_p99_ms": 1e3 * pct(list(plain_done), 0.99)},
+                  "mean_service_ms": 1e3 * mean_service, "capacity_solves_per_s": capacity},
+        "load_0p8": {"offered_req_per_s": n / max(fast[-1], 1e-9), "served": summary(fast_lat, fast_span),
+                     "plain": summary(pl_fast_lat, pl_fast_span)},
+        "saturated": {"served": summary(burst_lat, burst_span), "plain": summary(pl_burst_lat, pl_burst_span)},
         "offered_load_req_per_s": n / max(arrivals[-1], 1e-9), "requests": n, "slots": args.slots,
         "identical_to_plain": same, "server_launches": stats["launches"],
         "config": {"workload": f"served: first {n} of 200 requests, c3-law cohorts (G=19000, Nt=800, Nn=400), "
-                               "seeds 1000-1199, Poisson 5 req/s, h from {2:.3,3:.5,4:.2}, trace seed 5000"},
+                               "seeds 1000-1199, Poisson 5 req/s, h from {2:.3,3:.5,4:.2}, trace seed 5000; "
+                               "replayed as traced, compressed to 0.8x the plain loop's capacity, and all at once"},
     })
 
 

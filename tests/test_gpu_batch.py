@@ -67,6 +67,27 @@ def test_batch_of_c2_law_cohorts(mh, tmp_path, monkeypatch):
         H.close()
 
 
+def test_full_size_batch16_members(mh, tmp_path, monkeypatch):
+    """The batched workload at full size in one call: every member equals its solo
+    solve, and the two members the CPU finishes in seconds (G = 2,050 and 4,098,
+    h = 3) equal the threaded CPU P-DFS (checked against the oracle on the CPU)."""
+    monkeypatch.setenv("MH_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    specs = synth.batch16()
+    cohorts = [synth.generate(sp) for sp in specs]
+    handles = [mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) for c in cohorts]
+    try:
+        hs = [sp.h for sp in specs]
+        got = mh.mh_solve_batch(handles, hs)
+        for H, h, g in zip(handles, hs, got):
+            _same(g, mh.mh_solve(H, h))
+        for i in (3, 1):
+            c = cohorts[i]
+            _same(got[i], oracle.pdfs_mt(c.bitmaps, c.G, c.Nt, c.Nn, hs[i]))
+    finally:
+        for H in handles:
+            H.close()
+
+
 def test_batch_rejects_bad_splits(mh):
     bm = np.zeros((4, 2), dtype=np.uint64)
     a = mh.mh_create(bm, 4, 64, 64)

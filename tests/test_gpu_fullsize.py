@@ -9,12 +9,25 @@ one instead, with the oracle's counting routines:
   the sparsity order (§III-C) and the loop bounds of Algorithm 2;
 * the final cover equals the tumors with at least h mutated genes, no combination
   repeats (the closing invariants of Algorithm 1).
+
+And element by element against stored oracle results (tests/golden/, written by
+make_oracle_goldens.py from the oracle alone):
+
+* c3_r2: the first two greedy rounds of this workload, every selection and every
+  per-depth visited / pruned counter (the oracle needs hours for them);
+* c3w_pdfs: the same law at the same sample width (14 tumor words, 7 normal
+  words) with G = 5,000, the whole solve (485 selections), every counter.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from golden_io import GOLDEN
 from test_gpu_parity import _replay_checks
 
 pytestmark = pytest.mark.gpu
@@ -104,3 +117,52 @@ def test_c3_sampled_optimality(c3_solved):
             assert a >= 1
             s = ALPHA[0] * int(a) + ALPHA[1] * (c.Nn - int(b))
             assert s < s0 or (s == s0 and tuple(genes) <= tuple(int(x) for x in t))
+
+
+def _stored(name, spec):
+    """Cohort and stored oracle result, or None when this machine's generator drew
+    a different cohort (the hash does not match)."""
+    path = os.path.join(GOLDEN, f"{name}.json")
+    c = synth.generate(spec)
+    if not os.path.exists(path):
+        return c, None
+    g = json.load(open(path))
+    if g["cohort_sha256"] != hashlib.sha256(c.bitmaps.tobytes()).hexdigest():
+        return c, None
+    return c, g
+
+
+def _same_as_stored(got, g, rounds=None):
+    recs = [(tuple(x[0]), x[1], x[2]) for x in g["records"]]
+    vis = np.array(g["visited"], dtype=np.uint64)
+    pru = np.array(g["pruned"], dtype=np.uint64)
+    if rounds is not None:
+        recs, vis, pru = recs[:rounds], vis[:rounds], pru[:rounds]
+    assert got.records() == recs
+    assert got.visited.shape == vis.shape
+    assert np.array_equal(got.visited, vis) and np.array_equal(got.pruned, pru)
+
+
+def test_c3_first_rounds_match_stored_oracle(mh):
+    c, g = _stored("c3_r2", synth.c3())
+    if g is None:
+        pytest.skip("no stored oracle result for this machine's c3 cohort (the oracle needs hours)")
+    R = len(g["visited"])
+    for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
+        with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
+            got = mh.mh_solve_ex(H, 4, ALPHA, max_rounds=R, mode=mode)
+        _same_as_stored(got, g, R)
+
+
+def test_c3w_whole_solve_matches_stored_oracle(mh):
+    spec = synth.c3_law(5000, 800, 400, 3)
+    c, g = _stored("c3w_pdfs", spec)
+    if g is None:  # recompute with the threaded CPU P-DFS (itself checked against the oracle)
+        sol = oracle.pdfs_mt(c.bitmaps, c.G, c.Nt, c.Nn, 4, ALPHA)
+        g = {"records": [[list(t), a, b] for t, a, b in sol.records()],
+             "visited": sol.visited.astype(int).tolist(), "pruned": sol.pruned.astype(int).tolist()}
+    for mode in (mh.MH_MODE_PERSISTENT, mh.MH_MODE_LAUNCHES):
+        with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as H:
+            got = mh.mh_solve_ex(H, 4, ALPHA, mode=mode)
+        assert got.mode == mode
+        _same_as_stored(got, g)
