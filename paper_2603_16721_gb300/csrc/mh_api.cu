@@ -170,9 +170,13 @@ struct mh_handle {
     int *dState = nullptr, *dRes = nullptr;
     Key *dSlots = nullptr, *dCand = nullptr, *dChamp = nullptr;
     int *dChampOk = nullptr;
+    u64 *dSsum = nullptr;                 // per-sample sums of the counters (Nt x 2h)
     u32 *dCounts = nullptr;               // frontier sizes, one per depth, then work-distribution counters
     Rec *dF[kMaxH] = {};               // frontier of depth l at index l
     u32 cap[kMaxH] = {};
+    unsigned char *dSide[kMaxH] = {};     // per record slot of depth l: sig, lb, lc (incremental rounds)
+    u32 *dGK = nullptr;                   // per gene: uncovered tumors carrying it (incremental rounds)
+    u64 *dCov = nullptr;                  // tumors covered by the last round's winner
     int *hState = nullptr;                // pinned: state + frontier counts
     GridSync *dSync = nullptr;            // barrier of the persistent solve
     int coop = 0, pgrid = 0;              // cooperative launch supported; persistent grid size
@@ -187,10 +191,15 @@ struct mh_handle {
         for (int i = 0; i < 2; ++i)
             if (evk[i]) cudaEventDestroy(evk[i]);
         for (void *p : {(void *)dStore, (void *)dU,
-                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk,
+                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk, (void *)dSsum,
                         (void *)dCounts, (void *)dSync})
             dfree(p, stream);
-        for (int l = 0; l < kMaxH; ++l) dfree(dF[l], stream);
+        for (int l = 0; l < kMaxH; ++l) {
+            dfree(dF[l], stream);
+            dfree(dSide[l], stream);
+        }
+        dfree(dGK, stream);
+        dfree(dCov, stream);
         pinned_state_put(hState);
     }
 };
@@ -291,6 +300,31 @@ int build_store(mh_handle *H, const uint64_t *bm)
         for (u32 k = SO[sm]; k < SO[sm + 1]; ++k) SLo[k] = orig[SL[k]];
         std::sort(SLo.begin() + SO[sm], SLo.begin() + SO[sm + 1]);
     }
+    // static depth-1 record of every gene (search order): all its tumors and
+    // normals, listed when few; a round filters the listed tumors by U
+    std::vector<Rec> GR((size_t)G);
+    std::vector<u64> GS((size_t)G, 0);
+    for (int i = 0; i < G; ++i) {
+        Rec &r = GR[i];
+        memset(&r, 0, sizeof r);
+        r.p.w0 = (u64)i;
+        int ky = 0, kn = 0;
+        for (int w = 0; w < Wt; ++w) ky += __builtin_popcountll(T[(size_t)i * c.WTp + w]);
+        for (int w = 0; w < Wn; ++w) kn += __builtin_popcountll(N[(size_t)i * c.WNp + w]);
+        r.ky = (u16)std::min(ky, 0xffff);
+        r.kn = (u16)std::min(kn, 0xffff);
+        if (ky <= kListT) {
+            int k = 0;
+            for (int w = 0; w < Wt; ++w)
+                for (u64 x = T[(size_t)i * c.WTp + w]; x; x &= x - 1) r.ids[k++] = (u16)(w * 64 + __builtin_ctzll(x));
+        }
+        if (kn <= kListN) {
+            int k = kListT;
+            for (int w = 0; w < Wn; ++w)
+                for (u64 x = N[(size_t)i * c.WNp + w]; x; x &= x - 1) r.ids[k++] = (u16)(w * 64 + __builtin_ctzll(x));
+        }
+        for (int w = 0; w < Wt; ++w) GS[i] |= T[(size_t)i * c.WTp + w];  // bit s & 63 of every tumor s
+    }
     int rc;
     cudaStream_t st = H->stream;
     // the whole store in one device block, filled by one copy (256-byte aligned pieces)
@@ -305,6 +339,7 @@ int build_store(mh_handle *H, const uint64_t *bm)
     const size_t oCC = piece(CC.size() * sizeof(u16)), oSL = piece(SL.size() * sizeof(u16));
     const size_t oSLo = piece(SLo.size() * sizeof(u16)), oSO = piece(SO.size() * sizeof(u32));
     const size_t oOrig = piece((size_t)G * sizeof(u16)), oInv = piece((size_t)G * sizeof(u32));
+    const size_t oGR = piece((size_t)G * sizeof(Rec)), oGS = piece((size_t)G * sizeof(u64));
     std::vector<unsigned char> host(off, 0);
     auto put = [&](size_t o, const void *src, size_t bytes) {
         if (bytes) memcpy(host.data() + o, src, bytes);
@@ -319,6 +354,8 @@ int build_store(mh_handle *H, const uint64_t *bm)
     put(oSO, SO.data(), SO.size() * sizeof(u32));
     put(oOrig, orig.data(), (size_t)G * sizeof(u16));
     put(oInv, inv.data(), (size_t)G * sizeof(u32));
+    put(oGR, GR.data(), (size_t)G * sizeof(Rec));
+    put(oGS, GS.data(), (size_t)G * sizeof(u64));
     if ((rc = dalloc(&H->dStore, off, &H->device_bytes, H->dev, st))) return rc;
     MH_CUDA(cudaMemcpyAsync(H->dStore, host.data(), off, cudaMemcpyHostToDevice, st));
     H->dT = (u64 *)(H->dStore + oT);
@@ -336,6 +373,8 @@ int build_store(mh_handle *H, const uint64_t *bm)
     c.SL = H->dSL;
     c.SO = H->dSO;
     c.SLo = H->dSLo;
+    c.GR = (const Rec *)(H->dStore + oGR);
+    c.GS = (const u64 *)(H->dStore + oGS);
     MH_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
     return MH_OK;
 }
@@ -375,20 +414,25 @@ int ensure_frontier(mh_handle *H, int l, u64 n, bool exact = false)
     if (mn && *mn && atoll(mn) > 0) least = (u64)atoll(mn);
     u64 want = std::max<u64>(exact ? n : n + n / 4, least);
     if (want > 0xffffffffull / kShards) want = 0xffffffffull / kShards;
-    const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)sizeof(Rec);
-    const int64_t new_bytes = (int64_t)want * kShards * (int64_t)sizeof(Rec);
+    const int64_t old_bytes = (int64_t)H->cap[l] * kShards * (int64_t)kSlotBytes;
+    const int64_t new_bytes = (int64_t)want * kShards * (int64_t)kSlotBytes;
     const char *fixed = getenv("MH_FRONTIER_BUDGET_MB");
     const bool over = (fixed && *fixed) ? (size_t)(H->frontier_bytes - old_bytes + new_bytes) > frontier_budget()
                                         : (size_t)(new_bytes - old_bytes) > frontier_budget(H->dev);
     if (over || n > want)
         return fail(MH_ENOMEM, "depth-%d frontier needs %llu records per shard (%.1f GB), above the frontier budget",
-                    l, (unsigned long long)n, (double)n * kShards * sizeof(Rec) / 1e9);
+                    l, (unsigned long long)n, (double)n * kShards * kSlotBytes / 1e9);
     dfree(H->dF[l], H->stream);  // stream-ordered: after the kernels that used it
+    dfree(H->dSide[l], H->stream);
     H->dF[l] = nullptr;
+    H->dSide[l] = nullptr;
     H->frontier_bytes -= old_bytes;
     H->device_bytes -= old_bytes;
     H->cap[l] = 0;
     int rc = dalloc(&H->dF[l], (size_t)want * kShards, &H->device_bytes, H->dev, H->stream);
+    if (rc) return rc;
+    rc = dalloc(&H->dSide[l], (size_t)want * kShards * (kSlotBytes - sizeof(Rec)), &H->device_bytes, H->dev,
+                H->stream);
     if (rc) return rc;
     H->cap[l] = (u32)want;
     H->frontier_bytes += new_bytes;
@@ -428,6 +472,9 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dChamp, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dChampOk, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dSsum, (size_t)std::max(H->Nt, 1) * 2 * kMaxH, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dGK, (size_t)H->G, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCov, (size_t)H->c.WTp, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
         if (!(H->hState = pinned_state_get())) return fail(MH_ENOMEM, "pinned host allocation failed");
@@ -543,6 +590,9 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     s->cand = H->dCand;
     s->champ = H->dChamp;
     s->champ_ok = H->dChampOk;
+    s->ssum = H->dSsum;
+    s->gk = H->dGK;
+    s->cov = H->dCov;
     s->work = H->dWork;
     s->best_hint = H->dWork + kWorkCount;
     *max_rounds = H->Nt + 1;
@@ -557,6 +607,12 @@ Frontiers frontiers_of(const mh_handle *H)
     for (int l = 0; l < kMaxH; ++l) {
         f.F[l] = H->dF[l];
         f.cap[l] = H->cap[l];
+        // side arrays of the slots: lb (Key), then sig and lc (u64)
+        const size_t n = (size_t)H->cap[l] * kShards;
+        unsigned char *side = H->dSide[l];
+        f.lb[l] = side ? (Key *)side : nullptr;
+        f.sig[l] = side ? (u64 *)(side + n * sizeof(Key)) : nullptr;
+        f.lc[l] = side ? (u64 *)(side + n * (sizeof(Key) + sizeof(u64))) : nullptr;
     }
     return f;
 }
@@ -781,11 +837,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
         // One cooperative launch runs every round; it returns early only when a
         // frontier overflowed (grown here, then the round is run again).
         while (!done) {
-            Frontiers f;
-            for (int l = 0; l < kMaxH; ++l) {
-                f.F[l] = H->dF[l];
-                f.cap[l] = H->cap[l];
-            }
+            const Frontiers f = frontiers_of(H);
             MH_CUDA(cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st));
             MH_CUDA(cudaEventRecord(H->evk[0], st));
             MH_CUDA(launch_solve_persistent(c, s, f, H->dSync, counts, pgrid, large, st));
@@ -826,10 +878,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
     s.champ = nullptr;  // the per-sample champions are computed by the persistent kernels only
     s.champ_ok = nullptr;
     while (!done) {
-        for (int l = 0; l < kMaxH; ++l) {
-            fl.F[l] = H->dF[l];
-            fl.cap[l] = H->cap[l];
-        }
+        fl = frontiers_of(H);
         const size_t first_ev = round_ev.size();
         const int n = std::min(batch, max_rounds - rounds_done);
         for (int b = 0; b < n; ++b) {
@@ -1382,8 +1431,8 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, dou
         for (int w = 0; w < Wt; ++w)
             for (uint64_t x = bm[(size_t)g * (Wt + Wn) + w]; x; x &= x - 1) ++m[w * 64 + __builtin_ctzll(x)];
     const int64_t gw = ((G + 63) / 64 + 2);
-    int64_t bytes = (int64_t)G * (Wt + Wn + 4) * 8 + (int64_t)(Nt + Nn) * gw * 8;
-    bytes += (int64_t)((G + kShards - 1) / kShards + 64) * kShards * (int64_t)sizeof(Rec);
+    int64_t bytes = (int64_t)G * (Wt + Wn + 4) * 8 + (int64_t)(Nt + Nn) * gw * 8 + (int64_t)G * (sizeof(Rec) + 12);
+    bytes += (int64_t)((G + kShards - 1) / kShards + 64) * kShards * (int64_t)kSlotBytes;
     // sets[d]: the d-gene sets sharing a tumor, summed over tumors
     std::vector<double> sets(std::max(h, 1), 0.0);
     for (int x : m) {
@@ -1394,8 +1443,8 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, dou
         }
     }
     for (int l = 2; l < h; ++l)
-        bytes += (int64_t)(frontier_records_estimate(sets[l], l) * 1.25 * (double)sizeof(Rec)) +
-                 (int64_t)(2048 * kShards) * (int64_t)sizeof(Rec);
+        bytes += (int64_t)(frontier_records_estimate(sets[l], l) * 1.25 * (double)kSlotBytes) +
+                 (int64_t)(2048 * kShards) * (int64_t)kSlotBytes;
     *work = (double)G + sets[h - 1];  // as work_estimate(H, h - 1)
     return bytes + (64 << 20);
 }

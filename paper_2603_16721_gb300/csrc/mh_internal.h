@@ -30,6 +30,8 @@ constexpr int kShardStride = 32;
 constexpr int kCountWords = kMaxH * kShards * kShardStride;
 __host__ __device__ constexpr int shard_slot(int level, int shard) { return (level * kShards + shard) * kShardStride; }
 
+struct Rec;
+
 // Device view of one cohort, genes in search order (most sparse first, §III-C).
 struct Cohort {
     int G, Nt, Nn;
@@ -52,6 +54,13 @@ struct Cohort {
     const u32 *SO;
     // The same genes as original row indices, ascending: SLo[SO[s] .. SO[s + 1]).
     const u16 *SLo;
+    // G static depth-1 records, one per gene in search order, built at create time
+    // over ALL tumors: ky / kn = the gene's tumor / normal mutation counts, the
+    // samples listed when few (see Rec).  A round filters the listed tumors by U.
+    // nullptr: depth-1 records are built from the rows.
+    const Rec *GR;
+    // G static tumor signatures: OR of 1 << (s & 63) over the tumors of each gene.
+    const u64 *GS;
 };
 
 // Best candidate of a search, compared as (score desc, original tuple asc).
@@ -103,6 +112,18 @@ struct Solve {
     // genes), 0 if its search exceeded its budget.  nullptr: not computed.
     Key *champ;
     int *champ_ok;
+    // Per tumor sample s (Nt x 2h entries): ssum[s * 2h + l - 1] = A_l(s), the
+    // number of in-bound depth-l nodes (prefixes whose genes are all mutated in s,
+    // each within its depth's loop bound), and ssum[s * 2h + h + l - 1] = V_l(s),
+    // the children the depth-(l-1) ones among them have (their loop ranges summed).
+    // Summed over the uncovered tumors they give a round's counters up to a
+    // correction from the nodes shared by two or more uncovered tumors (see
+    // mh_kernels.cu).  nullptr: the counters are counted node by node.
+    u64 *ssum;
+    // Incremental rounds: gk[g] = uncovered tumors carrying gene g (G entries);
+    // cov = the tumors the previous round's winner covered (WTp words).
+    u32 *gk;
+    u64 *cov;
 };
 
 constexpr int kCandidates = 32;
@@ -125,10 +146,20 @@ enum {
 };
 
 // Frontier buffers (depth l at index l): kShards regions of cap[l] records each.
+// Incremental rounds keep, per record slot of every depth: sig = the OR of
+// 1 << (s & 63) over the record's tumor samples (0: no longer shared by two
+// uncovered tumors, ~0: samples not listed), and for the leaf parents (depth h-1)
+// lb = the best key among the record's leaves with TP >= 2 and lc = the sum of
+// TP - 1 over them.  nullptr where not allocated.
 struct Frontiers {
     Rec *F[kMaxH];
     u32 cap[kMaxH];
+    u64 *sig[kMaxH];
+    Key *lb[kMaxH];
+    u64 *lc[kMaxH];
 };
+// Device bytes of one frontier record slot with its incremental-round data.
+constexpr size_t kSlotBytes = sizeof(Rec) + 2 * sizeof(u64) + sizeof(Key);
 
 // Grid-wide barrier state of the persistent solve (zeroed before each launch);
 // flag: a decision taken by the block that releases a barrier (the batch's yield).

@@ -50,14 +50,24 @@ __device__ __forceinline__ Team grid_team() { return Team{(int)blockIdx.x, (int)
 // threshold in s.best_hint.  Persistent solve: depth-1 nodes built from the gene
 // rows and the block's copy of U (Ush), bests stored into the round's slot array,
 // the round's threshold word, diagnostics by round parity.
+// fm: counters by per-sample sums and incremental rounds (see "Counting by
+// per-sample sums" and "Incremental rounds" below): only nodes shared by two or
+// more uncovered tumors are built and searched; build: the expansion builds the
+// kept frontiers of round 0 and adds no counters (the evaluation that follows
+// counts every kept node).
 struct RoundIO {
     const u64 *Ush;
     Key *slots;
     bool overwrite;
     u64 *hint;
     int par;
+    bool fm;
+    bool build;
 };
-__device__ __forceinline__ RoundIO launch_io(const Solve &s) { return RoundIO{nullptr, s.slots, false, s.best_hint, 0}; }
+__device__ __forceinline__ RoundIO launch_io(const Solve &s)
+{
+    return RoundIO{nullptr, s.slots, false, s.best_hint, 0, false, false};
+}
 
 __device__ __forceinline__ int prefix_gene(const Prefix &p, int i)
 {
@@ -438,12 +448,31 @@ struct Batch {
     u64 ns[kMaxWords];              // child masks and their (record, word) of one item per lane
     int cx[33];                     // expansion: exclusive prefix sum of the lanes' child counts
     u16 po[kBatch][kMaxH - 1];      // leaves: ascending original indices of each record's prefix
+    Key rb[kBatch];                 // incremental rounds: per leaf parent, its best leaf (TP >= 2)
+    u64 rc[kBatch];                 //   and the sum of TP - 1 over those leaves
 };
 
 // Depth-1 node of gene g (search order) built from its rows and U: y_1 = U & x_g,
 // n_1 = x^N_g, their sizes and, when few, their samples.  Returns |y_1| > 0.
 __device__ __forceinline__ bool gene_record(const Cohort &c, const u64 *Ush, int g, Rec &r)
 {
+    if (c.GR) {
+        // the gene's static record lists its tumors (all of them) and normals when
+        // few: y_1's samples are the listed tumors still in U
+        const uint4 *a = reinterpret_cast<const uint4 *>(c.GR + g);
+        uint4 *d = reinterpret_cast<uint4 *>(&r);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(Rec) / 16); ++i) d[i] = __ldg(a + i);
+        if (!is_dense(r.ky, r.kn)) {
+            int k = 0;
+            for (int q = 0; q < (int)r.ky; ++q) {
+                const int smp = r.ids[q];
+                if ((Ush[smp >> 6] >> (smp & 63)) & 1ull) r.ids[k++] = (u16)smp;
+            }
+            r.ky = (u16)k;
+            return k > 0;
+        }
+    }
     const u64 *trow = c.T + (size_t)g * c.WTp;
     const u64 *nrow = c.N + (size_t)g * c.WNp;
     int ky = 0, kn = 0;
@@ -530,7 +559,7 @@ __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io,
                                              u32 cap_s, u64 first, u64 stride, int R, u32 count, int L, int hi_bound,
                                              bool all_children, Batch &b, int lane, unsigned &dense_mask,
                                              u64 &visited, int h, int single, const int *champ_ok, u64 &alive_cf,
-                                             u64 *deep, const u16 *orig = nullptr)
+                                             u64 *deep, const u16 *orig = nullptr, bool fm = false)
 {
     const u64 i = first + (u64)lane * stride;
     bool valid = lane < R && i < count;
@@ -543,7 +572,28 @@ __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io,
     } else if (valid) {
         load_rec(&b.r[lane], front_rec(Fin, cap_s, b.soff, (u32)i));
     }
-    if (valid) {
+    if (valid && fm) {
+        // counting by per-sample sums: a node shared by fewer than two uncovered
+        // tumors is accounted for by those sums (nothing to search below it); a
+        // shared one adds (|y| - 1) x (its children) to the depth's correction
+        lo = prefix_gene(b.r[lane].p, L - 1) + 1;
+        hi = hi_bound;
+        ky = b.r[lane].ky;
+        kn = b.r[lane].kn;
+        if (ky < 2) hi = lo - 1;
+        else if (hi >= lo) visited += (u64)(ky - 1) * (u64)(hi - lo + 1);
+        if (orig && hi >= lo) {  // ascending original indices of the prefix genes (leaf keys)
+            for (int q = 0; q < L; ++q) {
+                const u16 v = orig[prefix_gene(b.r[lane].p, q)];
+                int k = q - 1;
+                while (k >= 0 && b.po[lane][k] > v) {
+                    b.po[lane][k + 1] = b.po[lane][k];
+                    --k;
+                }
+                b.po[lane][k + 1] = v;
+            }
+        }
+    } else if (valid) {
         lo = prefix_gene(b.r[lane].p, L - 1) + 1;
         hi = hi_bound;
         ky = b.r[lane].ky;
@@ -638,6 +688,53 @@ __device__ __forceinline__ void sibling_items(const Cohort &c, const Batch &b, i
     }
 #pragma unroll
     for (int u = 0; u < kIlp; ++u) m[u] &= rw[u];
+}
+
+// The same sibling test counting how many samples have each sibling: m = the
+// siblings of at least one sample (non-empty children), m2 = of at least two
+// (children shared by two or more uncovered tumors); with SUM, sum[u] = the
+// number of (sample, sibling) pairs in the range word (the children's sizes
+// summed).
+template <bool SUM>
+__device__ __forceinline__ void sibling_items2(const Cohort &c, const Batch &b, int t0, int total, int &j,
+                                               int (&jj)[kIlp], int (&wi)[kIlp], int (&ky)[kIlp], u64 (&m)[kIlp],
+                                               u64 (&m2)[kIlp], int (&sum)[kIlp])
+{
+    int kmax = 0;
+    u64 rw[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+        const int t = t0 + 32 * u;
+        ky[u] = 0;
+        wi[u] = 0;
+        rw[u] = 0;
+        m[u] = 0;
+        m2[u] = 0;
+        sum[u] = 0;
+        if (t < total) {
+            while (t >= b.off[j + 1]) ++j;
+            wi[u] = (b.lo[j] >> 6) + (t - b.off[j]);
+            ky[u] = b.r[j].ky;
+            rw[u] = range_word(wi[u], b.lo[j], b.hi[j]);
+        }
+        jj[u] = j;
+        kmax = ky[u] > kmax ? ky[u] : kmax;
+    }
+    for (int q = 0; q < kmax; q += 2) {
+        u64 x0[kIlp], x1[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            x0[u] = q < ky[u] ? __ldg(c.CT + (size_t)b.r[jj[u]].ids[q] * c.GW + wi[u]) : 0ull;
+            x1[u] = q + 1 < ky[u] ? __ldg(c.CT + (size_t)b.r[jj[u]].ids[q + 1] * c.GW + wi[u]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const u64 a = x0[u] & rw[u], e = x1[u] & rw[u];
+            m2[u] |= (m[u] & (a | e)) | (a & e);
+            m[u] |= a | e;
+            if (SUM) sum[u] += __popcll(a) + __popcll(e);
+        }
+    }
 }
 
 // Reserves n consecutive slots of the warp's shard for each lane with one atomic
@@ -884,6 +981,7 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int L = level - 1;
     RoundIO io = io_in;
+    const bool fm = io.fm;
     if (level != 2) io.Ush = nullptr;  // depth-1 nodes are built only as the parents of depth 2
     if (threadIdx.x == 0) overflow = 0;
     acc_begin(acc);
@@ -919,18 +1017,26 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
             single = single_sample_mode(c, s, __shfl_sync(kFull, thr, 0));
         }
         u64 alive_cf = 0;
+        if (fm) single = 0;
         const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, hi_bound, all_children, b,
-                                        lane, dense, visited, h, single, s.champ_ok, alive_cf, deep);
+                                        lane, dense, visited, h, single, s.champ_ok, alive_cf, deep, nullptr, fm);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
             int jj[kIlp], wi[kIlp], ky[kIlp];
             u64 m[kIlp], rw[kIlp];
-            sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
+            if (fm) {
+                // children shared by two or more uncovered tumors only
+                u64 m1[kIlp];
+                int sum[kIlp];
+                sibling_items2<false>(c, b, tb + lane, total, j, jj, wi, ky, m1, m, sum);
+            } else {
+                sibling_items(c, b, tb + lane, total, j, jj, wi, ky, m, rw);
 #pragma unroll
-            for (int u = 0; u < kIlp; ++u) {
-                alive += (u64)__popcll(m[u]);
-                if (all_children) m[u] = rw[u];
+                for (int u = 0; u < kIlp; ++u) {
+                    alive += (u64)__popcll(m[u]);
+                    if (all_children) m[u] = rw[u];
+                }
             }
             // spread the children of each item round over all lanes: lane i builds
             // children i, i+32, ... of the warp, whichever lane's item they came from
@@ -963,6 +1069,7 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
                         child.pad[0] = child.pad[1] = child.pad[2] = 0;
                         child_tumors(c, parent, L, (int)(u32)jw, g & 63, child);
                         emit = true;
+                        if (fm) alive += (u64)(child.ky - 1);  // the depth's correction
                         // a child of a listed parent is listed: one sample -> closed form
                         if (single && child.ky == 1 && single_sample_closed(single, s.champ_ok, child.ids[0])) {
                             single_sample_count(c, h, level, g, child.ids[0], leaf_vis, leaf_alive, deep);
@@ -998,11 +1105,16 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
                         kyc += __popcll(yw);
                     }
                 }
-                alive += (u64)(kyc > 0);
                 bool closed = false;
-                if (single && kyc == 1 && g <= hi && single_sample_closed(single, s.champ_ok, smp)) {
-                    single_sample_count(c, h, level, g, smp, leaf_vis, leaf_alive, deep);
-                    closed = true;
+                if (fm) {
+                    closed = kyc < 2;  // single-sample children: in the per-sample sums
+                    if (!closed) alive += (u64)(kyc - 1);
+                } else {
+                    alive += (u64)(kyc > 0);
+                    if (single && kyc == 1 && g <= hi && single_sample_closed(single, s.champ_ok, smp)) {
+                        single_sample_count(c, h, level, g, smp, leaf_vis, leaf_alive, deep);
+                        closed = true;
+                    }
                 }
                 const bool emit = g <= hi && (all_children || kyc > 0) && !closed;
                 const u32 pos = warp_reserve(emit ? 1 : 0, my_count, lane);
@@ -1023,8 +1135,9 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     d1.visited = warp_sum_u64(d1.visited);
     d1.pruned = warp_sum_u64(d1.pruned);
     if (lane == 0) {
+        // fm: the depth's corrections (visited, surviving), finished at the end of the round
         acc_add(acc, 0, visited);
-        acc_add(acc, 1, visited - alive);
+        acc_add(acc, 1, fm ? alive : visited - alive);
         acc_add(acc, 8, d1.visited);
         acc_add(acc, 9, d1.pruned);
         acc_add(deep, 2 * h, leaf_vis);
@@ -1032,11 +1145,13 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     }
     warp_cycles(acc, t0, lane);
     __syncthreads();
-    if (threadIdx.x < 2 && acc[threadIdx.x])
-        atomicAdd(s.cnt + ((size_t)round * s.h + (level - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
-    if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
-        atomicAdd(s.cnt + ((size_t)round * s.h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
-    acc_flush_deep(s, round, acc);
+    if (!io.build) {
+        if (threadIdx.x < 2 && acc[threadIdx.x])
+            atomicAdd(s.cnt + ((size_t)round * s.h + (level - 1)) * 2 + threadIdx.x, acc[threadIdx.x]);
+        if (threadIdx.x >= 8 && threadIdx.x < 10 && acc[threadIdx.x])
+            atomicAdd(s.cnt + ((size_t)round * s.h) * 2 + (threadIdx.x - 8), acc[threadIdx.x]);
+        acc_flush_deep(s, round, acc);
+    }
     warp_cycles_flush(s, acc, 0, io.par);
     return true;
 }
@@ -1566,6 +1681,454 @@ __device__ void block_seed(const Cohort &c, const Solve &s, const Team &t, const
     if ((threadIdx.x & 31) == 0 && best) atomicMax(hint, best);
 }
 
+// ---------------------------------------------------------------------------
+// Counting by per-sample sums.  A depth-l node (an in-bound prefix P) survives iff
+// some uncovered tumor carries all its genes.  Summing over the uncovered tumors s
+// the number A_l(s) of in-bound depth-l prefixes made of s's genes counts every
+// surviving node |y_l(P)| times, so
+//   alive[l]   = sum_{s in U} A_l(s) - sum_{P at depth l, |y_l(P)| >= 2} (|y_l(P)| - 1),
+// and since a depth-l node is visited once per surviving parent, one per gene of
+// the parent's loop range (last(P), hi(l)],
+//   visited[l] = sum_{s in U} V_l(s) - sum_{P at depth l-1, |y(P)| >= 2} (|y(P)| - 1) (hi(l) - last(P)),
+// with V_l(s) those ranges summed over the in-bound depth-(l-1) prefixes of s's
+// genes.  A_l and V_l depend only on s's genes and the loop bounds, so they are
+// computed once per solve; the corrections come from the nodes that two or more
+// uncovered tumors share, the only nodes this mode builds and searches (with the
+// per-sample champions standing for every TP = 1 leaf).  The counters are those
+// of Algorithm 2's loops exactly (as u64, i.e. modulo 2^64 like the counters
+// themselves), and no node of a single uncovered tumor is ever visited.
+
+// A_l(s) and V_l(s) of every tumor s from its genes b_1 < b_2 < ... (search
+// positions): with f_k(b) the in-bound k-prefixes of s's genes ending at b,
+// f_1(b) = [b <= hi(1)], f_k(b) = [b <= hi(k)] * sum_{b' < b} f_{k-1}(b'),
+// A_k = sum_b f_k(b) and V_{k+1} = sum_b f_k(b) (hi(k+1) - b).
+__device__ __noinline__ void phase_sample_sums(const Cohort &c, const Solve &s, const Team &t)
+{
+    const int h = s.h;
+    const int hi0 = c.G - h - 1;  // hi(k) = hi0 + k (0-based, inclusive)
+    for (int smp = t.rank * (int)blockDim.x + (int)threadIdx.x; smp < c.Nt; smp += t.size * (int)blockDim.x) {
+        const u32 off = __ldg(c.SO + smp);
+        const int m = (int)(__ldg(c.SO + smp + 1) - off);
+        u64 S[kMaxH + 1], A[kMaxH + 1], V[kMaxH + 1];
+#pragma unroll
+        for (int k = 0; k <= kMaxH; ++k) S[k] = A[k] = V[k] = 0;
+        for (int i = 0; i < m; ++i) {
+            const int b = (int)__ldg(c.SL + off + i);
+            // descending k: f_k reads the sum of f_{k-1} over the earlier genes
+#pragma unroll
+            for (int k = kMaxH; k >= 1; --k) {
+                if (k > h || b > hi0 + k) continue;
+                const u64 f = k == 1 ? 1ull : S[k - 1];
+                A[k] += f;
+                S[k] += f;
+                if (k < h) V[k + 1] += f * (u64)(hi0 + k + 1 - b);
+            }
+        }
+        u64 *out = s.ssum + (size_t)smp * 2 * h;
+#pragma unroll
+        for (int k = 1; k <= kMaxH; ++k) {
+            if (k > h) break;
+            out[k - 1] = A[k];
+            out[h + k - 1] = V[k];
+        }
+    }
+}
+
+// tot[0 .. 2h) = the per-sample sums over the uncovered tumors (the block's copy Ush).
+__device__ void block_sample_totals(const Cohort &c, const Solve &s, const u64 *Ush, u64 *tot)
+{
+    const int h2 = 2 * s.h, lane = threadIdx.x & 31;
+    if (threadIdx.x < 2 * kMaxH) tot[threadIdx.x] = 0;
+    __syncthreads();
+    for (int k = 0; k < h2; ++k) {
+        u64 v = 0;
+        for (int smp = threadIdx.x; smp < c.Nt; smp += blockDim.x)
+            if ((Ush[smp >> 6] >> (smp & 63)) & 1ull) v += __ldcg(s.ssum + (size_t)smp * h2 + k);
+        v = warp_sum_u64(v);
+        if (lane == 0 && v) atomicAdd(&tot[k], v);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Incremental rounds.  U only shrinks from one round to the next, so the nodes
+// that two or more uncovered tumors share in a later round are among those of
+// round 0, and a node's tumor intersection -- its size, its children's TP and its
+// leaves' scores -- changes only if it holds a tumor that the previous winner
+// covered.  With counting by per-sample sums, round 0 builds the shared
+// ("multi-sample") nodes of every depth below the leaves and keeps them for the
+// whole solve, and evaluates every leaf parent once, caching its best leaf key
+// among its leaves with TP >= 2 and the sum of TP - 1 over them.  A later round
+// scans the kept nodes, brings up to date only those holding a newly covered
+// tumor (re-evaluating the leaf parents among them), reads everything else from
+// the caches, and ends after one grid barrier.  The argmax and every counter are
+// those of a full search of the round.
+
+__device__ __forceinline__ bool in_mask(const u64 *m, int smp) { return (m[smp >> 6] >> (smp & 63)) & 1ull; }
+
+// Signature of a record's tumor samples: OR of 1 << (s & 63) (~0 when not listed).
+__device__ __forceinline__ u64 sample_sig(const Rec &r)
+{
+    if (is_dense(r.ky, r.kn)) return ~0ull;
+    u64 g = 0;
+    for (int q = 0; q < (int)r.ky; ++q) g |= 1ull << (r.ids[q] & 63);
+    return g;
+}
+
+// Slot (shard * cap + offset) of record i of a sharded frontier (soff from front_open).
+__device__ __forceinline__ u32 front_slot(u32 cap_s, const int *soff, u32 i)
+{
+    int lo = 0, hi = kShards - 1;  // last shard with soff <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((u32)soff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return (u32)lo * cap_s + (i - (u32)soff[lo]);
+}
+
+// Uncovered tumors carrying gene g: its static record's listed tumors in U, or
+// the popcount of its row and U.
+__device__ __forceinline__ u32 gene_uncovered(const Cohort &c, const u64 *Ush, int g)
+{
+    const Rec &sr = c.GR[g];
+    const int ky = (int)__ldg(&sr.ky);
+    if (ky <= kListT) {
+        u32 k = 0;
+        for (int q = 0; q < ky; ++q) k += (u32)in_mask(Ush, (int)__ldg(&sr.ids[q]));
+        return k;
+    }
+    const u64 *trow = c.T + (size_t)g * c.WTp;
+    u32 k = 0;
+    for (int w = 0; w < c.Wt; ++w) k += (u32)__popcll(__ldg(trow + w) & Ush[w]);
+    return k;
+}
+
+// Brings a kept record of depth L up to date with U; returns true if its tumor
+// intersection changed (always with force).  Listed samples: the covered ones are
+// dropped.  Unlisted: the intersection is recounted from the rows, and listed
+// once it is small enough.
+__device__ bool refresh_record(const Cohort &c, const u64 *Ush, int L, Rec &r, bool force)
+{
+    if (!is_dense(r.ky, r.kn)) {
+        int k = 0;
+        for (int q = 0; q < (int)r.ky; ++q) {
+            const int smp = r.ids[q];
+            if (in_mask(Ush, smp)) r.ids[k++] = (u16)smp;
+        }
+        const bool changed = k != (int)r.ky;
+        r.ky = (u16)k;
+        return changed || force;
+    }
+    int ky = 0;
+    for (int w = 0; w < c.Wt; ++w) {
+        u64 y = Ush[w];
+        for (int i = 0; i < L && y; ++i) y &= __ldg(c.T + (size_t)prefix_gene(r.p, i) * c.WTp + w);
+        ky += __popcll(y);
+    }
+    if (ky == (int)r.ky && !force) return false;
+    r.ky = sat16(ky);
+    if (!is_dense(ky, r.kn)) {
+        int k = 0;
+        for (int w = 0; w < c.Wt; ++w) {
+            u64 y = Ush[w];
+            for (int i = 0; i < L && y; ++i) y &= __ldg(c.T + (size_t)prefix_gene(r.p, i) * c.WTp + w);
+            for (; y; y &= y - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        }
+        k = kListT;
+        for (int w = 0; w < c.Wn; ++w) {
+            u64 n = ~0ull;
+            for (int i = 0; i < L; ++i) n &= __ldg(c.N + (size_t)prefix_gene(r.p, i) * c.WNp + w);
+            for (; n; n &= n - 1) r.ids[k++] = (u16)(w * 64 + __ffsll((long long)n) - 1);
+        }
+    }
+    return true;
+}
+
+// Merges the per-lane keys of one item step into the records' best keys: items of
+// a step sit on the lanes in record order, so a segmented warp maximum leaves each
+// record's best on its first lane, which merges it into rb.
+__device__ __forceinline__ void merge_item_keys(Batch &b, int jr, Key k, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Key o;
+        o.s = __shfl_down_sync(kFull, k.s, off);
+        o.t0 = __shfl_down_sync(kFull, k.t0, off);
+        o.t1 = __shfl_down_sync(kFull, k.t1, off);
+        o.t2 = __shfl_down_sync(kFull, k.t2, off);
+        const int jo = __shfl_down_sync(kFull, jr, off);
+        if (lane + off < 32 && jo == jr && key_better(o, k)) k = o;
+    }
+    const int jp = __shfl_up_sync(kFull, jr, 1);
+    if (jr >= 0 && (lane == 0 || jp != jr) && k.s != 0 && key_better(k, b.rb[jr])) b.rb[jr] = k;
+    __syncwarp();
+}
+
+// Evaluates the leaf parents b.r[j] (depth L = h - 1) of the lanes with `live`:
+// b.rb[j] = the best key among the record's leaves with TP >= 2 (empty if none),
+// b.rc[j] = the sum of TP - 1 over them.  TP = 1 leaves are left to the
+// champions.  The (record, column word) items are spread over the lanes as in the
+// leaf phase; unlisted records take the row path, the whole warp per record.
+__device__ void leaf_parents_eval(const Cohort &c, const Solve &s, Batch &b, bool live, int L, int lane)
+{
+    int lo = 1, hi = 0, ky = 0, kn = 0;
+    b.rb[lane] = key_empty();
+    b.rc[lane] = 0;
+    if (live) {
+        const Rec &r = b.r[lane];
+        lo = prefix_gene(r.p, L - 1) + 1;
+        hi = c.G - 1;
+        ky = r.ky;
+        kn = r.kn;
+        for (int q = 0; q < L; ++q) {  // ascending original indices of the prefix (leaf keys)
+            const u16 v = c.orig[prefix_gene(r.p, q)];
+            int k = q - 1;
+            while (k >= 0 && b.po[lane][k] > v) {
+                b.po[lane][k + 1] = b.po[lane][k];
+                --k;
+            }
+            b.po[lane][k + 1] = v;
+        }
+    }
+    b.lo[lane] = lo;
+    b.hi[lane] = hi;
+    const bool any = live && hi >= lo;
+    const bool dense = any && is_dense(ky, kn);
+    unsigned dmask = __ballot_sync(kFull, dense);
+    const int nw = (any && !dense) ? (hi >> 6) - (lo >> 6) + 1 : 0;
+    const int incl = warp_incl_scan(nw, lane);
+    b.off[lane] = incl - nw;
+    if (lane == 31) b.off[kBatch] = incl;
+    __syncwarp();
+    const int total = __shfl_sync(kFull, incl, 31);
+    int j = 0;
+    for (int tb = 0; tb < total; tb += 32 * kIlp) {
+        int jj[kIlp], wi[kIlp], kv[kIlp], sum[kIlp];
+        u64 m[kIlp], m2[kIlp];
+        sibling_items2<true>(c, b, tb + lane, total, j, jj, wi, kv, m, m2, sum);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const bool valid = tb + 32 * u + lane < total;
+            Key ib = key_empty();
+            if (valid) {
+                const u64 corr = (u64)(sum[u] - __popcll(m[u]));
+                if (corr) atomicAdd(&b.rc[jj[u]], corr);
+                if (m2[u]) score_item(c, s, b, jj[u], wi[u], m2[u], L, 0, ib);
+            }
+            merge_item_keys(b, valid ? jj[u] : -1, ib, lane);
+        }
+    }
+    // unlisted records: the whole warp, one leaf gene per lane, on the rows
+    while (dmask) {
+        const int jd = __ffs(dmask) - 1;
+        dmask &= dmask - 1;
+        const Prefix p = b.r[jd].p;
+        const int dlo = b.lo[jd], dhi = b.hi[jd];
+        unsigned by, bn;
+        dense_setup(c, s, p, L, b, by, bn, lane);
+        int po[kMaxH - 1];
+#pragma unroll
+        for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[jd][q] : 0;
+        Key best = key_empty();
+        u64 corr = 0;
+        for (int g = dlo + lane; g <= dhi; g += 32) {
+            const u64 *trow = c.T + (size_t)g * c.WTp;
+            int tp = 0;
+            for (unsigned bits = by; bits; bits &= bits - 1) {
+                const int w = __ffs(bits) - 1;
+                tp += __popcll(b.ys[w] & trow[w]);
+            }
+            if (tp < 2) continue;
+            corr += (u64)(tp - 1);
+            const u64 *nrow = c.N + (size_t)g * c.WNp;
+            int fp = 0;
+            for (unsigned bits = bn; bits; bits &= bits - 1) {
+                const int w = __ffs(bits) - 1;
+                fp += __popcll(b.ns[w] & nrow[w]);
+            }
+            const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+            if (s1 < best.s) continue;
+            const Key k = leaf_key(s1, po, L, c.orig[g]);
+            if (key_better(k, best)) best = k;
+        }
+        best = warp_max_key(best);
+        corr = warp_sum_u64(corr);
+        if (lane == 0) {
+            b.rb[jd] = best;
+            b.rc[jd] = corr;
+        }
+        __syncwarp();
+    }
+}
+
+// Round 0 of an incremental solve with h = 2: the depth-1 nodes that two or more
+// uncovered tumors share (the leaf parents) into the depth-1 frontier.  Every
+// thread of the block must call it.
+__device__ void phase_build1(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, Batch &b,
+                             const Team &t, const u64 *Ush)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int n = c.G - s.h + 1;  // depth-1 nodes
+    u32 *my_count = counts + shard_slot(1, my_shard(t));
+    Rec *out = f.F[1] + (size_t)my_shard(t) * f.cap[1];
+    for (int base = (t.rank * nwarps + warp) * 32; base < n; base += t.size * nwarps * 32) {
+        const int g = base + lane;
+        bool keep = false;
+        if (g < n) keep = gene_record(c, Ush, g, b.r[lane]) && b.r[lane].ky >= 2;
+        const u32 pos = warp_reserve(keep ? 1 : 0, my_count, lane);
+        if (keep && pos < f.cap[1]) {
+            b.r[lane].pad[0] = b.r[lane].pad[1] = b.r[lane].pad[2] = 0;
+            copy_rec(&out[pos], &b.r[lane]);
+        }
+    }
+}
+
+// One incremental round, or with force the evaluation that follows round 0's
+// build, by every block of the team: the block brings its share of the genes and
+// of every depth's kept records up to date with U (Csh: the tumors covered since
+// the previous round), re-evaluates the leaf parents that changed, and adds its
+// share of the round's corrections -- depth 1's surviving count; over the genes
+// shared by k >= 2 uncovered tumors, (k - 1)(hi(2) - g); over the kept nodes of
+// depth l >= 2 with k >= 2 tumors, k - 1 to depth l and (k - 1)(hi(l+1) - last)
+// to depth l + 1; the leaf parents' cached corrections to depth h.  Its best key
+// (leaf caches, and the champions of its uncovered tumors, which stand for the
+// TP = 1 leaves) goes to its slot.  Every thread of the block must call it;
+// returns false (for every thread) if round 0 overflowed a frontier.
+__device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
+                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force)
+{
+    __shared__ u64 acc[kAccN];
+    __shared__ int overflow;
+    const long long t0 = clock64();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int h = s.h;
+    const u64 *Ush = io.Ush;
+    u64 *deep = acc + kAccDeep;  // deep[2l]: depth l's visited correction, deep[2l + 1]: surviving
+    if (threadIdx.x == 0) overflow = 0;
+    acc_begin(acc);
+    u64 csig = 0;
+    for (int w = 0; w < c.Wt; ++w) csig |= Csh[w];
+    Key best = key_empty();
+    for (int smp = t.rank * (int)blockDim.x + (int)threadIdx.x; smp < c.Nt; smp += t.size * (int)blockDim.x) {
+        if (!in_mask(Ush, smp)) continue;
+        Key k;
+        k.s = __ldcg(&s.champ[smp].s);
+        if (k.s == 0 || k.s < best.s) continue;
+        k.t0 = __ldcg(&s.champ[smp].t0);
+        k.t1 = __ldcg(&s.champ[smp].t1);
+        k.t2 = __ldcg(&s.champ[smp].t2);
+        if (key_better(k, best)) best = k;
+    }
+    // depth 1: the genes of a contiguous share, one per thread
+    {
+        const int last1 = c.G - h, hi2 = c.G - h + 1;
+        const int g0 = (int)((long long)c.G * t.rank / t.size), g1 = (int)((long long)c.G * (t.rank + 1) / t.size);
+        u64 alive1 = 0, corrv = 0;
+        for (int g = g0 + (int)threadIdx.x; g < g1; g += (int)blockDim.x) {
+            u32 k = force ? 0u : __ldcg(s.gk + g);
+            if (force || (k != 0 && (__ldg(c.GS + g) & csig) != 0)) {
+                const u32 k2 = gene_uncovered(c, Ush, g);
+                if (force || k2 != k) s.gk[g] = k2;
+                k = k2;
+            }
+            if (g <= last1) {
+                alive1 += (u64)(k >= 1);
+                if (k >= 2) corrv += (u64)(k - 1) * (u64)(hi2 - g);
+            }
+        }
+        alive1 = warp_sum_u64(alive1);
+        corrv = warp_sum_u64(corrv);
+        if (lane == 0) {
+            acc_add(deep, 3, alive1);
+            acc_add(deep, 4, corrv);
+        }
+    }
+    // kept records: depth 1 (h = 2) or 2 .. h-1; the deepest are the leaf parents
+    for (int l = h == 2 ? 1 : 2; l <= h - 1; ++l) {
+        const long long n_in = front_open(counts, l, f.cap[l], b.soff, lane);
+        if (n_in < 0 && lane == 0) overflow = 1;
+        __syncthreads();
+        if (overflow) return false;
+        const u64 n = (u64)n_in;
+        const u32 i0 = (u32)(n * (u64)t.rank / (u64)t.size), i1 = (u32)(n * (u64)(t.rank + 1) / (u64)t.size);
+        const bool leafp = l == h - 1;
+        const int hiN = c.G - h + l;  // hi(l + 1), 0-based
+        u64 corrA = 0, corrV = 0, corrL = 0;
+        for (u32 base = i0 + (u32)warp * 32; base < i1; base += (u32)nwarps * 32) {
+            const u32 i = base + (u32)lane;
+            Rec &r = b.r[lane];
+            u32 slot = 0;
+            u64 sg = 0;
+            bool changed = false;
+            int ky = 0;
+            if (i < i1) {
+                slot = front_slot(f.cap[l], b.soff, i);
+                sg = force ? ~0ull : __ldcg(f.sig[l] + slot);
+                if (sg != 0) {
+                    load_rec(&r, f.F[l] + slot);
+                    if (force || (sg & csig) != 0) changed = refresh_record(c, Ush, l, r, force);
+                    ky = r.ky;
+                    if (changed) {
+                        f.sig[l][slot] = ky >= 2 ? sample_sig(r) : 0ull;
+                        copy_rec(f.F[l] + slot, &r);
+                    }
+                    if (ky >= 2 && l >= 2) {
+                        corrA += (u64)(ky - 1);
+                        corrV += (u64)(ky - 1) * (u64)(hiN - prefix_gene(r.p, l - 1));
+                    }
+                }
+            }
+            if (!leafp) continue;
+            const bool eval = changed && ky >= 2;
+            if (sg != 0 && !eval) {
+                if (ky >= 2) {  // unchanged: its cache
+                    Key k;
+                    k.s = __ldcg(&f.lb[l][slot].s);
+                    if (k.s != 0 && k.s >= best.s) {
+                        k.t0 = __ldcg(&f.lb[l][slot].t0);
+                        k.t1 = __ldcg(&f.lb[l][slot].t1);
+                        k.t2 = __ldcg(&f.lb[l][slot].t2);
+                        if (key_better(k, best)) best = k;
+                    }
+                    corrL += __ldcg(f.lc[l] + slot);
+                } else if (changed) {  // no longer shared: no leaf with TP >= 2
+                    f.lb[l][slot] = key_empty();
+                    f.lc[l][slot] = 0;
+                }
+            }
+            if (__ballot_sync(kFull, eval)) {
+                leaf_parents_eval(c, s, b, eval, l, lane);
+                if (eval) {
+                    const Key k = b.rb[lane];
+                    f.lb[l][slot] = k;
+                    f.lc[l][slot] = b.rc[lane];
+                    corrL += b.rc[lane];
+                    if (k.s != 0 && key_better(k, best)) best = k;
+                }
+                __syncwarp();
+            }
+        }
+        corrA = warp_sum_u64(corrA);
+        corrV = warp_sum_u64(corrV);
+        corrL = warp_sum_u64(corrL);
+        if (lane == 0) {
+            acc_add(deep, 2 * l + 1, corrA);
+            acc_add(deep, 2 * (l + 1), corrV);
+            acc_add(deep, 2 * h + 1, corrL);
+        }
+    }
+    warp_cycles(acc, t0, lane);
+    __syncthreads();
+    const int e = (int)threadIdx.x - 32;  // depth e's two corrections
+    if (e >= 1 && e <= h) {
+        if (deep[2 * e]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, deep[2 * e]);
+        if (deep[2 * e + 1]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2 + 1, deep[2 * e + 1]);
+    }
+    warp_cycles_flush(s, acc, 1, io.par);
+    block_commit_best(best, io.slots, t.rank, io.overwrite);
+    return true;
+}
+
 // End of round r of the persistent solve, run by EVERY block of the team on the
 // same inputs, so that all of them reach the same decisions without another
 // barrier: the winner (largest key of the round's slots), its TP / FP, the next U
@@ -1574,7 +2137,7 @@ __device__ void block_seed(const Cohort &c, const Solve &s, const Team &t, const
 // for a later launch), rescores them into the next threshold (next_hint), and
 // records the selection and the round state.  Returns true when the solve is done.
 __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots, const Team &t,
-                             u64 *Ush, Key *cand_sh, u64 *next_hint)
+                             u64 *Ush, Key *cand_sh, u64 *next_hint, bool fm, u64 *tot, u64 *Csh)
 {
     __shared__ Key wbest[kMaxWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
@@ -1617,6 +2180,7 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             s.work[mx] = 0;
         }
         bool done = true;
+        u64 ycov = 0;  // word `lane` of the tumors the winner covers
         if (best.s != 0) {
             if (lane < h) {
                 const int o = key_get(best, lane);
@@ -1641,6 +2205,7 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             }
             __syncwarp();
             if (lane < c.Wt) {
+                ycov = y;
                 u &= ~y;
                 Ush[lane] = u;
                 s.U[lane] = u;
@@ -1656,6 +2221,26 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
                 s.state[kStK] = k + 1;
             }
         }
+        if (fm) {
+            // the round's counters: depth 1 from its surviving count, depths 2..h from
+            // the per-sample sums over the round's U minus the corrections the update
+            // phase accumulated in their place
+            u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
+            if (lead && lane == 0) {
+                const u64 v1 = c.G >= h ? (u64)(c.G - h + 1) : 0ull;
+                const u64 a1 = __ldcg(cv + 1);
+                cv[0] = v1;
+                cv[1] = v1 - a1;
+            } else if (lead && lane < h) {
+                const u64 vis = tot[h + lane] - __ldcg(cv);
+                const u64 alive = tot[lane] - __ldcg(cv + 1);
+                cv[0] = vis;
+                cv[1] = vis - alive;
+            }
+            // the covered tumors: the next round updates what holds them
+            if (lane < kMaxWords) Csh[lane] = ycov;
+            if (lead && lane < c.WTp) s.cov[lane] = ycov;
+        }
         if (lane == 0) {
             done_sh = done;
             if (lead) {
@@ -1666,9 +2251,20 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
     }
     __syncthreads();
     const bool done = done_sh != 0;
+    if (fm && !done) {
+        // the covered tumors leave the sums of the next round (after the lead block
+        // has read them for this round's counters): one (tumor, sum) pair per thread
+        const int h2 = 2 * h;
+        for (int i = threadIdx.x; i < c.Nt * h2; i += blockDim.x) {
+            const int smp = i / h2;
+            if ((Csh[smp >> 6] >> (smp & 63)) & 1ull) atomicAdd(&tot[i - smp * h2], 0ull - __ldcg(s.ssum + i));
+        }
+        __syncthreads();
+    }
     // one block suffices: the threshold is a lower bound whichever blocks have merged
-    // into it, and it is first read after the next round's first barrier (h >= 3)
-    if (!done && h > 1 && lead) block_rescore(c, s, cand_sh, Ush, next_hint);
+    // into it, and it is first read after the next round's first barrier (h >= 3);
+    // incremental rounds score from their caches and need none
+    if (!done && h > 1 && lead && !fm) block_rescore(c, s, cand_sh, Ush, next_hint);
     return done;
 }
 
@@ -1686,6 +2282,9 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
 {
     __shared__ u64 Ush[kMaxWords];
     __shared__ Key cand_sh[kCandidates];
+    __shared__ u64 tot[2 * kMaxH];
+    __shared__ u64 Csh[kMaxWords];
+    __shared__ int fm_sh;
     const int h = s.h;
     const bool timer = t.rank == 0 && threadIdx.x == 0;
     u64 tm = timer ? global_ns() : 0;
@@ -1712,14 +2311,32 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         // the champions and the first round's threshold, complete before any block
         // starts searching
         if (s.champ) phase_champions(c, s, t, b);
+        if (s.ssum) phase_sample_sums(c, s, t);
         block_seed(c, s, t, Ush, s.best_hint);
         if (!grid_sync(gsync, s.state, t.size)) return;
     }
+    // counting by per-sample sums when every tumor's champion is known (the
+    // champions stand for the TP = 1 leaves that this mode never visits)
+    bool fm = false;
+    if (h > 1 && s.prune == 0 && c.CC && s.champ && s.ssum) {
+        if (threadIdx.x == 0) fm_sh = 1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < c.Nt; i += blockDim.x)
+            if (!__ldcg(s.champ_ok + i)) fm_sh = 0;
+        __syncthreads();
+        fm = fm_sh != 0;
+        if (fm) block_sample_totals(c, s, Ush, tot);
+        // incremental rounds: the tumors covered by the last round's winner
+        for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x)
+            Csh[i] = (fm && round > 0 && i < c.WTp) ? __ldcg(&s.cov[i]) : 0ull;
+        __syncthreads();
+    }
     for (;;) {
         const int par = round & 1;
-        u32 *counts = counts_base + (size_t)par * kCountWords;
-        const RoundIO io{Ush, s.slots + (size_t)par * s.nslots, true, s.best_hint + par, par};
-        if (t.rank == 0) {  // the next round's counters and threshold start from zero
+        // incremental rounds keep round 0's frontiers and their counts (set 0)
+        u32 *counts = counts_base + (size_t)(fm ? 0 : par) * kCountWords;
+        const RoundIO io{Ush, s.slots + (size_t)par * s.nslots, true, s.best_hint + par, par, fm, fm};
+        if (t.rank == 0 && !fm) {  // the next round's counters and threshold start from zero
             u32 *cn = counts_base + (size_t)(par ^ 1) * kCountWords;
             for (int i = threadIdx.x; i < kMaxH * kShards; i += blockDim.x) cn[i * kShardStride] = 0;
             if (threadIdx.x == 0) *(volatile u64 *)(s.best_hint + (par ^ 1)) = 0;
@@ -1739,6 +2356,26 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         if (h == 1) {
             phase_level1(c, s, round, f, counts, t, io);
             lap(0);
+        } else if (fm) {
+            // round 0 builds the kept frontiers; every round then updates them
+            if (round == 0) {
+                if (h == 2) {
+                    phase_build1(c, s, f, counts, b, t, Ush);
+                    if (!grid_sync(gsync, s.state, t.size)) return;
+                }
+                for (int l = 2; l <= h - 1; ++l) {
+                    if (!phase_expand(c, s, round, l, f, counts, b, t, io)) {
+                        overflow();
+                        return;
+                    }
+                    if (!grid_sync(gsync, s.state, t.size)) return;
+                }
+            }
+            lap(1);
+            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0)) {
+                overflow();
+                return;
+            }
         } else {
             // every block reads the same shard counts after the same barrier, so an
             // overflow is seen by all of them and they leave together
@@ -1760,7 +2397,8 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         if (!grid_sync(gsync, s.state, t.size, yield)) return;
         const bool stop = yield && *(volatile int *)&gsync->flag;
         lap(2);
-        const bool done = end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1));
+        const bool done = end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1), fm,
+                                       tot, Csh);
         lap(3);
         if (done) {
             // batch: a team that finished asks the others to stop after their current

@@ -219,6 +219,8 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     c.SL = nullptr;
     c.SO = nullptr;
     c.SLo = nullptr;
+    c.GR = nullptr;
+    c.GS = nullptr;
 
     Solve s;
     s.h = h;
@@ -235,6 +237,9 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.cand = (Key *)(base + kOffCand);
     s.champ = nullptr;  // one kernel per phase: no per-sample champions
     s.champ_ok = nullptr;
+    s.ssum = nullptr;
+    s.gk = nullptr;
+    s.cov = nullptr;
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
@@ -244,6 +249,9 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     for (int l = 0; l < kMaxH; ++l) {
         fr.F[l] = nullptr;
         fr.cap[l] = 0;
+        fr.sig[l] = nullptr;
+        fr.lb[l] = nullptr;
+        fr.lc[l] = nullptr;
     }
     fr.F[1] = (Rec *)(base + kOffF1);
     fr.cap[1] = kNaMaxG / kShards;
