@@ -340,6 +340,7 @@ int build_store(mh_handle *H, const uint64_t *bm)
     const size_t oSLo = piece(SLo.size() * sizeof(u16)), oSO = piece(SO.size() * sizeof(u32));
     const size_t oOrig = piece((size_t)G * sizeof(u16)), oInv = piece((size_t)G * sizeof(u32));
     const size_t oGR = piece((size_t)G * sizeof(Rec)), oGS = piece((size_t)G * sizeof(u64));
+    const size_t oTO = piece(T.size() * sizeof(u64)), oNO = piece(N.size() * sizeof(u64));
     std::vector<unsigned char> host(off, 0);
     auto put = [&](size_t o, const void *src, size_t bytes) {
         if (bytes) memcpy(host.data() + o, src, bytes);
@@ -356,6 +357,11 @@ int build_store(mh_handle *H, const uint64_t *bm)
     put(oInv, inv.data(), (size_t)G * sizeof(u32));
     put(oGR, GR.data(), (size_t)G * sizeof(Rec));
     put(oGS, GS.data(), (size_t)G * sizeof(u64));
+    for (int g = 0; g < G; ++g) {  // original order: row g of the caller's input
+        const int i = (int)inv[g];
+        memcpy(host.data() + oTO + (size_t)g * c.WTp * sizeof(u64), &T[(size_t)i * c.WTp], c.WTp * sizeof(u64));
+        memcpy(host.data() + oNO + (size_t)g * c.WNp * sizeof(u64), &N[(size_t)i * c.WNp], c.WNp * sizeof(u64));
+    }
     if ((rc = dalloc(&H->dStore, off, &H->device_bytes, H->dev, st))) return rc;
     MH_CUDA(cudaMemcpyAsync(H->dStore, host.data(), off, cudaMemcpyHostToDevice, st));
     H->dT = (u64 *)(H->dStore + oT);
@@ -375,6 +381,8 @@ int build_store(mh_handle *H, const uint64_t *bm)
     c.SLo = H->dSLo;
     c.GR = (const Rec *)(H->dStore + oGR);
     c.GS = (const u64 *)(H->dStore + oGS);
+    c.TO = (const u64 *)(H->dStore + oTO);
+    c.NO = (const u64 *)(H->dStore + oNO);
     MH_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
     return MH_OK;
 }
@@ -474,7 +482,7 @@ int ensure_workspace(mh_handle *H, int h)
         if ((rc = dalloc(&H->dChampOk, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dSsum, (size_t)std::max(H->Nt, 1) * 2 * kMaxH, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dGK, (size_t)H->G, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dCov, (size_t)H->c.WTp, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCov, (size_t)H->c.WTp + 2 * (kMaxH + 1), &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
         if (!(H->hState = pinned_state_get())) return fail(MH_ENOMEM, "pinned host allocation failed");
@@ -593,6 +601,7 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     s->ssum = H->dSsum;
     s->gk = H->dGK;
     s->cov = H->dCov;
+    s->run = H->dCov + H->c.WTp;
     s->work = H->dWork;
     s->best_hint = H->dWork + kWorkCount;
     *max_rounds = H->Nt + 1;

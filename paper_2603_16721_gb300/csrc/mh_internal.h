@@ -61,6 +61,9 @@ struct Cohort {
     const Rec *GR;
     // G static tumor signatures: OR of 1 << (s & 63) over the tumors of each gene.
     const u64 *GS;
+    // The rows again in the caller's (original) gene order, G x WTp and G x WNp: a
+    // key's genes read without the search-position lookup.  nullptr: use inv.
+    const u64 *TO, *NO;
 };
 
 // Best candidate of a search, compared as (score desc, original tuple asc).
@@ -124,6 +127,7 @@ struct Solve {
     // cov = the tumors the previous round's winner covered (WTp words).
     u32 *gk;
     u64 *cov;
+    u64 *run;  // 2 (kMaxH + 1) words: running totals of the counter corrections (see mh_kernels.cu)
 };
 
 constexpr int kCandidates = 32;
@@ -165,7 +169,8 @@ constexpr size_t kSlotBytes = sizeof(Rec) + 2 * sizeof(u64) + sizeof(Key);
 // flag: a decision taken by the block that releases a barrier (the batch's yield).
 struct GridSync {
     unsigned count, gen;
-    int flag, pad;
+    int flag;
+    unsigned arrived;  // barriers without a sampled decision: arrivals of the launch so far
 };
 
 // The persistent solve keeps the frontier counters (kCountWords) twice, by round

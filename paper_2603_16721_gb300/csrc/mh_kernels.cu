@@ -812,8 +812,22 @@ __device__ __forceinline__ int score_item(const Cohort &c, const Solve &s, const
     const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
     u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
     u64 fpl[kPlanesN] = {0, 0, 0, 0};
-    for (int q = 0; q < ky; ++q) planes_add(tpl, c.CT[(size_t)r.ids[q] * c.GW + wi], pt);
-    for (int q = 0; q < kn; ++q) planes_add(fpl, c.CN[(size_t)r.ids[kListT + q] * c.GW + wi], pn);
+    // four column loads in flight at a time (a zero word leaves the planes as they are)
+    for (int q = 0; q < ky; q += 4) {
+        u64 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = q + k < ky ? __ldg(c.CT + (size_t)r.ids[q + k] * c.GW + wi) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) planes_add(tpl, x[k], pt);
+    }
+    for (int q = 0; q < kn; q += 4) {
+        u64 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            x[k] = q + k < kn ? __ldg(c.CN + (size_t)r.ids[kListT + q + k] * c.GW + wi) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) planes_add(fpl, x[k], pn);
+    }
     int n = 0;
     while (m) {
         const int bt = __ffsll((long long)m) - 1;
@@ -1472,7 +1486,25 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, 
 {
     __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !sample) {
+        // one atomic per block: arrivals count up across the barriers of a launch
+        // (the word starts at zero), so barrier k ends when the count reaches
+        // (k + 1) * nblocks, and a block learns k from the count it found
+        ok = 1;
+        __threadfence();
+        const unsigned old = atomicAdd(&g->arrived, 1u);
+        const unsigned target = (old / (unsigned)nblocks + 1u) * (unsigned)nblocks;
+        unsigned long long spins = 0;
+        while ((int)(*(volatile unsigned *)&g->arrived - target) < 0) {
+            __nanosleep(32);
+            if (++spins > (1ull << 25)) {
+                atomicExch(&state[kStError], kErrTimeout);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+    } else if (threadIdx.x == 0) {
         ok = 1;
         const unsigned gen = *(volatile unsigned *)&g->gen;
         __threadfence();
@@ -1807,7 +1839,7 @@ __device__ __forceinline__ u32 gene_uncovered(const Cohort &c, const u64 *Ush, i
 // intersection changed (always with force).  Listed samples: the covered ones are
 // dropped.  Unlisted: the intersection is recounted from the rows, and listed
 // once it is small enough.
-__device__ bool refresh_record(const Cohort &c, const u64 *Ush, int L, Rec &r, bool force)
+__device__ bool refresh_record(const Cohort &c, const u64 *Ush, const u64 *Csh, int L, Rec &r, bool force)
 {
     if (!is_dense(r.ky, r.kn)) {
         int k = 0;
@@ -1819,13 +1851,38 @@ __device__ bool refresh_record(const Cohort &c, const u64 *Ush, int L, Rec &r, b
         r.ky = (u16)k;
         return changed || force;
     }
-    int ky = 0;
-    for (int w = 0; w < c.Wt; ++w) {
-        u64 y = Ush[w];
-        for (int i = 0; i < L && y; ++i) y &= __ldg(c.T + (size_t)prefix_gene(r.p, i) * c.WTp + w);
-        ky += __popcll(y);
+    const u64 *rows[kMaxH - 1];
+#pragma unroll
+    for (int i = 0; i < kMaxH - 1; ++i) rows[i] = i < L ? c.T + (size_t)prefix_gene(r.p, i) * c.WTp : nullptr;
+    if (!force) {
+        // unchanged unless the prefix rows meet a covered tumor (few words of Csh are non-zero)
+        bool hit = false;
+        for (int w = 0; w < c.Wt && !hit; ++w) {
+            u64 y = Csh[w];
+            if (!y) continue;
+#pragma unroll
+            for (int i = 0; i < kMaxH - 1; ++i)
+                if (i < L) y &= __ldg(rows[i] + w);
+            hit = y != 0;
+        }
+        if (!hit) return false;
     }
-    if (ky == (int)r.ky && !force) return false;
+    // recount over U, four words (and their rows) in flight at a time
+    int ky = 0;
+    for (int w0 = 0; w0 < c.Wt; w0 += 4) {
+        u64 y[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) y[k] = w0 + k < c.Wt ? Ush[w0 + k] : 0ull;
+#pragma unroll
+        for (int i = 0; i < kMaxH - 1; ++i) {
+            if (i >= L) break;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (w0 + k < c.Wt) y[k] &= __ldg(rows[i] + w0 + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ky += __popcll(y[k]);
+    }
     r.ky = sat16(ky);
     if (!is_dense(ky, r.kn)) {
         int k = 0;
@@ -1984,18 +2041,32 @@ __device__ void phase_build1(const Cohort &c, const Solve &s, const Frontiers &f
 }
 
 // One incremental round, or with force the evaluation that follows round 0's
-// build, by every block of the team: the block brings its share of the genes and
-// of every depth's kept records up to date with U (Csh: the tumors covered since
-// the previous round), re-evaluates the leaf parents that changed, and adds its
-// share of the round's corrections -- depth 1's surviving count; over the genes
-// shared by k >= 2 uncovered tumors, (k - 1)(hi(2) - g); over the kept nodes of
-// depth l >= 2 with k >= 2 tumors, k - 1 to depth l and (k - 1)(hi(l+1) - last)
-// to depth l + 1; the leaf parents' cached corrections to depth h.  Its best key
-// (leaf caches, and the champions of its uncovered tumors, which stand for the
-// TP = 1 leaves) goes to its slot.  Every thread of the block must call it;
-// returns false (for every thread) if round 0 overflowed a frontier.
+// build, by every block of the team.  Depth 1: in round 0 the block counts its
+// share of the genes; later, each gene of a tumor covered since the previous
+// round loses one uncovered tumor.  Kept records: the block scans its share of
+// every depth (record i to block i mod B, then to warp (i / B) mod W, so that
+// records appended together spread out), brings up to date those holding a
+// covered tumor (their signature meets the covered tumors'), re-evaluates the leaf
+// parents among them, and takes the others' best keys from the caches.  What it
+// adds to the round's counter slots are CHANGES of the corrections (in round 0,
+// the corrections themselves), which the end of the round adds to running totals:
+// depth 1's surviving count; (k - 1)(hi(2) - g) over the genes shared by k >= 2
+// uncovered tumors; for a kept node of depth l >= 2 with k >= 2 tumors, k - 1 to
+// depth l and (k - 1)(hi(l+1) - last) to depth l + 1; the leaf parents' sums of
+// TP - 1 to depth h.  The block's best key (leaf caches, and the champions of its
+// uncovered tumors, which stand for the TP = 1 leaves) goes to its slot.  Every
+// thread of the block must call it; returns false (for every thread) if round 0
+// overflowed a frontier.
+constexpr int kScanIlp = 4;  // records whose signature and cached score a lane loads at once
+// soffs / nrec / tab_ok: the kept frontiers' shard offsets and sizes, read once per
+// launch (after round 0's build) into the block's shared memory.
+struct FrontTab {
+    int soff[kMaxH][kShards + 1];
+    long long n[kMaxH];
+    int ok;
+};
 __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
-                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force)
+                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -2003,13 +2074,20 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     const u64 *Ush = io.Ush;
-    u64 *deep = acc + kAccDeep;  // deep[2l]: depth l's visited correction, deep[2l + 1]: surviving
+    u64 *deep = acc + kAccDeep;  // deep[2l], deep[2l + 1]: depth l's two correction changes
     if (threadIdx.x == 0) overflow = 0;
     acc_begin(acc);
     u64 csig = 0;
     for (int w = 0; w < c.Wt; ++w) csig |= Csh[w];
     Key best = key_empty();
-    for (int smp = t.rank * (int)blockDim.x + (int)threadIdx.x; smp < c.Nt; smp += t.size * (int)blockDim.x) {
+    // After round 0 the block's last warp takes the champions and depth 1 while the
+    // others scan the kept records, so that their chains of loads overlap; the lead
+    // block (rank 0), which ends the round with more work than the others, scans no
+    // records then.
+    const int gwarp = nwarps - 1;
+    const bool side = force || warp == gwarp;
+    const int sstride = force ? (int)blockDim.x : 32, sbase = force ? (int)threadIdx.x : lane;
+    for (int smp = t.rank * sstride + sbase; side && smp < c.Nt; smp += t.size * sstride) {
         if (!in_mask(Ush, smp)) continue;
         Key k;
         k.s = __ldcg(&s.champ[smp].s);
@@ -2019,21 +2097,33 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         k.t2 = __ldcg(&s.champ[smp].t2);
         if (key_better(k, best)) best = k;
     }
-    // depth 1: the genes of a contiguous share, one per thread
-    {
+    // depth 1
+    if (side) {
         const int last1 = c.G - h, hi2 = c.G - h + 1;
-        const int g0 = (int)((long long)c.G * t.rank / t.size), g1 = (int)((long long)c.G * (t.rank + 1) / t.size);
         u64 alive1 = 0, corrv = 0;
-        for (int g = g0 + (int)threadIdx.x; g < g1; g += (int)blockDim.x) {
-            u32 k = force ? 0u : __ldcg(s.gk + g);
-            if (force || (k != 0 && (__ldg(c.GS + g) & csig) != 0)) {
-                const u32 k2 = gene_uncovered(c, Ush, g);
-                if (force || k2 != k) s.gk[g] = k2;
-                k = k2;
+        if (force) {  // the genes of a contiguous share, one per thread
+            const int g0 = (int)((long long)c.G * t.rank / t.size), g1 = (int)((long long)c.G * (t.rank + 1) / t.size);
+            for (int g = g0 + (int)threadIdx.x; g < g1; g += (int)blockDim.x) {
+                const u32 k = gene_uncovered(c, Ush, g);
+                s.gk[g] = k;
+                if (g <= last1) {
+                    alive1 += (u64)(k >= 1);
+                    if (k >= 2) corrv += (u64)(k - 1) * (u64)(hi2 - g);
+                }
             }
-            if (g <= last1) {
-                alive1 += (u64)(k >= 1);
-                if (k >= 2) corrv += (u64)(k - 1) * (u64)(hi2 - g);
+        } else {  // each gene of a covered tumor loses one uncovered tumor
+            for (int smp = t.rank; smp < c.Nt; smp += t.size) {
+                if (!in_mask(Csh, smp)) continue;
+                const u32 off = __ldg(c.SO + smp);
+                const int m = (int)(__ldg(c.SO + smp + 1) - off);
+                for (int q = lane; q < m; q += 32) {
+                    const int g = (int)__ldg(c.SL + off + q);
+                    const u32 old = atomicSub(s.gk + g, 1u);
+                    if (g <= last1) {
+                        if (old == 1) alive1 -= 1ull;
+                        if (old >= 2) corrv -= (u64)(hi2 - g);
+                    }
+                }
             }
         }
         alive1 = warp_sum_u64(alive1);
@@ -2044,82 +2134,112 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         }
     }
     // kept records: depth 1 (h = 2) or 2 .. h-1; the deepest are the leaf parents
-    for (int l = h == 2 ? 1 : 2; l <= h - 1; ++l) {
-        const long long n_in = front_open(counts, l, f.cap[l], b.soff, lane);
-        if (n_in < 0 && lane == 0) overflow = 1;
-        __syncthreads();
-        if (overflow) return false;
-        const u64 n = (u64)n_in;
-        const u32 i0 = (u32)(n * (u64)t.rank / (u64)t.size), i1 = (u32)(n * (u64)(t.rank + 1) / (u64)t.size);
-        const bool leafp = l == h - 1;
-        const int hiN = c.G - h + l;  // hi(l + 1), 0-based
-        u64 corrA = 0, corrV = 0, corrL = 0;
-        for (u32 base = i0 + (u32)warp * 32; base < i1; base += (u32)nwarps * 32) {
-            const u32 i = base + (u32)lane;
-            Rec &r = b.r[lane];
-            u32 slot = 0;
-            u64 sg = 0;
-            bool changed = false;
-            int ky = 0;
-            if (i < i1) {
-                slot = front_slot(f.cap[l], b.soff, i);
-                sg = force ? ~0ull : __ldcg(f.sig[l] + slot);
-                if (sg != 0) {
-                    load_rec(&r, f.F[l] + slot);
-                    if (force || (sg & csig) != 0) changed = refresh_record(c, Ush, l, r, force);
-                    ky = r.ky;
-                    if (changed) {
-                        f.sig[l][slot] = ky >= 2 ? sample_sig(r) : 0ull;
-                        copy_rec(f.F[l] + slot, &r);
-                    }
-                    if (ky >= 2 && l >= 2) {
-                        corrA += (u64)(ky - 1);
-                        corrV += (u64)(ky - 1) * (u64)(hiN - prefix_gene(r.p, l - 1));
-                    }
-                }
-            }
-            if (!leafp) continue;
-            const bool eval = changed && ky >= 2;
-            if (sg != 0 && !eval) {
-                if (ky >= 2) {  // unchanged: its cache
-                    Key k;
-                    k.s = __ldcg(&f.lb[l][slot].s);
-                    if (k.s != 0 && k.s >= best.s) {
-                        k.t0 = __ldcg(&f.lb[l][slot].t0);
-                        k.t1 = __ldcg(&f.lb[l][slot].t1);
-                        k.t2 = __ldcg(&f.lb[l][slot].t2);
-                        if (key_better(k, best)) best = k;
-                    }
-                    corrL += __ldcg(f.lc[l] + slot);
-                } else if (changed) {  // no longer shared: no leaf with TP >= 2
-                    f.lb[l][slot] = key_empty();
-                    f.lc[l][slot] = 0;
-                }
-            }
-            if (__ballot_sync(kFull, eval)) {
-                leaf_parents_eval(c, s, b, eval, l, lane);
-                if (eval) {
-                    const Key k = b.rb[lane];
-                    f.lb[l][slot] = k;
-                    f.lc[l][slot] = b.rc[lane];
-                    corrL += b.rc[lane];
-                    if (k.s != 0 && key_better(k, best)) best = k;
-                }
-                __syncwarp();
+    if (force || !ft.ok) {  // their sizes and shard offsets, once per launch
+        for (int l = h == 2 ? 1 : 2; l <= h - 1; ++l) {
+            if (warp == 0) {
+                const long long nl = front_open(counts, l, f.cap[l], b.soff, lane);
+                if (nl < 0 && lane == 0) overflow = 1;
+                for (int i = lane; i <= kShards; i += 32) ft.soff[l][i] = b.soff[i];
+                if (lane == 0) ft.n[l] = nl;
             }
         }
-        corrA = warp_sum_u64(corrA);
-        corrV = warp_sum_u64(corrV);
-        corrL = warp_sum_u64(corrL);
+        __syncthreads();
+        if (overflow) return false;
+        if (threadIdx.x == 0) ft.ok = 1;
+    }
+    for (int l = h == 2 ? 1 : 2; l <= h - 1; ++l) {
+        const long long n_in = ft.n[l];
+        const int *soff = ft.soff[l];
+        const bool leafp = l == h - 1;
+        const int hiN = c.G - h + l;  // hi(l + 1), 0-based
+        u64 dA = 0, dV = 0, dL = 0;
+        // scanners: every block and warp in round 0; later all warps but the last of
+        // every block but the lead
+        const bool split = !force && t.size > 1 && nwarps > 1;
+        const u64 B = split ? (u64)(t.size - 1) : (u64)t.size, W = split ? (u64)(nwarps - 1) : (u64)nwarps;
+        const u64 rk = split ? (u64)(t.rank - 1) : (u64)t.rank;
+        const u64 n = (n_in < 0 || (split && (t.rank == 0 || warp == gwarp))) ? 0ull : (u64)n_in;
+        for (u64 k = 0; rk + B * ((u64)warp + W * 32ull * kScanIlp * k) < n; ++k) {
+            u32 slot[kScanIlp];
+            u64 sg[kScanIlp], ls[kScanIlp];
+#pragma unroll
+            for (int u = 0; u < kScanIlp; ++u) {
+                const u64 i = rk + B * ((u64)warp + W * ((u64)lane + 32ull * (kScanIlp * k + u)));
+                slot[u] = 0;
+                sg[u] = ls[u] = 0;
+                if (i < n) {
+                    slot[u] = front_slot(f.cap[l], soff, (u32)i);
+                    sg[u] = force ? ~0ull : __ldcg(f.sig[l] + slot[u]);
+                    if (leafp && !force) ls[u] = __ldcg(&f.lb[l][slot[u]].s);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kScanIlp; ++u) {
+                const bool dirty = sg[u] != 0 && (force || (sg[u] & csig) != 0);
+                bool cached = leafp && sg[u] != 0 && !dirty;
+                if (__ballot_sync(kFull, dirty)) {
+                    Rec &r = b.r[lane];
+                    bool changed = false;
+                    int kyn = 0;
+                    u64 lco = 0;
+                    if (dirty) {
+                        load_rec(&r, f.F[l] + slot[u]);
+                        if (leafp && !force) lco = __ldcg(f.lc[l] + slot[u]);
+                        const int kyo = force ? 0 : (int)r.ky;  // nothing counted before round 0
+                        changed = refresh_record(c, Ush, Csh, l, r, force);
+                        kyn = r.ky;
+                        if (changed) {
+                            f.sig[l][slot[u]] = kyn >= 2 ? sample_sig(r) : 0ull;
+                            copy_rec(f.F[l] + slot[u], &r);
+                            if (l >= 2) {
+                                const u64 fo = kyo >= 2 ? (u64)(kyo - 1) : 0ull, fn = kyn >= 2 ? (u64)(kyn - 1) : 0ull;
+                                dA += fn - fo;
+                                dV += (fn - fo) * (u64)(hiN - prefix_gene(r.p, l - 1));
+                            }
+                        } else {
+                            cached = leafp;  // nothing covered in it after all
+                        }
+                    }
+                    const bool eval = leafp && changed && kyn >= 2;
+                    if (leafp && changed && kyn < 2) {  // no longer shared: no leaf with TP >= 2
+                        f.lb[l][slot[u]] = key_empty();
+                        f.lc[l][slot[u]] = 0;
+                        dL -= lco;
+                    }
+                    if (__ballot_sync(kFull, eval)) {
+                        leaf_parents_eval(c, s, b, eval, l, lane);
+                        if (eval) {
+                            const Key kb = b.rb[lane];
+                            f.lb[l][slot[u]] = kb;
+                            f.lc[l][slot[u]] = b.rc[lane];
+                            dL += b.rc[lane] - lco;
+                            if (kb.s != 0 && key_better(kb, best)) best = kb;
+                        }
+                        __syncwarp();
+                    }
+                }
+                if (cached && ls[u] != 0 && ls[u] >= best.s) {  // unchanged: its cached best
+                    Key kc;
+                    kc.s = ls[u];
+                    kc.t0 = __ldcg(&f.lb[l][slot[u]].t0);
+                    kc.t1 = __ldcg(&f.lb[l][slot[u]].t1);
+                    kc.t2 = __ldcg(&f.lb[l][slot[u]].t2);
+                    if (key_better(kc, best)) best = kc;
+                }
+            }
+        }
+        dA = warp_sum_u64(dA);
+        dV = warp_sum_u64(dV);
+        dL = warp_sum_u64(dL);
         if (lane == 0) {
-            acc_add(deep, 2 * l + 1, corrA);
-            acc_add(deep, 2 * (l + 1), corrV);
-            acc_add(deep, 2 * h + 1, corrL);
+            acc_add(deep, 2 * l + 1, dA);
+            acc_add(deep, 2 * (l + 1), dV);
+            acc_add(deep, 2 * h + 1, dL);
         }
     }
     warp_cycles(acc, t0, lane);
     __syncthreads();
-    const int e = (int)threadIdx.x - 32;  // depth e's two corrections
+    const int e = (int)threadIdx.x - 32;  // depth e's two correction changes
     if (e >= 1 && e <= h) {
         if (deep[2 * e]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, deep[2 * e]);
         if (deep[2 * e + 1]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2 + 1, deep[2 * e + 1]);
@@ -2137,7 +2257,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
 // for a later launch), rescores them into the next threshold (next_hint), and
 // records the selection and the round state.  Returns true when the solve is done.
 __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots, const Team &t,
-                             u64 *Ush, Key *cand_sh, u64 *next_hint, bool fm, u64 *tot, u64 *Csh)
+                             u64 *Ush, Key *cand_sh, u64 *next_hint, bool fm, u64 *tot, u64 *Csh, u64 *run)
 {
     __shared__ Key wbest[kMaxWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
@@ -2185,18 +2305,26 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             if (lane < h) {
                 const int o = key_get(best, lane);
                 os[lane] = o;
-                gs[lane] = (int)c.inv[o];
+                if (!c.TO) gs[lane] = (int)c.inv[o];
             }
             __syncwarp();
             u64 y = 0, n = 0, u = 0;
+            // the winner's rows: by original index, or by search position
+            const u64 *TR = c.TO ? c.TO : c.T;
+            const u64 *NR = c.TO ? c.NO : c.N;
+            const int *ri = c.TO ? os : gs;
             if (lane < c.Wt) {
                 u = Ush[lane];
                 y = u;
-                for (int i = 0; i < h; ++i) y &= c.T[(size_t)gs[i] * c.WTp + lane];
+#pragma unroll
+                for (int i = 0; i < kMaxH; ++i)
+                    if (i < h) y &= __ldg(TR + (size_t)ri[i] * c.WTp + lane);
             }
             if (lane < c.Wn) {
                 n = ~0ull;
-                for (int i = 0; i < h; ++i) n &= c.N[(size_t)gs[i] * c.WNp + lane];
+#pragma unroll
+                for (int i = 0; i < kMaxH; ++i)
+                    if (i < h) n &= __ldg(NR + (size_t)ri[i] * c.WNp + lane);
             }
             int tp = __popcll(y), fp = __popcll(n);
             for (int off = 16; off; off >>= 1) {
@@ -2225,17 +2353,24 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             // the round's counters: depth 1 from its surviving count, depths 2..h from
             // the per-sample sums over the round's U minus the corrections the update
             // phase accumulated in their place
+            // (the round's changes of the corrections join the lead's running totals)
             u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
-            if (lead && lane == 0) {
-                const u64 v1 = c.G >= h ? (u64)(c.G - h + 1) : 0ull;
-                const u64 a1 = __ldcg(cv + 1);
-                cv[0] = v1;
-                cv[1] = v1 - a1;
-            } else if (lead && lane < h) {
-                const u64 vis = tot[h + lane] - __ldcg(cv);
-                const u64 alive = tot[lane] - __ldcg(cv + 1);
+            if (lead && lane < h) {
+                const int l = lane + 1;
+                run[2 * l] += __ldcg(cv);
+                run[2 * l + 1] += __ldcg(cv + 1);
+                u64 vis, alive;
+                if (l == 1) {
+                    vis = c.G >= h ? (u64)(c.G - h + 1) : 0ull;
+                    alive = run[3];
+                } else {
+                    vis = tot[h + lane] - run[2 * l];
+                    alive = tot[lane] - run[2 * l + 1];
+                }
                 cv[0] = vis;
                 cv[1] = vis - alive;
+                s.run[2 * l] = run[2 * l];
+                s.run[2 * l + 1] = run[2 * l + 1];
             }
             // the covered tumors: the next round updates what holds them
             if (lane < kMaxWords) Csh[lane] = ycov;
@@ -2251,9 +2386,10 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
     }
     __syncthreads();
     const bool done = done_sh != 0;
-    if (fm && !done) {
+    if (fm && !done && lead) {
         // the covered tumors leave the sums of the next round (after the lead block
-        // has read them for this round's counters): one (tumor, sum) pair per thread
+        // has read them for this round's counters): one (tumor, sum) pair per thread;
+        // only the lead block finishes the counters, so only it keeps the sums
         const int h2 = 2 * h;
         for (int i = threadIdx.x; i < c.Nt * h2; i += blockDim.x) {
             const int smp = i / h2;
@@ -2284,6 +2420,8 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     __shared__ Key cand_sh[kCandidates];
     __shared__ u64 tot[2 * kMaxH];
     __shared__ u64 Csh[kMaxWords];
+    __shared__ u64 run[2 * (kMaxH + 1)];  // incremental rounds, rank 0: the corrections' running totals
+    __shared__ FrontTab ftab;
     __shared__ int fm_sh;
     const int h = s.h;
     const bool timer = t.rank == 0 && threadIdx.x == 0;
@@ -2297,6 +2435,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     };
     if (*(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStError]) return;
     int round = *(volatile int *)&s.state[kStRound];
+    if (threadIdx.x == 0) ftab.ok = 0;
     // start of a launch: U and the candidates left by the previous round
     for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x) Ush[i] = i < c.WTp ? __ldcg(&s.U[i]) : 0ull;
     for (int i = threadIdx.x; i < kCandidates; i += blockDim.x) {
@@ -2325,10 +2464,12 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
             if (!__ldcg(s.champ_ok + i)) fm_sh = 0;
         __syncthreads();
         fm = fm_sh != 0;
-        if (fm) block_sample_totals(c, s, Ush, tot);
+        if (fm && t.rank == 0) block_sample_totals(c, s, Ush, tot);
         // incremental rounds: the tumors covered by the last round's winner
         for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x)
             Csh[i] = (fm && round > 0 && i < c.WTp) ? __ldcg(&s.cov[i]) : 0ull;
+        for (int i = threadIdx.x; i < 2 * (kMaxH + 1); i += blockDim.x)
+            run[i] = (fm && round > 0) ? __ldcg(s.run + i) : 0ull;
         __syncthreads();
     }
     for (;;) {
@@ -2372,7 +2513,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
             lap(1);
-            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0)) {
+            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab)) {
                 overflow();
                 return;
             }
@@ -2398,7 +2539,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         const bool stop = yield && *(volatile int *)&gsync->flag;
         lap(2);
         const bool done = end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1), fm,
-                                       tot, Csh);
+                                       tot, Csh, run);
         lap(3);
         if (done) {
             // batch: a team that finished asks the others to stop after their current

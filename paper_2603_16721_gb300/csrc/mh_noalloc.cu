@@ -221,6 +221,8 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     c.SLo = nullptr;
     c.GR = nullptr;
     c.GS = nullptr;
+    c.TO = nullptr;
+    c.NO = nullptr;
 
     Solve s;
     s.h = h;
@@ -240,6 +242,7 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.ssum = nullptr;
     s.gk = nullptr;
     s.cov = nullptr;
+    s.run = nullptr;
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);
