@@ -1901,6 +1901,66 @@ __device__ bool refresh_record(const Cohort &c, const u64 *Ush, const u64 *Csh, 
     return true;
 }
 
+// One (record j, column word wi) item of a leaf parent: the record's tumor
+// columns, eight loads in flight at a time, give the non-empty children m, the
+// children of two or more tumors m2, the children's summed sizes (corr = that sum
+// minus |m|, the item's share of sum(TP - 1) over its TP >= 2 leaves) and
+// bit-sliced TP counts; the normal columns, read only when m2 is non-empty, give
+// FP; the children in m2 are scored into best.
+constexpr int kEvalLoads = 8;
+__device__ __forceinline__ void leaf_item_eval(const Cohort &c, const Solve &s, const Batch &b, int j, int wi, u64 rw,
+                                               int L, u64 &corr, Key &best)
+{
+    const Rec &r = b.r[j];
+    const int ky = r.ky, kn = r.kn;
+    const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
+    u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
+    u64 m = 0, m2 = 0;
+    int sum = 0;
+    for (int q = 0; q < ky; q += kEvalLoads) {
+        u64 x[kEvalLoads];
+#pragma unroll
+        for (int k = 0; k < kEvalLoads; ++k)
+            x[k] = q + k < ky ? __ldg(c.CT + (size_t)r.ids[q + k] * c.GW + wi) & rw : 0ull;
+#pragma unroll
+        for (int k = 0; k < kEvalLoads; ++k) {
+            m2 |= m & x[k];
+            m |= x[k];
+            sum += __popcll(x[k]);
+            planes_add(tpl, x[k], pt);
+        }
+    }
+    corr = (u64)(sum - __popcll(m));
+    if (!m2) return;
+    u64 fpl[kPlanesN] = {0, 0, 0, 0};
+    for (int q = 0; q < kn; q += kEvalLoads) {
+        u64 x[kEvalLoads];
+#pragma unroll
+        for (int k = 0; k < kEvalLoads; ++k)
+            x[k] = q + k < kn ? __ldg(c.CN + (size_t)r.ids[kListT + q + k] * c.GW + wi) : 0ull;
+#pragma unroll
+        for (int k = 0; k < kEvalLoads; ++k) planes_add(fpl, x[k], pn);
+    }
+    int po[kMaxH - 1];
+#pragma unroll
+    for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[j][q] : 0;
+    while (m2) {
+        const int bt = __ffsll((long long)m2) - 1;
+        m2 &= m2 - 1;
+        const int tp = planes_get(tpl, bt, pt);
+        const int fp = planes_get(fpl, bt, pn);
+        const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
+        if (s1 < best.s) continue;
+        const Key k = leaf_key(s1, po, L, c.orig[wi * 64 + bt]);
+        if (key_better(k, best)) best = k;
+    }
+}
+
+// Original indices of a kept record's prefix genes, ascending, in the record's
+// spare bytes (prefixes of up to kPadGenes genes).
+constexpr int kPadGenes = 6;
+__device__ __forceinline__ u16 *pad_po(Rec &r) { return reinterpret_cast<u16 *>(r.pad); }
+
 // Merges the per-lane keys of one item step into the records' best keys: items of
 // a step sit on the lanes in record order, so a segmented warp maximum leaves each
 // record's best on its first lane, which merges it into rb.
@@ -1932,19 +1992,23 @@ __device__ void leaf_parents_eval(const Cohort &c, const Solve &s, Batch &b, boo
     b.rb[lane] = key_empty();
     b.rc[lane] = 0;
     if (live) {
-        const Rec &r = b.r[lane];
+        Rec &r = b.r[lane];
         lo = prefix_gene(r.p, L - 1) + 1;
         hi = c.G - 1;
         ky = r.ky;
         kn = r.kn;
-        for (int q = 0; q < L; ++q) {  // ascending original indices of the prefix (leaf keys)
-            const u16 v = c.orig[prefix_gene(r.p, q)];
-            int k = q - 1;
-            while (k >= 0 && b.po[lane][k] > v) {
-                b.po[lane][k + 1] = b.po[lane][k];
-                --k;
+        if (L <= kPadGenes) {  // ascending original indices of the prefix (leaf keys)
+            for (int q = 0; q < L; ++q) b.po[lane][q] = pad_po(r)[q];
+        } else {
+            for (int q = 0; q < L; ++q) {
+                const u16 v = c.orig[prefix_gene(r.p, q)];
+                int k = q - 1;
+                while (k >= 0 && b.po[lane][k] > v) {
+                    b.po[lane][k + 1] = b.po[lane][k];
+                    --k;
+                }
+                b.po[lane][k + 1] = v;
             }
-            b.po[lane][k + 1] = v;
         }
     }
     b.lo[lane] = lo;
@@ -1959,21 +2023,18 @@ __device__ void leaf_parents_eval(const Cohort &c, const Solve &s, Batch &b, boo
     __syncwarp();
     const int total = __shfl_sync(kFull, incl, 31);
     int j = 0;
-    for (int tb = 0; tb < total; tb += 32 * kIlp) {
-        int jj[kIlp], wi[kIlp], kv[kIlp], sum[kIlp];
-        u64 m[kIlp], m2[kIlp];
-        sibling_items2<true>(c, b, tb + lane, total, j, jj, wi, kv, m, m2, sum);
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-            const bool valid = tb + 32 * u + lane < total;
-            Key ib = key_empty();
-            if (valid) {
-                const u64 corr = (u64)(sum[u] - __popcll(m[u]));
-                if (corr) atomicAdd(&b.rc[jj[u]], corr);
-                if (m2[u]) score_item(c, s, b, jj[u], wi[u], m2[u], L, 0, ib);
-            }
-            merge_item_keys(b, valid ? jj[u] : -1, ib, lane);
+    for (int tb = 0; tb < total; tb += 32) {
+        const int t = tb + lane;
+        const bool valid = t < total;
+        Key ib = key_empty();
+        if (valid) {
+            while (t >= b.off[j + 1]) ++j;
+            const int wi = (b.lo[j] >> 6) + (t - b.off[j]);
+            u64 corr = 0;
+            leaf_item_eval(c, s, b, j, wi, range_word(wi, b.lo[j], b.hi[j]), L, corr, ib);
+            if (corr) atomicAdd(&b.rc[j], corr);
         }
+        merge_item_keys(b, valid ? j : -1, ib, lane);
     }
     // unlisted records: the whole warp, one leaf gene per lane, on the rows
     while (dmask) {
@@ -2188,6 +2249,18 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                         const int kyo = force ? 0 : (int)r.ky;  // nothing counted before round 0
                         changed = refresh_record(c, Ush, Csh, l, r, force);
                         kyn = r.ky;
+                        if (force && leafp && l <= kPadGenes) {  // the key genes, once
+                            u16 *po = pad_po(r);
+                            for (int q = 0; q < l; ++q) {
+                                const u16 v = c.orig[prefix_gene(r.p, q)];
+                                int k = q - 1;
+                                while (k >= 0 && po[k] > v) {
+                                    po[k + 1] = po[k];
+                                    --k;
+                                }
+                                po[k + 1] = v;
+                            }
+                        }
                         if (changed) {
                             f.sig[l][slot[u]] = kyn >= 2 ? sample_sig(r) : 0ull;
                             copy_rec(f.F[l] + slot[u], &r);
