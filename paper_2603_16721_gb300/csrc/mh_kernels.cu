@@ -2127,7 +2127,8 @@ struct FrontTab {
     int ok;
 };
 __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
-                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft)
+                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft,
+                             u64 *tot, int *tot_pending)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -2157,6 +2158,22 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         k.t1 = __ldcg(&s.champ[smp].t1);
         k.t2 = __ldcg(&s.champ[smp].t2);
         if (key_better(k, best)) best = k;
+    }
+    // the lead's idle warps: the covered tumors leave the per-sample sums, and the
+    // previous round's longest warps join the diagnostics
+    if (t.rank == 0 && !side) {
+        if (*tot_pending) {
+            const int h2 = 2 * h;
+            for (int i = (int)threadIdx.x; i < c.Nt * h2; i += gwarp * 32) {
+                const int smp = i / h2;
+                if (in_mask(Csh, smp)) atomicAdd(&tot[i - smp * h2], 0ull - __ldcg(s.ssum + i));
+            }
+        }
+        if (warp == 0 && lane < 2 && round > 0) {
+            const int mx = (((round - 1) & 1) ? kWorkWarpMaxOdd : kWorkWarpMax) + lane;
+            s.work[kWorkWarpMaxSum + lane] += __ldcg(&s.work[mx]);
+            s.work[mx] = 0;
+        }
     }
     // depth 1
     if (side) {
@@ -2312,6 +2329,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     }
     warp_cycles(acc, t0, lane);
     __syncthreads();
+    if (threadIdx.x == 0) *tot_pending = 0;
     const int e = (int)threadIdx.x - 32;  // depth e's two correction changes
     if (e >= 1 && e <= h) {
         if (deep[2 * e]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, deep[2 * e]);
@@ -2330,7 +2348,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
 // for a later launch), rescores them into the next threshold (next_hint), and
 // records the selection and the round state.  Returns true when the solve is done.
 __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots, const Team &t,
-                             u64 *Ush, Key *cand_sh, u64 *next_hint, bool fm, u64 *tot, u64 *Csh, u64 *run)
+                             u64 *Ush, Key *cand_sh, u64 *next_hint)
 {
     __shared__ Key wbest[kMaxWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
@@ -2373,7 +2391,6 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             s.work[mx] = 0;
         }
         bool done = true;
-        u64 ycov = 0;  // word `lane` of the tumors the winner covers
         if (best.s != 0) {
             if (lane < h) {
                 const int o = key_get(best, lane);
@@ -2406,7 +2423,6 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
             }
             __syncwarp();
             if (lane < c.Wt) {
-                ycov = y;
                 u &= ~y;
                 Ush[lane] = u;
                 s.U[lane] = u;
@@ -2422,33 +2438,6 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
                 s.state[kStK] = k + 1;
             }
         }
-        if (fm) {
-            // the round's counters: depth 1 from its surviving count, depths 2..h from
-            // the per-sample sums over the round's U minus the corrections the update
-            // phase accumulated in their place
-            // (the round's changes of the corrections join the lead's running totals)
-            u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
-            if (lead && lane < h) {
-                const int l = lane + 1;
-                run[2 * l] += __ldcg(cv);
-                run[2 * l + 1] += __ldcg(cv + 1);
-                u64 vis, alive;
-                if (l == 1) {
-                    vis = c.G >= h ? (u64)(c.G - h + 1) : 0ull;
-                    alive = run[3];
-                } else {
-                    vis = tot[h + lane] - run[2 * l];
-                    alive = tot[lane] - run[2 * l + 1];
-                }
-                cv[0] = vis;
-                cv[1] = vis - alive;
-                s.run[2 * l] = run[2 * l];
-                s.run[2 * l + 1] = run[2 * l + 1];
-            }
-            // the covered tumors: the next round updates what holds them
-            if (lane < kMaxWords) Csh[lane] = ycov;
-            if (lead && lane < c.WTp) s.cov[lane] = ycov;
-        }
         if (lane == 0) {
             done_sh = done;
             if (lead) {
@@ -2459,22 +2448,125 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
     }
     __syncthreads();
     const bool done = done_sh != 0;
-    if (fm && !done && lead) {
-        // the covered tumors leave the sums of the next round (after the lead block
-        // has read them for this round's counters): one (tumor, sum) pair per thread;
-        // only the lead block finishes the counters, so only it keeps the sums
-        const int h2 = 2 * h;
-        for (int i = threadIdx.x; i < c.Nt * h2; i += blockDim.x) {
-            const int smp = i / h2;
-            if ((Csh[smp >> 6] >> (smp & 63)) & 1ull) atomicAdd(&tot[i - smp * h2], 0ull - __ldcg(s.ssum + i));
-        }
-        __syncthreads();
-    }
     // one block suffices: the threshold is a lower bound whichever blocks have merged
-    // into it, and it is first read after the next round's first barrier (h >= 3);
-    // incremental rounds score from their caches and need none
-    if (!done && h > 1 && lead && !fm) block_rescore(c, s, cand_sh, Ush, next_hint);
+    // into it, and it is first read after the next round's first barrier (h >= 3)
+    if (!done && h > 1 && lead) block_rescore(c, s, cand_sh, Ush, next_hint);
     return done;
+}
+
+// End of an incremental round, by every block on the same inputs: warp 0 alone
+// reduces the blocks' slots to the winner, computes its TP / FP and the tumors it
+// covers, applies DelCols to the block's copy of U and keeps the covered tumors
+// (Csh) for the next round's update.  The lead block (rank 0) also records the
+// selection and finishes the round's counters: depth 1 from its surviving count,
+// depths 2..h as the per-sample sums over the round's U (tot) minus the running
+// totals of the corrections (run, to which it adds the round's changes, read
+// together with the slots).  Taking the covered tumors out of tot waits for the
+// lead's idle warps in the next round's update (*tot_pending).  kk: the lead's
+// count of selections; maxr: the round limit.  Returns true when the solve is done.
+__device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots,
+                                 const Team &t, u64 *Ush, const u64 *tot, u64 *Csh, u64 *run, int *kk, int maxr,
+                                 int *tot_pending)
+{
+    __shared__ int os[kMaxH];
+    __shared__ int done_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = s.h;
+    const bool lead = t.rank == 0;
+    if (warp == 0) {
+        u64 dv = 0, da = 0;
+        u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
+        if (lead && lane < h) {
+            dv = __ldcg(cv);
+            da = __ldcg(cv + 1);
+        }
+        Key best = key_empty();
+        for (int i = lane; i < nslots; i += 32) {
+            Key k;
+            k.s = __ldcg(&slots[i].s);
+            k.t0 = __ldcg(&slots[i].t0);
+            k.t1 = __ldcg(&slots[i].t1);
+            k.t2 = __ldcg(&slots[i].t2);
+            if (key_better(k, best)) best = k;
+        }
+        best = warp_max_key(best);
+        bool done = true;
+        u64 ycov = 0;
+        if (best.s != 0) {
+            if (lane < h) os[lane] = key_get(best, lane);
+            __syncwarp();
+            const u64 *TR = c.TO ? c.TO : c.T;
+            const u64 *NR = c.TO ? c.NO : c.N;
+            int ri[kMaxH];
+#pragma unroll
+            for (int i = 0; i < kMaxH; ++i) ri[i] = i < h ? (c.TO ? os[i] : (int)c.inv[os[i]]) : 0;
+            u64 y = 0, n = 0, u = 0;
+            if (lane < c.Wt) {
+                u = Ush[lane];
+                y = u;
+#pragma unroll
+                for (int i = 0; i < kMaxH; ++i)
+                    if (i < h) y &= __ldg(TR + (size_t)ri[i] * c.WTp + lane);
+            }
+            if (lane < c.Wn) {
+                n = ~0ull;
+#pragma unroll
+                for (int i = 0; i < kMaxH; ++i)
+                    if (i < h) n &= __ldg(NR + (size_t)ri[i] * c.WNp + lane);
+            }
+            int tp = __popcll(y), fp = __popcll(n);
+            for (int off = 16; off; off >>= 1) {
+                tp += __shfl_xor_sync(kFull, tp, off);
+                fp += __shfl_xor_sync(kFull, fp, off);
+            }
+            if (lane < c.Wt) {
+                ycov = y;
+                u &= ~y;
+                Ush[lane] = u;
+                s.U[lane] = u;
+            }
+            const unsigned left = __ballot_sync(kFull, u != 0);
+            done = !left || round + 1 >= maxr;
+            if (lead && lane == 0) {
+                const int k = *kk;
+                int *r = s.res + (size_t)k * (h + 2);
+                for (int i = 0; i < h; ++i) r[i] = os[i];
+                r[h] = tp;
+                r[h + 1] = fp;
+                s.state[kStK] = k + 1;
+                *kk = k + 1;
+            }
+        }
+        if (lead && lane < h) {
+            const int l = lane + 1;
+            run[2 * l] += dv;
+            run[2 * l + 1] += da;
+            u64 vis, alive;
+            if (l == 1) {
+                vis = c.G >= h ? (u64)(c.G - h + 1) : 0ull;
+                alive = run[3];
+            } else {
+                vis = tot[h + lane] - run[2 * l];
+                alive = tot[lane] - run[2 * l + 1];
+            }
+            cv[0] = vis;
+            cv[1] = vis - alive;
+            s.run[2 * l] = run[2 * l];
+            s.run[2 * l + 1] = run[2 * l + 1];
+        }
+        Csh[lane] = ycov;  // kMaxWords == 32 words, one per lane
+        if (lead && lane < c.WTp) s.cov[lane] = ycov;
+        if (lane == 0) {
+            done_sh = done;
+            if (lead) {
+                s.state[kStRound] = round + 1;
+                if (done) s.state[kStDone] = 1;
+                *tot_pending = done ? 0 : 1;
+            }
+        }
+    }
+    __syncthreads();
+    return done_sh != 0;
 }
 
 // The greedy loop of one cohort run by a team of co-resident blocks.  A round is
@@ -2495,7 +2587,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     __shared__ u64 Csh[kMaxWords];
     __shared__ u64 run[2 * (kMaxH + 1)];  // incremental rounds, rank 0: the corrections' running totals
     __shared__ FrontTab ftab;
-    __shared__ int fm_sh;
+    __shared__ int fm_sh, kk_sh, tot_pending;
     const int h = s.h;
     const bool timer = t.rank == 0 && threadIdx.x == 0;
     u64 tm = timer ? global_ns() : 0;
@@ -2508,7 +2600,12 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     };
     if (*(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStError]) return;
     int round = *(volatile int *)&s.state[kStRound];
-    if (threadIdx.x == 0) ftab.ok = 0;
+    const int maxr = *(volatile int *)&s.state[kStMaxRounds];
+    if (threadIdx.x == 0) {
+        ftab.ok = 0;
+        kk_sh = *(volatile int *)&s.state[kStK];
+        tot_pending = 0;
+    }
     // start of a launch: U and the candidates left by the previous round
     for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x) Ush[i] = i < c.WTp ? __ldcg(&s.U[i]) : 0ull;
     for (int i = threadIdx.x; i < kCandidates; i += blockDim.x) {
@@ -2586,7 +2683,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
             lap(1);
-            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab)) {
+            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
                 overflow();
                 return;
             }
@@ -2611,8 +2708,9 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         if (!grid_sync(gsync, s.state, t.size, yield)) return;
         const bool stop = yield && *(volatile int *)&gsync->flag;
         lap(2);
-        const bool done = end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1), fm,
-                                       tot, Csh, run);
+        const bool done = fm ? end_of_round_inc(c, s, round, io.slots, t.size, t, Ush, tot, Csh, run, &kk_sh, maxr,
+                                                &tot_pending)
+                             : end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1));
         lap(3);
         if (done) {
             // batch: a team that finished asks the others to stop after their current
