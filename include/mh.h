@@ -63,9 +63,21 @@ typedef struct {
  *                   uncovered tumors is empty, at every depth (§III-D).
  *   MH_PRUNE_OFF:   exhaustive enumeration of every h-subset (the paper's
  *                   BOUND=OFF baseline); the result is identical, the counters
- *                   are the closed forms C(G-h+l, l). */
+ *                   are the closed forms C(G-h+l, l).
+ *   MH_PRUNE_BOUND: paper pruning plus a score bound, an addition (the paper uses
+ *                   no branch and bound, §II-B): a non-empty prefix with tumor
+ *                   intersection y can only lead to leaves scoring at most
+ *                   alpha.num * |y| + alpha.den * Nn (TP <= |y|, FP >= 0 in the
+ *                   score of §II-B), so it is cut when that bound is below the
+ *                   score of a candidate already found in the round (strictly:
+ *                   an equal score could still win on the tuple order).  The
+ *                   selections are those of MH_PRUNE_PAPER; visited / pruned
+ *                   count the nodes the bounded search computed and cut counts
+ *                   the prefixes it cut, both depending on when candidates were
+ *                   found (not reproducible from run to run). */
 #define MH_PRUNE_PAPER 0
 #define MH_PRUNE_OFF 1
+#define MH_PRUNE_BOUND 2
 
 /* Execution of a solve.
  *   MH_MODE_PERSISTENT: one cooperative kernel runs every round, its phases
@@ -79,7 +91,7 @@ typedef struct {
 typedef struct {
     int32_t h;            /* hits per combination, 1..9 */
     mh_rational alpha;    /* weight of true positives */
-    int32_t prune;        /* MH_PRUNE_PAPER (default 0) or MH_PRUNE_OFF */
+    int32_t prune;        /* MH_PRUNE_PAPER (default 0), MH_PRUNE_OFF or MH_PRUNE_BOUND */
     int32_t max_rounds;   /* stop after this many greedy rounds; <= 0 means no limit */
     int32_t time_kernels; /* non-zero: time every kernel launch with CUDA events */
     int32_t mode;         /* MH_MODE_PERSISTENT (default 0) or MH_MODE_LAUNCHES */
@@ -119,6 +131,8 @@ typedef struct {
     double kernel_ms;        /* persistent mode: the solve kernel's own duration (CUDA events around
                                 each cooperative launch, summed over relaunches); launch mode with
                                 time_kernels: the four phase times summed; else 0 */
+    uint64_t *cut;           /* rounds*h: MH_PRUNE_BOUND, the depth-l prefixes cut by the score bound
+                                (cut[r*h + l-1]); zero in the other modes */
 } mh_result;
 
 /* Create a handle for one cohort from packed rows in HOST memory.

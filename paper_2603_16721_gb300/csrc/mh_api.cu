@@ -166,7 +166,7 @@ struct mh_handle {
     u32 *dInv = nullptr;
     // solve workspace (grown on demand)
     int ws_h = 0, ws_rounds = 0, ws_slots = 0;
-    u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr;
+    u64 *dU = nullptr, *dCnt = nullptr, *dWork = nullptr, *dCut = nullptr;
     int *dState = nullptr, *dRes = nullptr;
     Key *dSlots = nullptr, *dCand = nullptr, *dChamp = nullptr;
     int *dChampOk = nullptr;
@@ -191,7 +191,7 @@ struct mh_handle {
         for (int i = 0; i < 2; ++i)
             if (evk[i]) cudaEventDestroy(evk[i]);
         for (void *p : {(void *)dStore, (void *)dU,
-                        (void *)dCnt, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk, (void *)dSsum,
+                        (void *)dCnt, (void *)dCut, (void *)dWork, (void *)dState, (void *)dRes, (void *)dSlots, (void *)dCand, (void *)dChamp, (void *)dChampOk, (void *)dSsum,
                         (void *)dCounts, (void *)dSync})
             dfree(p, stream);
         for (int l = 0; l < kMaxH; ++l) {
@@ -490,10 +490,13 @@ int ensure_workspace(mh_handle *H, int h)
     if (h > H->ws_h || rounds > H->ws_rounds) {
         dfree(H->dCnt, st);
         dfree(H->dRes, st);
+        dfree(H->dCut, st);
         H->dCnt = nullptr;
         H->dRes = nullptr;
+        H->dCut = nullptr;
         const int hh = std::max(h, H->ws_h);
         if ((rc = dalloc(&H->dCnt, (size_t)rounds * hh * 2, &H->device_bytes, dev, st))) return rc;
+        if ((rc = dalloc(&H->dCut, (size_t)rounds * hh, &H->device_bytes, dev, st))) return rc;
         if ((rc = dalloc(&H->dRes, (size_t)rounds * (hh + 2), &H->device_bytes, dev, st))) return rc;
         H->ws_h = hh;
         H->ws_rounds = rounds;
@@ -578,13 +581,13 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     if (h < 1 || h > kMaxH) return fail(MH_EINVAL, "h=%d outside [1, %d]", h, kMaxH);
     if (opts->alpha.num < 0 || opts->alpha.den <= 0)
         return fail(MH_EINVAL, "alpha=%d/%d: need num >= 0 and den > 0", opts->alpha.num, opts->alpha.den);
-    if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
+    if (opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF && opts->prune != MH_PRUNE_BOUND)
         return fail(MH_EINVAL, "prune=%d is not a pruning mode", opts->prune);
     if (opts->mode != MH_MODE_PERSISTENT && opts->mode != MH_MODE_LAUNCHES)
         return fail(MH_EINVAL, "mode=%d is not an execution mode", opts->mode);
     int rc = ensure_workspace(H, h);
     if (rc) return rc;
-    if (opts->prune == MH_PRUNE_PAPER && (rc = presize_frontiers(H, h))) return rc;
+    if (opts->prune != MH_PRUNE_OFF && (rc = presize_frontiers(H, h))) return rc;
     s->h = h;
     s->prune = opts->prune;
     s->a_num = (u64)opts->alpha.num;
@@ -596,12 +599,15 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     s->slots = H->dSlots;
     s->nslots = H->ws_slots;
     s->cand = H->dCand;
-    s->champ = H->dChamp;
-    s->champ_ok = H->dChampOk;
-    s->ssum = H->dSsum;
+    // per-sample champions and sums serve paper pruning only
+    const bool paper = opts->prune == MH_PRUNE_PAPER;
+    s->champ = paper ? H->dChamp : nullptr;
+    s->champ_ok = paper ? H->dChampOk : nullptr;
+    s->ssum = paper ? H->dSsum : nullptr;
     s->gk = H->dGK;
     s->cov = H->dCov;
     s->run = H->dCov + H->c.WTp;
+    s->cut = H->dCut;
     s->work = H->dWork;
     s->best_hint = H->dWork + kWorkCount;
     *max_rounds = H->Nt + 1;
@@ -647,7 +653,8 @@ int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const 
     R->fp = (int32_t *)malloc(sizeof(int32_t) * (size_t)std::max(1, k));
     R->visited = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
     R->pruned = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)std::max(1, rounds * h));
-    if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned) {
+    R->cut = (uint64_t *)calloc((size_t)std::max(1, rounds * h), sizeof(uint64_t));
+    if (!R->genes || !R->tp || !R->fp || !R->visited || !R->pruned || !R->cut) {
         mh_result_free(R);
         return fail(MH_ENOMEM, "host allocation of the result failed");
     }
@@ -658,6 +665,8 @@ int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const 
     if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && rounds)
         e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && rounds)
+        e = cudaMemcpyAsync(R->cut, H->dCut, sizeof(u64) * (size_t)rounds * h, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -787,6 +796,7 @@ MH_API void mh_result_free(mh_result *r)
     free(r->fp);
     free(r->visited);
     free(r->pruned);
+    free(r->cut);
     free(r);
 }
 
@@ -872,6 +882,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                     return rc;
                 }
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
+                MH_CUDA(cudaMemsetAsync(H->dCut + (size_t)rounds_done * h, 0, sizeof(u64) * h, st));
                 MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountSets * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
                 continue;
@@ -935,6 +946,7 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
                 return rc;
             }
             MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)rounds_done * h * 2, 0, sizeof(u64) * 2 * h, st));
+                MH_CUDA(cudaMemsetAsync(H->dCut + (size_t)rounds_done * h, 0, sizeof(u64) * h, st));
             MH_CUDA(cudaMemsetAsync(counts, 0, sizeof(u32) * kCountSets * kCountWords, st));
             MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
             continue;
@@ -1280,6 +1292,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
                 int rc = grow_overflowed(H, opts[i].h, (const u32 *)(H->hState + kStateWords));
                 if (rc) return rc;
                 MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)r * opts[i].h * 2, 0, sizeof(u64) * 2 * opts[i].h, st));
+                MH_CUDA(cudaMemsetAsync(H->dCut + (size_t)r * opts[i].h, 0, sizeof(u64) * opts[i].h, st));
                 MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st));
                 MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
             }
@@ -1576,6 +1589,7 @@ struct mh_server {
                 rc = grow_overflowed(H, r->opts.h, hc.data());
                 if (rc == MH_OK) {
                     cudaMemsetAsync(H->dCnt + (size_t)st8[4] * r->opts.h * 2, 0, sizeof(u64) * 2 * r->opts.h, st);
+                    cudaMemsetAsync(H->dCut + (size_t)st8[4] * r->opts.h, 0, sizeof(u64) * r->opts.h, st);
                     cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st);
                     cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st);
                     cudaStreamSynchronize(st);

@@ -128,6 +128,7 @@ struct Solve {
     u32 *gk;
     u64 *cov;
     u64 *run;  // 2 (kMaxH + 1) words: running totals of the counter corrections (see mh_kernels.cu)
+    u64 *cut;  // score-bound mode: per round, per depth, the prefixes cut by the bound (nullptr: none)
 };
 
 constexpr int kCandidates = 32;

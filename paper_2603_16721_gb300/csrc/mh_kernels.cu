@@ -27,6 +27,7 @@
 // items of the batch's sparse prefixes are spread over the 32 lanes, so
 // neighbouring lanes read neighbouring column words; dense prefixes are taken by
 // the whole warp, one at a time.
+#include "mh.h"
 #include "mh_internal.h"
 
 namespace mh {
@@ -559,7 +560,8 @@ __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io,
                                              u32 cap_s, u64 first, u64 stride, int R, u32 count, int L, int hi_bound,
                                              bool all_children, Batch &b, int lane, unsigned &dense_mask,
                                              u64 &visited, int h, int single, const int *champ_ok, u64 &alive_cf,
-                                             u64 *deep, const u16 *orig = nullptr, bool fm = false)
+                                             u64 *deep, const u16 *orig = nullptr, bool fm = false,
+                                             u64 cut_thr = 0, u64 a_num = 0, u64 nn_term = 0, u64 *cutn = nullptr)
 {
     const u64 i = first + (u64)lane * stride;
     bool valid = lane < R && i < count;
@@ -598,7 +600,12 @@ __device__ __forceinline__ int batch_prepare(const Cohort &c, const RoundIO &io,
         hi = hi_bound;
         ky = b.r[lane].ky;
         kn = b.r[lane].kn;
-        if (single && ky == 1 && !is_dense(ky, kn) && hi >= lo &&
+        if (cutn && hi >= lo && ky > 0 && a_num * (u64)ky + nn_term < cut_thr) {
+            // score bound: every leaf below scores at most a_num |y| + a_den Nn, below
+            // a candidate already known, so the prefix is cut (nothing below is visited)
+            hi = lo - 1;
+            ++*cutn;
+        } else if (single && ky == 1 && !is_dense(ky, kn) && hi >= lo &&
             single_sample_closed(single, champ_ok, b.r[lane].ids[0])) {
             single_sample_count(c, h, L, lo - 1, b.r[lane].ids[0], visited, alive_cf, deep);
             hi = lo - 1;  // nothing left to search below this record
@@ -933,7 +940,7 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const F
             }
             continue;
         }
-        const bool keep = s.prune ? in : nonempty;
+        const bool keep = s.prune == MH_PRUNE_OFF ? in : nonempty;
         const u32 pos = warp_reserve(keep ? 1 : 0, my_count, lane);
         if (!keep || pos >= f.cap[1]) continue;
         Rec r;
@@ -1011,7 +1018,8 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     u32 *my_count = counts + shard_slot(level, my_shard(t));
     Rec *Fout = f.F[level] + (size_t)my_shard(t) * cap;
     const int hi_bound = c.G - s.h + level - 1;  // 0-based inclusive bound of this depth
-    const bool all_children = s.prune != 0;
+    const bool all_children = s.prune == MH_PRUNE_OFF;
+    u64 cutn = 0;  // prefixes cut by the score bound
     const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     u64 visited = 0, alive = 0;
     u64 leaf_vis = 0, leaf_alive = 0;  // closed-form leaves of single-sample children (level = h - 1)
@@ -1025,15 +1033,18 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
         // (with champions known, every sample whose champion is known qualifies: no
         // threshold needed)
         int single = 1;
-        if (!(s.champ && s.prune == 0 && c.CC)) {
-            u64 thr = 0;
+        u64 thr = 0;
+        if (!(s.champ && s.prune == MH_PRUNE_PAPER && c.CC)) {
             if (lane == 0) thr = *(volatile u64 *)io.hint;
-            single = single_sample_mode(c, s, __shfl_sync(kFull, thr, 0));
+            thr = __shfl_sync(kFull, thr, 0);
+            single = single_sample_mode(c, s, thr);
         }
         u64 alive_cf = 0;
         if (fm) single = 0;
+        const bool bound = s.prune == MH_PRUNE_BOUND;
         const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, hi_bound, all_children, b,
-                                        lane, dense, visited, h, single, s.champ_ok, alive_cf, deep, nullptr, fm);
+                                        lane, dense, visited, h, single, s.champ_ok, alive_cf, deep, nullptr, fm,
+                                        thr, s.a_num, s.a_den * (u64)c.Nn + 1, bound ? &cutn : nullptr);
         // sparse records: (record, column word) items spread over the lanes
         int j = 0;
         for (int tb = 0; tb < total; tb += 32 * kIlp) {
@@ -1146,6 +1157,8 @@ __device__ bool phase_expand(const Cohort &c, const Solve &s, int round, int lev
     alive = warp_sum_u64(alive);
     leaf_vis = warp_sum_u64(leaf_vis);
     leaf_alive = warp_sum_u64(leaf_alive);
+    cutn = warp_sum_u64(cutn);
+    if (lane == 0 && cutn && s.cut) atomicAdd(s.cut + (size_t)round * h + (L - 1), cutn);
     d1.visited = warp_sum_u64(d1.visited);
     d1.pruned = warp_sum_u64(d1.pruned);
     if (lane == 0) {
@@ -1210,7 +1223,7 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     Depth1 d1;
     const Rec *Fin = f.F[h - 1];
     const u32 cap_in = f.cap[h - 1];
-    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0;
+    u64 visited = 0, alive = 0, words = 0, prefixes = 0, scored = 0, dense_n = 0, cutn = 0;
     const u64 nn_term = s.a_den * (u64)c.Nn + 1;
     const u64 nw = (u64)t.size * (blockDim.x >> 5), gw = (u64)t.rank * (blockDim.x >> 5) + warp;
     Dispenser disp((u32)nw, (u32)gw, count, dispenser_counters(counts, h - 2));
@@ -1223,9 +1236,10 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
         u64 alive_cf = 0;
         // (with pruning off, the empty depth-1 nodes built here still have leaves)
         const int total = batch_prepare(c, io, d1, Fin, cap_in, first, nw, (int)disp.R, count, L, c.G - 1,
-                                        io.Ush != nullptr && s.prune != 0, b, lane, dense, visited, h,
+                                        io.Ush != nullptr && s.prune == MH_PRUNE_OFF, b, lane, dense, visited, h,
                                         single_sample_mode(c, s, thr), s.champ_ok, alive_cf, acc + kAccDeep,
-                                        c.orig);
+                                        c.orig, false, thr, s.a_num, nn_term,
+                                        s.prune == MH_PRUNE_BOUND ? &cutn : nullptr);
         alive += alive_cf;
         prefixes += (u64)(lane < (int)disp.R && first + (u64)lane * nw < count);
         int j = 0;
@@ -1292,6 +1306,8 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
     }
     visited = warp_sum_u64(visited);
     alive = warp_sum_u64(alive);
+    cutn = warp_sum_u64(cutn);
+    if (lane == 0 && cutn && s.cut) atomicAdd(s.cut + (size_t)round * h + (L - 1), cutn);
     words = warp_sum_u64(words);
     prefixes = warp_sum_u64(prefixes);
     scored = warp_sum_u64(scored);
@@ -2616,18 +2632,18 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     }
     __syncthreads();
     if (h > 1 && t.rank == 0) block_rescore(c, s, cand_sh, Ush, s.best_hint + (round & 1));
-    if (h > 1 && round == 0 && s.prune == 0 && c.CC) {
+    if (h > 1 && round == 0 && s.prune != MH_PRUNE_OFF && c.CC) {
         // the champions and the first round's threshold, complete before any block
         // starts searching
-        if (s.champ) phase_champions(c, s, t, b);
-        if (s.ssum) phase_sample_sums(c, s, t);
+        if (s.champ && s.prune == MH_PRUNE_PAPER) phase_champions(c, s, t, b);
+        if (s.ssum && s.prune == MH_PRUNE_PAPER) phase_sample_sums(c, s, t);
         block_seed(c, s, t, Ush, s.best_hint);
         if (!grid_sync(gsync, s.state, t.size)) return;
     }
     // counting by per-sample sums when every tumor's champion is known (the
     // champions stand for the TP = 1 leaves that this mode never visits)
     bool fm = false;
-    if (h > 1 && s.prune == 0 && c.CC && s.champ && s.ssum) {
+    if (h > 1 && s.prune == MH_PRUNE_PAPER && c.CC && s.champ && s.ssum) {
         if (threadIdx.x == 0) fm_sh = 1;
         __syncthreads();
         for (int i = threadIdx.x; i < c.Nt; i += blockDim.x)
@@ -2828,6 +2844,7 @@ void launch_solve_init(const Cohort &c, const Solve &s, int counter_rounds, int 
                        cudaStream_t st)
 {
     cudaMemsetAsync(s.cnt, 0, sizeof(u64) * 2 * (size_t)s.h * (size_t)counter_rounds, st);
+    if (s.cut) cudaMemsetAsync(s.cut, 0, sizeof(u64) * (size_t)s.h * (size_t)counter_rounds, st);
     cudaMemsetAsync(s.slots, 0, sizeof(Key) * (size_t)s.nslots * sets, st);
     cudaMemsetAsync(s.cand, 0, sizeof(Key) * (size_t)kCandidates, st);
     cudaMemsetAsync(s.work, 0, sizeof(u64) * kWorkCount, st);

@@ -20,7 +20,7 @@ import numpy as np
 from . import _build
 
 MH_OK, MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT, MH_EAGAIN, MH_EREJECT = range(7)
-MH_PRUNE_PAPER, MH_PRUNE_OFF = 0, 1
+MH_PRUNE_PAPER, MH_PRUNE_OFF, MH_PRUNE_BOUND = 0, 1, 2
 MH_MODE_PERSISTENT, MH_MODE_LAUNCHES = 0, 1
 _NAMES = {0: "MH_OK", 1: "MH_EINVAL", 2: "MH_ENOMEM", 3: "MH_ECUDA", 4: "MH_ETIMEOUT", 5: "MH_EAGAIN",
           6: "MH_EREJECT"}
@@ -55,7 +55,8 @@ class mh_result(ctypes.Structure):
                 ("leaf_prefixes", ctypes.c_uint64), ("leaf_scored", ctypes.c_uint64),
                 ("leaf_alu_ops", ctypes.c_uint64), ("leaf_dense", ctypes.c_uint64),
                 ("level1_ms", ctypes.c_double), ("expand_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
-                ("mode", ctypes.c_int32), ("diag", ctypes.c_uint64 * 8), ("kernel_ms", ctypes.c_double)]
+                ("mode", ctypes.c_int32), ("diag", ctypes.c_uint64 * 8), ("kernel_ms", ctypes.c_double),
+                ("cut", ctypes.POINTER(ctypes.c_uint64))]
 
 
 _lib = None
@@ -156,6 +157,7 @@ class Result:
     mode: int = 0
     diag: tuple = ()
     kernel_ms: float = 0.0
+    cut: np.ndarray = None    # [rounds, h] prefixes cut by the score bound (MH_PRUNE_BOUND)
 
     @property
     def k(self) -> int:
@@ -183,7 +185,9 @@ def _to_result(p) -> Result:
                  leaf_prefixes=int(r.leaf_prefixes), leaf_scored=int(r.leaf_scored),
                  leaf_alu_ops=int(r.leaf_alu_ops), leaf_dense=int(r.leaf_dense),
                  level1_ms=float(r.level1_ms), expand_ms=float(r.expand_ms), finalize_ms=float(r.finalize_ms),
-                 mode=int(r.mode), diag=tuple(int(x) for x in r.diag), kernel_ms=float(r.kernel_ms))
+                 mode=int(r.mode), diag=tuple(int(x) for x in r.diag), kernel_ms=float(r.kernel_ms),
+                 cut=(arr(r.cut, rounds * h, np.uint64).reshape(rounds, h) if r.cut
+                      else np.zeros((rounds, h), np.uint64)))
     load().mh_result_free(p)
     return out
 

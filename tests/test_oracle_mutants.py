@@ -54,7 +54,9 @@ def _compile(src_text, out_dir, name):
     so = os.path.join(out_dir, f"{name}.so")
     with open(c, "w") as f:
         f.write(src_text)
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", so, c])
+    # the threaded P-DFS is linked in unchanged: the binding loads its symbols too
+    mt = os.path.join(os.path.dirname(oracle.__file__), "pdfs_mt.c")
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", "-o", so, c, mt])
     return so
 
 
