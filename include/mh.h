@@ -298,6 +298,52 @@ MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, in
  * Errors: MH_EINVAL (bad op or NULL ops_per_s), MH_ECUDA. */
 MH_API int mh_int_peak(int32_t op, double *ops_per_s, double *kernel_ms);
 
+/* ---- Split search: one solve divided over processes --------------------------
+ * The paper runs each greedy round's search over many workers by handing out the
+ * lambda units of the search (§III-E) and reducing their best candidates; here a
+ * process (a rank, e.g. one per GPU) searches the depth-1 genes g of its shard
+ * (g % nshards == shard, in the sparsity order of §III-C) and the caller merges
+ * the shards' results between rounds.  Per round, every rank calls
+ * mh_shard_search, exchanges its mh_round_best with the others (an all-gather of
+ * a few hundred bytes), merges them -- the winner is the candidate with the
+ * largest score, ties to the smallest ascending tuple of original indices
+ * (§III-D); the counters are summed (modulo 2^64) -- and calls mh_shard_commit
+ * with the same merged value, which applies the winner (DelCols, Algorithm 1)
+ * identically on every rank.  The selections and summed counters equal those of
+ * mh_solve_ex in MH_MODE_LAUNCHES.  Runs the one-kernel-per-phase path on the
+ * handle's stream; each call is synchronous.  A handle serves one split search
+ * at a time and no other solve meanwhile. */
+typedef struct mh_shard mh_shard;
+typedef struct {
+    int32_t done;               /* search: 1 if the solve has ended (nothing was searched) */
+    int32_t have;               /* 1 if there is a candidate (search: in this shard; commit: a winner) */
+    int64_t score;              /* S = alpha.num * TP + alpha.den * (Nn - FP) of the candidate */
+    int32_t genes[MH_MAX_H];    /* its original gene indices, ascending (the first h are used) */
+    uint64_t visited[MH_MAX_H]; /* the round's counters per depth: this shard's share from search; */
+    uint64_t pruned[MH_MAX_H];  /* the sums over all shards for commit */
+} mh_round_best;
+
+/* Starts the split search of one solve on handle H: opts as for mh_solve_ex (prune
+ * MH_PRUNE_PAPER or MH_PRUNE_OFF; mode is ignored), shard in [0, nshards).
+ * Errors: MH_EINVAL, MH_ENOMEM, MH_ECUDA. */
+MH_API int mh_shard_begin(mh_handle *H, const mh_solve_opts *opts, int32_t shard, int32_t nshards, mh_shard **out);
+
+/* Searches the current round on this shard (growing a frontier and rerunning the
+ * round when one overflows).  *out: have / score / genes of the shard's best
+ * candidate and its share of the round's counters; done = 1 once the solve has
+ * ended.  Errors: MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT. */
+MH_API int mh_shard_search(mh_shard *X, mh_round_best *out);
+
+/* Applies the merged round (the winner, or have = 0 to end the solve, and the
+ * summed counters) and advances to the next round; *done (may be NULL) becomes 1
+ * when the solve has ended.  Every shard must commit the same merged value. */
+MH_API int mh_shard_commit(mh_shard *X, const mh_round_best *merged, int32_t *done);
+
+/* The solve's result so far (selections, merged counters), as from mh_solve_ex. */
+MH_API int mh_shard_result(mh_shard *X, mh_result **out);
+
+MH_API void mh_shard_free(mh_shard *X);
+
 /* Cohort dimensions of a handle (any pointer may be NULL). */
 MH_API int mh_handle_info(const mh_handle *handle, int32_t *G, int32_t *Nt, int32_t *Nn,
                           int64_t *device_bytes);

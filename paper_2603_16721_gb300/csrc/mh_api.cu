@@ -608,6 +608,9 @@ int prepare_solve(mh_handle *H, const mh_solve_opts *opts, Solve *s, int *max_ro
     s->cov = H->dCov;
     s->run = H->dCov + H->c.WTp;
     s->cut = H->dCut;
+    s->shard = 0;
+    s->nshards = 1;
+    s->xbest = nullptr;
     s->work = H->dWork;
     s->best_hint = H->dWork + kWorkCount;
     *max_rounds = H->Nt + 1;
@@ -1847,6 +1850,196 @@ MH_API void mh_server_destroy(mh_server *S)
     if (S->st) cudaStreamDestroy(S->st);
     if (S->st_up) cudaStreamDestroy(S->st_up);
     delete S;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Split search: one greedy solve divided over processes by depth-1 genes (the
+// lambda units of §III-E), each process searching its share of every round and
+// applying the winner merged over all of them.  Runs the one-kernel-per-phase
+// path; the merge (largest key, summed counters) is the caller's.
+
+struct mh_shard {
+    mh_handle *H = nullptr;
+    mh_solve_opts opts{};
+    Solve s{};
+    int max_rounds = 0;
+    int64_t launches = 0, leaf_launches = 0;
+    Key *dX = nullptr;  // xbest[0] (the shard's best), xbest[1] (the merged winner)
+    bool done = false;
+};
+
+namespace {
+
+Key pack_round_key(const mh_round_best *rb, int h)
+{
+    Key k;
+    memset(&k, 0, sizeof k);
+    if (!rb->have) return k;
+    k.s = (u64)rb->score + 1;
+    for (int i = 0; i < h; ++i) {
+        const u64 x = (u64)(u16)rb->genes[i] << (16 * (3 - (i & 3)));
+        if (i < 4) k.t0 |= x;
+        else if (i < 8) k.t1 |= x;
+        else k.t2 |= x;
+    }
+    return k;
+}
+
+int shard_state(mh_shard *X, int *hs)
+{
+    mh_handle *H = X->H;
+    MH_CUDA(cudaMemcpyAsync(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost, H->stream));
+    MH_CUDA(cudaMemcpyAsync(H->hState + kStateWords, H->dCounts, sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost,
+                            H->stream));
+    MH_CUDA(cudaStreamSynchronize(H->stream));
+    memcpy(hs, H->hState, sizeof(int) * kStateWords);
+    return MH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+MH_API int mh_shard_begin(mh_handle *H, const mh_solve_opts *opts, int32_t shard, int32_t nshards, mh_shard **out)
+{
+    if (!out) return fail(MH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nshards < 1 || shard < 0 || shard >= nshards)
+        return fail(MH_EINVAL, "shard %d of %d: need 0 <= shard < nshards", shard, nshards);
+    if (opts && opts->prune != MH_PRUNE_PAPER && opts->prune != MH_PRUNE_OFF)
+        return fail(MH_EINVAL, "split search: prune must be MH_PRUNE_PAPER or MH_PRUNE_OFF");
+    mh_shard *X = new (std::nothrow) mh_shard();
+    if (!X) return fail(MH_ENOMEM, "host allocation of the split search failed");
+    X->H = H;
+    if (opts) X->opts = *opts;
+    X->opts.mode = MH_MODE_LAUNCHES;
+    int rc = prepare_solve(H, &X->opts, &X->s, &X->max_rounds);
+    if (!rc) rc = dalloc(&X->dX, 2, &H->device_bytes, H->dev, H->stream);
+    if (rc) {
+        delete X;
+        return rc;
+    }
+    X->s.champ = nullptr;  // one kernel per phase: no per-sample champions, no sums
+    X->s.champ_ok = nullptr;
+    X->s.ssum = nullptr;
+    X->s.shard = shard;
+    X->s.nshards = nshards;
+    X->s.xbest = X->dX;
+    launch_solve_init(H->c, X->s, H->ws_rounds, X->max_rounds, H->dCounts, kCountSets, H->stream);
+    ++X->launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        dfree(X->dX, H->stream);
+        delete X;
+        return fail(MH_ECUDA, "starting the split search: %s", cudaGetErrorString(e));
+    }
+    X->done = H->Nt == 0;
+    *out = X;
+    return MH_OK;
+}
+
+MH_API int mh_shard_search(mh_shard *X, mh_round_best *out)
+{
+    if (!X || !out) return fail(MH_EINVAL, "shard or out is NULL");
+    memset(out, 0, sizeof *out);
+    if (X->done) {
+        out->done = 1;
+        return MH_OK;
+    }
+    mh_handle *H = X->H;
+    const int h = X->opts.h;
+    cudaStream_t st = H->stream;
+    int hs[kStateWords];
+    for (;;) {  // one round of this shard; rerun after growing an overflowed frontier
+        const Frontiers fl = frontiers_of(H);
+        launch_level1(H->c, X->s, fl, H->dCounts, st);
+        for (int l = 2; l <= h - 1; ++l) launch_expand(H->c, X->s, l, fl, H->dCounts, leaf_grid(H), st);
+        if (h >= 2) {
+            launch_leaf(H->c, X->s, fl, H->dCounts, leaf_grid(H), st);
+            ++X->leaf_launches;
+        }
+        launch_finalize_split(H->c, X->s, H->dCounts, 1, st);
+        X->launches += 2 + (h >= 2 ? 1 : 0) + std::max(0, h - 2);
+        MH_CUDA(cudaGetLastError());
+        int rc = shard_state(X, hs);
+        if (rc) return rc;
+        if (hs[2]) return fail(MH_ETIMEOUT, "a bounded wait of the split search timed out");
+        if (!hs[3]) break;
+        const int r = hs[4];
+        if ((rc = grow_overflowed(H, h, (const u32 *)(H->hState + kStateWords)))) return rc;
+        MH_CUDA(cudaMemsetAsync(H->dCnt + (size_t)r * h * 2, 0, sizeof(u64) * 2 * h, st));
+        MH_CUDA(cudaMemsetAsync(H->dCut + (size_t)r * h, 0, sizeof(u64) * h, st));
+        MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st));
+        MH_CUDA(cudaMemsetAsync(H->dState + 3, 0, sizeof(int), st));
+    }
+    const int r = hs[4];
+    Key k;
+    std::vector<u64> cnt((size_t)2 * h);
+    MH_CUDA(cudaMemcpyAsync(&k, X->dX, sizeof(Key), cudaMemcpyDeviceToHost, st));
+    MH_CUDA(cudaMemcpyAsync(cnt.data(), H->dCnt + (size_t)r * h * 2, sizeof(u64) * 2 * h, cudaMemcpyDeviceToHost,
+                            st));
+    MH_CUDA(cudaStreamSynchronize(st));
+    out->have = k.s != 0;
+    if (k.s) {
+        out->score = (int64_t)(k.s - 1);
+        for (int i = 0; i < h; ++i) {
+            const u64 w = i < 4 ? k.t0 : (i < 8 ? k.t1 : k.t2);
+            out->genes[i] = (int32_t)((w >> (16 * (3 - (i & 3)))) & 0xffffull);
+        }
+    }
+    for (int l = 0; l < h; ++l) {
+        out->visited[l] = cnt[(size_t)l * 2];
+        out->pruned[l] = cnt[(size_t)l * 2 + 1];
+    }
+    return MH_OK;
+}
+
+MH_API int mh_shard_commit(mh_shard *X, const mh_round_best *merged, int32_t *done)
+{
+    if (!X || !merged) return fail(MH_EINVAL, "shard or merged is NULL");
+    if (X->done) {
+        if (done) *done = 1;
+        return MH_OK;
+    }
+    mh_handle *H = X->H;
+    const int h = X->opts.h;
+    cudaStream_t st = H->stream;
+    int hs[kStateWords];
+    int rc = shard_state(X, hs);
+    if (rc) return rc;
+    const int r = hs[4];
+    const Key k = pack_round_key(merged, h);
+    std::vector<u64> cnt((size_t)2 * h);
+    for (int l = 0; l < h; ++l) {
+        cnt[(size_t)l * 2] = merged->visited[l];
+        cnt[(size_t)l * 2 + 1] = merged->pruned[l];
+    }
+    MH_CUDA(cudaMemcpyAsync(X->dX + 1, &k, sizeof(Key), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dCnt + (size_t)r * h * 2, cnt.data(), sizeof(u64) * 2 * h, cudaMemcpyHostToDevice,
+                            st));
+    launch_finalize_split(H->c, X->s, H->dCounts, 2, st);
+    ++X->launches;
+    MH_CUDA(cudaGetLastError());
+    if ((rc = shard_state(X, hs))) return rc;
+    X->done = hs[1] != 0 || hs[4] >= X->max_rounds;
+    if (done) *done = X->done ? 1 : 0;
+    return MH_OK;
+}
+
+MH_API int mh_shard_result(mh_shard *X, mh_result **out)
+{
+    if (!X || !out) return fail(MH_EINVAL, "shard or out is NULL");
+    *out = nullptr;
+    return collect_result(X->H, X->opts.h, false, 0.0, nullptr, X->launches, X->leaf_launches, out);
+}
+
+MH_API void mh_shard_free(mh_shard *X)
+{
+    if (!X) return;
+    dfree(X->dX, X->H->stream);
+    delete X;
 }
 
 }  // extern "C"

@@ -129,6 +129,11 @@ struct Solve {
     u64 *cov;
     u64 *run;  // 2 (kMaxH + 1) words: running totals of the counter corrections (see mh_kernels.cu)
     u64 *cut;  // score-bound mode: per round, per depth, the prefixes cut by the bound (nullptr: none)
+    // Split search (one kernel per phase only): this solve searches the depth-1
+    // genes g (search order) with g % nshards == shard; xbest[0] receives the
+    // shard's best key of a round, xbest[1] holds the winner merged over all shards.
+    int shard, nshards;
+    Key *xbest;
 };
 
 constexpr int kCandidates = 32;
@@ -192,6 +197,9 @@ void launch_expand(const Cohort &c, const Solve &s, int level, const Frontiers &
                    cudaStream_t st);
 void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *counts, int grid, cudaStream_t st);
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st);
+// Split search: step 1 reduces the round's blocks to the shard's best key (xbest[0]),
+// step 2 applies the merged winner xbest[1] (DelCols, selection, next round).
+void launch_finalize_split(const Cohort &c, const Solve &s, u32 *counts, int step, cudaStream_t st);
 
 // Persistent solve: all rounds in one cooperative launch of `grid` blocks
 // (persistent_grid(): one block per SM for the default build, the co-resident

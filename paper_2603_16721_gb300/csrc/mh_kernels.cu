@@ -916,7 +916,7 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const F
     Key best = key_empty();
     for (int base = t.rank * blockDim.x; base < c.G; base += t.size * blockDim.x) {
         const int g = base + threadIdx.x;
-        const bool in = g <= last;
+        const bool in = g <= last && (s.nshards <= 1 || g % s.nshards == s.shard);  // split search: my genes
         int ky = 0;
         if (in) {
             const u64 *row = c.T + (size_t)g * c.WTp;
@@ -1344,13 +1344,16 @@ __device__ bool phase_leaf(const Cohort &c, const Solve &s, int round, const Fro
 // candidates for the next round's threshold, reset the frontier counters and
 // advance the round; raise the done flag when nothing was found, every tumor is
 // covered or the round limit is reached.  Every thread of the block must call it.
-__device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int nslots)
+// step (split search only): 1 = stop after the reduction, writing the shard's best
+// key to xbest[0]; 2 = skip the reduction and apply the merged winner xbest[1].
+__device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int nslots, int step = 0)
 {
     __shared__ Key wbest[kMaxWarpsPerBlock];
     __shared__ int gs[kMaxH], os[kMaxH];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     Key best = key_empty();
+    if (step == 2) nslots = 0;
     for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
         Key k;
         k.s = __ldcg(&s.slots[i].s);
@@ -1370,22 +1373,32 @@ __device__ void phase_finalize(const Cohort &c, const Solve &s, u32 *counts, int
         if (m.s != 0 && mine.s == m.s && mine.t0 == m.t0 && mine.t1 == m.t1 && mine.t2 == m.t2) mine = key_empty();
         if (r == 0 && lane == 0) wbest[warp] = m;
     }
-    for (int i = threadIdx.x; i < kMaxH * kShards; i += blockDim.x) counts[i * kShardStride] = 0;
+    if (step != 2)
+        for (int i = threadIdx.x; i < kMaxH * kShards; i += blockDim.x) counts[i * kShardStride] = 0;
     __syncthreads();
     if (warp == 0) {
         best = lane < nwarps ? wbest[lane] : key_empty();
         best = warp_max_key(best);
+        if (step == 1 && lane == 0) s.xbest[0] = best;  // the shard's best; the round goes on
+        if (step == 2) {
+            best.s = __ldcg(&s.xbest[1].s);
+            best.t0 = __ldcg(&s.xbest[1].t0);
+            best.t1 = __ldcg(&s.xbest[1].t1);
+            best.t2 = __ldcg(&s.xbest[1].t2);
+        }
         const int round = *(volatile int *)&s.state[kStRound];
         const bool last_round = round + 1 >= *(volatile int *)&s.state[kStMaxRounds];
-        if (lane == 0) {
+        if (step == 1) best = key_empty();  // nothing is applied in step 1
+        if (lane == 0 && step != 1) {
             *(volatile u64 *)s.best_hint = 0;
             s.state[kStRound] = round + 1;
         }
-        if (lane < 2) {  // diagnostics: the round's longest warps
+        if (lane < 2 && step != 1) {  // diagnostics: the round's longest warps
             s.work[kWorkWarpMaxSum + lane] += __ldcg(&s.work[kWorkWarpMax + lane]);
             s.work[kWorkWarpMax + lane] = 0;
         }
-        if (best.s == 0) {
+        if (step == 1) {
+        } else if (best.s == 0) {
             if (lane == 0) s.state[kStDone] = 1;
         } else {
             if (lane < h) {
@@ -1489,6 +1502,13 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const __grid_constant__ C
 {
     if (halted(s)) return;
     phase_finalize(c, s, counts, s.nslots);
+}
+
+__global__ void __launch_bounds__(kThreads) k_finalize_split(const __grid_constant__ Cohort c,
+                                                             const __grid_constant__ Solve s, u32 *counts, int step)
+{
+    if (halted(s)) return;
+    phase_finalize(c, s, counts, s.nslots, step);
 }
 
 // ---------------------------------------------------------------------------
@@ -2874,6 +2894,11 @@ void launch_leaf(const Cohort &c, const Solve &s, const Frontiers &f, u32 *count
 void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t st)
 {
     k_finalize<<<1, kThreads, 0, st>>>(c, s, counts);
+}
+
+void launch_finalize_split(const Cohort &c, const Solve &s, u32 *counts, int step, cudaStream_t st)
+{
+    k_finalize_split<<<1, kThreads, 0, st>>>(c, s, counts, step);
 }
 
 int persistent_grid(int num_sms, bool large)

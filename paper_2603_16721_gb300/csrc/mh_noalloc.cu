@@ -244,6 +244,9 @@ extern "C" MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int
     s.cov = nullptr;
     s.run = nullptr;
     s.cut = nullptr;
+    s.shard = 0;
+    s.nshards = 1;
+    s.xbest = nullptr;
     const int leaf_blocks = num_sms * 4;
     s.nslots = level1_grid(c) > leaf_blocks ? level1_grid(c) : leaf_blocks;
     if (s.nslots > kNaMaxSlots) return na_fail(MH_EINVAL, "mh_solve_noalloc: %d SMs exceed the slot array", num_sms);

@@ -112,6 +112,73 @@ def mh_check_bounded_wait() -> int:
     return int(st.value)
 
 
+class mh_round_best(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("have", ctypes.c_int32), ("score", ctypes.c_int64),
+                ("genes", ctypes.c_int32 * 9), ("visited", ctypes.c_uint64 * 9), ("pruned", ctypes.c_uint64 * 9)]
+
+
+class Shard:
+    """One rank's share of a split solve (``mh_shard_*``): search a round, commit the
+    merged round, read the result.  Closed with ``mh_shard_free``."""
+
+    def __init__(self, handle: "Handle", h: int, alpha=(1, 10), shard: int = 0, nshards: int = 1,
+                 prune: int = MH_PRUNE_PAPER):
+        lib = load()
+        lib.mh_shard_begin.restype = ctypes.c_int
+        lib.mh_shard_begin.argtypes = [_P, ctypes.POINTER(mh_solve_opts), ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(_P)]
+        lib.mh_shard_search.restype = ctypes.c_int
+        lib.mh_shard_search.argtypes = [_P, ctypes.POINTER(mh_round_best)]
+        lib.mh_shard_commit.restype = ctypes.c_int
+        lib.mh_shard_commit.argtypes = [_P, ctypes.POINTER(mh_round_best), ctypes.POINTER(ctypes.c_int32)]
+        lib.mh_shard_result.restype = ctypes.c_int
+        lib.mh_shard_result.argtypes = [_P, ctypes.POINTER(ctypes.POINTER(mh_result))]
+        lib.mh_shard_free.restype = None
+        lib.mh_shard_free.argtypes = [_P]
+        self.h = h
+        opts = mh_solve_opts(h=h, alpha=mh_rational(*alpha), prune=prune, mode=MH_MODE_LAUNCHES)
+        p = _P()
+        _check(lib.mh_shard_begin(handle.ptr, ctypes.byref(opts), shard, nshards, ctypes.byref(p)))
+        self.ptr = p
+
+    def search(self) -> dict:
+        rb = mh_round_best()
+        _check(load().mh_shard_search(self.ptr, ctypes.byref(rb)))
+        h = self.h
+        return {"done": bool(rb.done), "have": bool(rb.have), "score": int(rb.score),
+                "genes": tuple(int(g) for g in rb.genes[:h]),
+                "visited": np.array(rb.visited[:h], dtype=np.uint64), "pruned": np.array(rb.pruned[:h], dtype=np.uint64)}
+
+    def commit(self, merged: dict) -> bool:
+        rb = mh_round_best()
+        rb.have = int(bool(merged["have"]))
+        rb.score = int(merged["score"])
+        for i, g in enumerate(merged["genes"]):
+            rb.genes[i] = int(g)
+        for i in range(self.h):
+            rb.visited[i] = int(merged["visited"][i])
+            rb.pruned[i] = int(merged["pruned"][i])
+        done = ctypes.c_int32(0)
+        _check(load().mh_shard_commit(self.ptr, ctypes.byref(rb), ctypes.byref(done)))
+        return bool(done.value)
+
+    def result(self) -> "Result":
+        out = ctypes.POINTER(mh_result)()
+        _check(load().mh_shard_result(self.ptr, ctypes.byref(out)))
+        return _to_result(out)
+
+    def close(self):
+        if self.ptr:
+            load().mh_shard_free(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def mh_int_peak(op: int = 0):
     """Measured integer throughput of the current GPU: (thread ops/s, kernel ms) of
     op 0 = LOP3, 1 = POPC, 2 = IADD."""

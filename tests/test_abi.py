@@ -79,7 +79,7 @@ def _c_layout(tmp_path, struct, fields):
 
 
 @pytest.mark.parametrize("struct,cls", [("mh_result", "mh_result"), ("mh_solve_opts", "mh_solve_opts"),
-                                        ("mh_server_opts", "mh_server_opts")])
+                                        ("mh_server_opts", "mh_server_opts"), ("mh_round_best", "mh_round_best")])
 def test_binding_structs_match_header_layout(tmp_path, struct, cls):
     c = getattr(mh, cls)
     names = [f[0] for f in c._fields_]
