@@ -46,6 +46,7 @@ extern "C" {
 #define MH_ETIMEOUT 4 /* a bounded device-side wait expired; the kernel returned early */
 #define MH_EAGAIN 5   /* the result is not ready yet (served mode) */
 #define MH_EREJECT 6  /* a request does not fit the server's memory budget */
+#define MH_ECANCELED 7 /* a served request was cancelled (mh_cancel) */
 
 #define MH_MAX_H 9
 
@@ -232,6 +233,8 @@ typedef struct {
                                  admitted at a time, run batched together; <= 0: 2.  Large
                                  requests start in arrival order; smaller ones queued behind a
                                  waiting large one may start first (backfill) */
+    int32_t large_wait_ms;    /* an admitted large request paused longer than this (while small
+                                 ones run) joins the next launch with them; <= 0: 250 */
 } mh_server_opts;
 
 /* Starts a server on the current device.  opts may be NULL (defaults).
@@ -251,6 +254,22 @@ MH_API int mh_poll(mh_server *server, uint64_t ticket, mh_result **out);
 
 /* As mh_poll, waiting up to timeout_ms (< 0: without limit); MH_EAGAIN on timeout. */
 MH_API int mh_wait(mh_server *server, uint64_t ticket, int32_t timeout_ms, mh_result **out);
+
+/* Cancels a request: a queued one completes at once with MH_ECANCELED; an admitted
+ * one is retired at its next round boundary (the running launch is asked to end
+ * there) and completes with MH_ECANCELED; a finished one keeps its result.  The
+ * ticket stays valid until mh_poll / mh_wait returns its status.  Errors:
+ * MH_EINVAL (unknown ticket). */
+MH_API int mh_cancel(mh_server *server, uint64_t ticket);
+
+/* Diagnostic (no counterpart in the paper): host-side fault injection for tests of
+ * the error paths.  spec: "alloc_fail=N" -- the N-th next device allocation of the
+ * library fails (MH_ENOMEM); "timeout_after=N" -- the N-th next persistent solve
+ * reports MH_ETIMEOUT as if a bounded device wait had expired (after its kernel has
+ * run normally); "none" or NULL clears both.  The environment variable MH_FAULT
+ * takes the same specs and is read at the first allocation or solve.  Nothing is
+ * injected on the device.  Errors: MH_EINVAL (unknown spec). */
+MH_API int mh_set_fault(const char *spec);
 
 /* Launches made so far, queued and active requests, device bytes reserved. */
 MH_API int mh_server_stats(mh_server *server, int64_t *launches, int32_t *queued, int32_t *active,
@@ -343,6 +362,25 @@ MH_API int mh_shard_commit(mh_shard *X, const mh_round_best *merged, int32_t *do
 MH_API int mh_shard_result(mh_shard *X, mh_result **out);
 
 MH_API void mh_shard_free(mh_shard *X);
+
+/* ---- Coverage evaluation (§IV-D, Tables III and IV) ----------------------------
+ * The paper freezes the combinations learned on a training split and measures
+ * their coverage on a held-out split: a sample is covered when it carries every
+ * gene of at least one combination (the coverage of Eq. 1).  TC / NC: covered
+ * tumor / normal samples; TT / NT: all of them; sensitivity = TC / TT,
+ * specificity = 1 - NC / NT (0 when the total is 0). */
+typedef struct {
+    int32_t tc, tt, nc, nt;
+    double sensitivity, specificity;
+} mh_coverage;
+
+/* Coverage of k combinations (HOST array genes of k*h original gene indices of the
+ * handle's cohort) on the handle's samples, computed on the device.  The optional
+ * HOST buffers tumor_covered (Wt words) and normal_covered (Wn words) receive the
+ * covered samples as bit masks (layout of the packed rows).  Errors: MH_EINVAL (NULL
+ * out, h outside [1, 9], an index outside [0, G)), MH_ENOMEM, MH_ECUDA. */
+MH_API int mh_evaluate(mh_handle *H, const int32_t *genes, int32_t k, int32_t h, mh_coverage *out,
+                       uint64_t *tumor_covered, uint64_t *normal_covered);
 
 /* Cohort dimensions of a handle (any pointer may be NULL). */
 MH_API int mh_handle_info(const mh_handle *handle, int32_t *G, int32_t *Nt, int32_t *Nn,

@@ -270,3 +270,24 @@ def delcols(bitmaps, G, Nt, Nn, genes, U) -> np.ndarray:
     _check(_load().pdfs_mt_delcols(bm.ctypes.data, G, Nt, Nn, t.size, t.ctypes.data, out.ctypes.data),
            "pdfs_mt_delcols")
     return out
+
+
+def coverage(bitmaps, G, Nt, Nn, combos) -> dict:
+    """Coverage of combinations on a cohort's samples, the evaluation of §IV-D
+    (Tables III and IV): a sample is covered when it carries every gene of at
+    least one combination.  TC / NC = covered tumors / normals, TT / NT = all of
+    them, sensitivity = TC / TT, specificity = 1 - NC / NT (0.0 for an empty total)."""
+    bm = _prep(bitmaps, G, Nt, Nn)
+    Wt = (Nt + 63) // 64
+    T = np.unpackbits(np.ascontiguousarray(bm[:, :Wt]).view(np.uint8), bitorder="little", axis=1)[:, :Nt] != 0
+    N = np.unpackbits(np.ascontiguousarray(bm[:, Wt:]).view(np.uint8), bitorder="little", axis=1)[:, :Nn] != 0
+    tcov = np.zeros(Nt, dtype=bool)
+    ncov = np.zeros(Nn, dtype=bool)
+    for row in np.asarray(combos, dtype=np.int64).reshape(-1, np.asarray(combos).shape[-1] if np.size(combos) else 1):
+        if row.size == 0:
+            continue
+        tcov |= T[row].all(axis=0)
+        ncov |= N[row].all(axis=0)
+    tc, nc = int(tcov.sum()), int(ncov.sum())
+    return {"tc": tc, "tt": Nt, "nc": nc, "nt": Nn, "sensitivity": tc / Nt if Nt else 0.0,
+            "specificity": 1.0 - nc / Nn if Nn else 0.0, "tumor_covered": tcov, "normal_covered": ncov}

@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <sstream>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -100,11 +101,50 @@ size_t frontier_budget(int dev = -1)
 }
 
 // n elements from the device's pool, ordered on stream st.
+// Host-side fault injection (mh_set_fault, or MH_FAULT in the environment at the
+// first call): the n-th next device allocation fails, or the n-th next solve
+// reports that a bounded device wait expired.  Nothing is injected on the device.
+std::atomic<int> g_fault_alloc{0}, g_fault_timeout{0};
+std::atomic<int> g_fault_env_read{0};
+
+int parse_fault(const char *spec)
+{
+    if (!spec || !*spec || !strcmp(spec, "none")) {
+        g_fault_alloc = 0;
+        g_fault_timeout = 0;
+        return MH_OK;
+    }
+    int n = 0;
+    if (sscanf(spec, "alloc_fail=%d", &n) == 1 && n > 0) {
+        g_fault_alloc = n;
+        return MH_OK;
+    }
+    if (sscanf(spec, "timeout_after=%d", &n) == 1 && n > 0) {
+        g_fault_timeout = n;
+        return MH_OK;
+    }
+    return fail(MH_EINVAL, "fault spec '%s': expected none, alloc_fail=N or timeout_after=N (N >= 1)", spec);
+}
+
+// Counts an armed fault down; true when it fires.
+bool fault_fires(std::atomic<int> &f)
+{
+    if (!g_fault_env_read.exchange(1)) {
+        const char *env = getenv("MH_FAULT");
+        if (env && *env) parse_fault(env);
+    }
+    int v = f.load();
+    while (v > 0 && !f.compare_exchange_weak(v, v - 1)) {
+    }
+    return v == 1;
+}
+
 template <typename T>
 int dalloc(T **p, size_t n, int64_t *acct, int dev, cudaStream_t st)
 {
     *p = nullptr;
     if (n == 0) n = 1;
+    if (fault_fires(g_fault_alloc)) return fail(MH_ENOMEM, "injected device allocation failure (mh_set_fault)");
     cudaMemPool_t pool;
     const int rc = device_pool(dev, &pool);
     if (rc) return rc;
@@ -472,18 +512,17 @@ int ensure_workspace(mh_handle *H, int h)
     int rc;
     const int dev = H->dev;
     cudaStream_t st = H->stream;
-    if (!H->dU) {
-        if ((rc = dalloc(&H->dU, (size_t)H->c.WTp, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dState, (size_t)kStateWords, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dWork, (size_t)kWorkCount + 2, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dCounts, (size_t)kCountSets * kCountWords, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dCand, (size_t)kCandidates, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dChamp, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dChampOk, (size_t)std::max(H->Nt, 1), &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dSsum, (size_t)std::max(H->Nt, 1) * 2 * kMaxH, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dGK, (size_t)H->G, &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dCov, (size_t)H->c.WTp + 2 * (kMaxH + 1), &H->device_bytes, dev, st))) return rc;
-        if ((rc = dalloc(&H->dSync, 1, &H->device_bytes, dev, st))) return rc;
+    // each piece on its own, so that a call after a failed allocation completes the set
+    auto need = [&](auto **p, size_t n) { return *p ? MH_OK : dalloc(p, n, &H->device_bytes, dev, st); };
+    const size_t nt1 = (size_t)std::max(H->Nt, 1);
+    if ((rc = need(&H->dU, (size_t)H->c.WTp)) || (rc = need(&H->dState, (size_t)kStateWords)) ||
+        (rc = need(&H->dWork, (size_t)kWorkCount + 2)) || (rc = need(&H->dCounts, (size_t)kCountSets * kCountWords)) ||
+        (rc = need(&H->dCand, (size_t)kCandidates)) || (rc = need(&H->dChamp, nt1)) ||
+        (rc = need(&H->dChampOk, nt1)) || (rc = need(&H->dSsum, nt1 * 2 * kMaxH)) ||
+        (rc = need(&H->dGK, (size_t)H->G)) || (rc = need(&H->dCov, (size_t)H->c.WTp + 2 * (kMaxH + 1))) ||
+        (rc = need(&H->dSync, (size_t)1)))
+        return rc;
+    if (!H->hState) {
         H->pgrid = H->coop ? persistent_grid(H->num_sms, true) : 0;
         if (!(H->hState = pinned_state_get())) return fail(MH_ENOMEM, "pinned host allocation failed");
     }
@@ -873,6 +912,10 @@ MH_API int mh_solve_ex(mh_handle *H, const mh_solve_opts *opts, mh_result **out)
             float kx = 0.f;
             cudaEventElapsedTime(&kx, H->evk[0], H->evk[1]);
             kernel_ms += kx;
+            if (fault_fires(g_fault_timeout)) {
+                destroy_events();
+                return fail(MH_ETIMEOUT, "injected timeout (mh_set_fault) after round %d", rounds_done);
+            }
             if (hs[2]) {
                 destroy_events();
                 return fail(MH_ETIMEOUT, "a grid barrier of the persistent solve timed out in round %d", rounds_done);
@@ -1443,6 +1486,8 @@ struct ServerReq {
     int maxr = 0;
     double work = 0.0;   // expected search work (work_estimate with d = h - 1)
     bool large = false;  // work above kLargeWork
+    bool cancel = false; // mh_cancel on an admitted request: retired at the next round boundary
+    double t_ran = 0.0;  // last launch that included it (its admission before the first)
 };
 
 // Device memory a request needs: its store, workspace and (for h >= 3) the
@@ -1562,7 +1607,25 @@ struct mh_server {
     // launch stream, ahead of the next launch.
     void start_ready()
     {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            std::vector<ServerReq *> keep;
+            for (ServerReq *r : ready) {
+                if (!r->cancel) {
+                    keep.push_back(r);
+                    continue;
+                }
+                mh_destroy(r->H);
+                r->H = nullptr;
+                in_use -= r->footprint;
+                finish(r, MH_ECANCELED, "cancelled before it started");
+            }
+            ready.swap(keep);
+            cv.notify_all();
+        }
+        const double t0 = now_s();
         for (ServerReq *r : ready) {
+            r->t_ran = t0;
             launch_solve_init(r->H->c, r->s, r->H->ws_rounds, r->maxr, r->H->dCounts, kCountSets, st);
             if (r->Nt == 0) {
                 const int one = 1;
@@ -1584,6 +1647,15 @@ struct mh_server {
             int st8[kStateWords];
             cudaMemcpy(st8, H->dState, sizeof st8, cudaMemcpyDeviceToHost);
             int rc = MH_OK;
+            if (r->cancel && !st8[1]) {  // cancelled while running: its state stays behind
+                mh_destroy(H);
+                r->H = nullptr;
+                std::lock_guard<std::mutex> lock(mu);
+                in_use -= r->footprint;
+                finish(r, MH_ECANCELED, "cancelled while running");
+                cv.notify_all();
+                continue;
+            }
             if (st8[2]) rc = fail(MH_ETIMEOUT, "a team barrier of the served solve timed out");
             if (rc == MH_OK && st8[3]) {
                 std::vector<u32> hc(kCountWords);
@@ -1626,9 +1698,16 @@ struct mh_server {
     void run_active()
     {
         std::vector<ServerReq *> sel;
+        // a large request paused longer than large_wait_ms runs in this launch with
+        // the small ones (no request waits without bound under a stream of small ones)
+        const double t_now = now_s();
+        bool starving = false;
         for (ServerReq *r : active)
-            if (!r->large) sel.push_back(r);
+            if (r->large && (t_now - r->t_ran) * 1e3 > (double)o.large_wait_ms) starving = true;
+        for (ServerReq *r : active)
+            if (!r->large || starving) sel.push_back(r);
         if (sel.empty()) sel = active;
+        for (ServerReq *r : sel) r->t_ran = t_now;
         const int n = (int)sel.size();
         std::vector<double> work(n);
         for (int i = 0; i < n; ++i) work[i] = sel[i]->work;
@@ -1717,6 +1796,7 @@ MH_API int mh_server_create(const mh_server_opts *opts, mh_server **out)
     if (opts) S->o = *opts;
     if (S->o.slots <= 0) S->o.slots = 8;
     if (S->o.large_slots <= 0) S->o.large_slots = 2;
+    if (S->o.large_wait_ms <= 0) S->o.large_wait_ms = 250;
     int dev = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     S->dev = dev;
@@ -1818,6 +1898,32 @@ MH_API int mh_wait(mh_server *S, uint64_t ticket, int32_t timeout_ms, mh_result 
     if (timeout_ms < 0) S->cv.wait(lock, ready);
     else if (!S->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), ready)) return MH_EAGAIN;
     return take_result(S, S->all.find(ticket), out);
+}
+
+MH_API int mh_cancel(mh_server *S, uint64_t ticket)
+{
+    if (!S) return fail(MH_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return fail(MH_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
+    ServerReq *r = it->second;
+    if (r->status >= 0) return MH_OK;  // finished already: its result stands
+    for (auto q = S->queue.begin(); q != S->queue.end(); ++q) {
+        if (*q != r) continue;
+        S->queue.erase(q);
+        S->finish(r, MH_ECANCELED, "cancelled while queued");
+        S->cv.notify_all();
+        return MH_OK;
+    }
+    r->cancel = true;                      // admitted: retired at the next round boundary,
+    if (S->h_yield) *(volatile int *)S->h_yield = 1;  // which a running launch reaches soon
+    return MH_OK;
+}
+
+MH_API int mh_set_fault(const char *spec)
+{
+    g_fault_env_read = 1;  // an explicit setting replaces MH_FAULT
+    return parse_fault(spec);
 }
 
 MH_API int mh_server_stats(mh_server *S, int64_t *launches, int32_t *queued, int32_t *active, int64_t *bytes_in_use)
@@ -2043,3 +2149,48 @@ MH_API void mh_shard_free(mh_shard *X)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Coverage evaluation (§IV-D)
+
+extern "C" MH_API int mh_evaluate(mh_handle *H, const int32_t *genes, int32_t k, int32_t h, mh_coverage *out,
+                                  uint64_t *tumor_covered, uint64_t *normal_covered)
+{
+    if (!H || !out || (k > 0 && !genes)) return fail(MH_EINVAL, "handle, out or genes is NULL");
+    if (k < 0 || h < 1 || h > kMaxH) return fail(MH_EINVAL, "k=%d, h=%d: need k >= 0 and 1 <= h <= %d", k, h, kMaxH);
+    for (int64_t i = 0; i < (int64_t)k * h; ++i)
+        if (genes[i] < 0 || genes[i] >= H->G) return fail(MH_EINVAL, "gene index %d outside [0, %d)", genes[i], H->G);
+    cudaStream_t st = H->stream;
+    const Cohort &c = H->c;
+    const size_t words = (size_t)c.WTp + c.WNp;
+    unsigned char *buf = nullptr;
+    const size_t gbytes = ((size_t)std::max(1, k) * h * sizeof(int32_t) + 255) & ~(size_t)255;
+    int rc = dalloc(&buf, gbytes + words * sizeof(u64), &H->device_bytes, H->dev, st);
+    if (rc) return rc;
+    int *dg = (int *)buf;
+    u64 *dcov = (u64 *)(buf + gbytes);
+    std::vector<u64> cov(words, 0);
+    cudaError_t e = cudaMemsetAsync(dcov, 0, words * sizeof(u64), st);
+    if (e == cudaSuccess && k)
+        e = cudaMemcpyAsync(dg, genes, sizeof(int32_t) * (size_t)k * h, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        launch_coverage(c, dg, k, h, dcov, dcov + c.WTp, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cov.data(), dcov, words * sizeof(u64), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(buf, st);
+    if (e != cudaSuccess) return fail(MH_ECUDA, "coverage evaluation failed: %s", cudaGetErrorString(e));
+    int tc = 0, nc = 0;
+    for (int w = 0; w < c.Wt; ++w) tc += __builtin_popcountll(cov[w]);
+    for (int w = 0; w < c.Wn; ++w) nc += __builtin_popcountll(cov[(size_t)c.WTp + w]);
+    out->tc = tc;
+    out->tt = H->Nt;
+    out->nc = nc;
+    out->nt = H->Nn;
+    out->sensitivity = H->Nt ? (double)tc / H->Nt : 0.0;
+    out->specificity = H->Nn ? 1.0 - (double)nc / H->Nn : 0.0;
+    if (tumor_covered) memcpy(tumor_covered, cov.data(), sizeof(u64) * (size_t)c.Wt);
+    if (normal_covered) memcpy(normal_covered, cov.data() + c.WTp, sizeof(u64) * (size_t)c.Wn);
+    return MH_OK;
+}

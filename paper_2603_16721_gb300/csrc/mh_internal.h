@@ -200,6 +200,9 @@ void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t 
 // Split search: step 1 reduces the round's blocks to the shard's best key (xbest[0]),
 // step 2 applies the merged winner xbest[1] (DelCols, selection, next round).
 void launch_finalize_split(const Cohort &c, const Solve &s, u32 *counts, int step, cudaStream_t st);
+// Coverage masks of k combinations (k x h original indices, device): tcov (WTp
+// words) and ncov (WNp words), zeroed by the caller.
+void launch_coverage(const Cohort &c, const int *genes, int k, int h, u64 *tcov, u64 *ncov, cudaStream_t st);
 
 // Persistent solve: all rounds in one cooperative launch of `grid` blocks
 // (persistent_grid(): one block per SM for the default build, the co-resident

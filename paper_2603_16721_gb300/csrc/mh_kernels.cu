@@ -2896,6 +2896,35 @@ void launch_finalize(const Cohort &c, const Solve &s, u32 *counts, cudaStream_t 
     k_finalize<<<1, kThreads, 0, st>>>(c, s, counts);
 }
 
+// Coverage of a set of combinations (§IV-D): bit s of tcov (ncov) is set when tumor
+// (normal) sample s carries every gene of at least one of the k combinations
+// (original indices, k x h).  One thread per (combination, word); the words are
+// OR-ed into the masks.
+__global__ void k_coverage(const __grid_constant__ Cohort c, const int *genes, int k, int h, u64 *tcov, u64 *ncov)
+{
+    const int W = c.Wt + c.Wn;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)k * W) return;
+    const int j = (int)(t / W), w = (int)(t % W);
+    const bool tumor = w < c.Wt;
+    const int ww = tumor ? w : w - c.Wt;
+    u64 y = ~0ull;
+    for (int i = 0; i < h; ++i) {
+        const int g = genes[(size_t)j * h + i];
+        const u64 *row = tumor ? (c.TO ? c.TO + (size_t)g * c.WTp : c.T + (size_t)c.inv[g] * c.WTp)
+                               : (c.NO ? c.NO + (size_t)g * c.WNp : c.N + (size_t)c.inv[g] * c.WNp);
+        y &= __ldg(row + ww);
+    }
+    if (y) atomicOr(tumor ? tcov + ww : ncov + ww, y);
+}
+
+void launch_coverage(const Cohort &c, const int *genes, int k, int h, u64 *tcov, u64 *ncov, cudaStream_t st)
+{
+    const long long total = (long long)k * (c.Wt + c.Wn);
+    if (total == 0) return;
+    k_coverage<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c, genes, k, h, tcov, ncov);
+}
+
 void launch_finalize_split(const Cohort &c, const Solve &s, u32 *counts, int step, cudaStream_t st)
 {
     k_finalize_split<<<1, kThreads, 0, st>>>(c, s, counts, step);

@@ -19,11 +19,11 @@ import numpy as np
 
 from . import _build
 
-MH_OK, MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT, MH_EAGAIN, MH_EREJECT = range(7)
+MH_OK, MH_EINVAL, MH_ENOMEM, MH_ECUDA, MH_ETIMEOUT, MH_EAGAIN, MH_EREJECT, MH_ECANCELED = range(8)
 MH_PRUNE_PAPER, MH_PRUNE_OFF, MH_PRUNE_BOUND = 0, 1, 2
 MH_MODE_PERSISTENT, MH_MODE_LAUNCHES = 0, 1
 _NAMES = {0: "MH_OK", 1: "MH_EINVAL", 2: "MH_ENOMEM", 3: "MH_ECUDA", 4: "MH_ETIMEOUT", 5: "MH_EAGAIN",
-          6: "MH_EREJECT"}
+          6: "MH_EREJECT", 7: "MH_ECANCELED"}
 
 
 class MHLibraryError(RuntimeError):
@@ -177,6 +177,40 @@ class Shard:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class mh_coverage(ctypes.Structure):
+    _fields_ = [("tc", ctypes.c_int32), ("tt", ctypes.c_int32), ("nc", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("sensitivity", ctypes.c_double), ("specificity", ctypes.c_double)]
+
+
+def mh_evaluate(handle: "Handle", genes) -> dict:
+    """Coverage of combinations (rows of original gene indices) on the handle's
+    samples: tc, tt, nc, nt, sensitivity, specificity and the covered masks."""
+    lib = load()
+    lib.mh_evaluate.restype = ctypes.c_int
+    lib.mh_evaluate.argtypes = [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(mh_coverage), _P, _P]
+    g = np.ascontiguousarray(genes, dtype=np.int32)
+    if g.ndim != 2:
+        raise ValueError("genes must be a [k, h] array")
+    k, h = g.shape
+    G, Nt, Nn, _ = mh_handle_info(handle)
+    tmask = np.zeros(max(1, (Nt + 63) // 64), dtype=np.uint64)
+    nmask = np.zeros(max(1, (Nn + 63) // 64), dtype=np.uint64)
+    out = mh_coverage()
+    _check(lib.mh_evaluate(handle.ptr, g.ctypes.data if k else None, k, max(h, 1), ctypes.byref(out),
+                           tmask.ctypes.data, nmask.ctypes.data))
+    return {"tc": out.tc, "tt": out.tt, "nc": out.nc, "nt": out.nt, "sensitivity": out.sensitivity,
+            "specificity": out.specificity, "tumor_covered": tmask[:(Nt + 63) // 64],
+            "normal_covered": nmask[:(Nn + 63) // 64]}
+
+
+def mh_set_fault(spec) -> None:
+    """Host-side fault injection: "alloc_fail=N", "timeout_after=N" or None / "none"."""
+    lib = load()
+    lib.mh_set_fault.restype = ctypes.c_int
+    lib.mh_set_fault.argtypes = [ctypes.c_char_p]
+    _check(lib.mh_set_fault(spec.encode() if spec else None))
 
 
 def mh_int_peak(op: int = 0):
@@ -371,14 +405,15 @@ def mh_solve_batch(handles, hs, alphas=None, blocks=None, prune: int = MH_PRUNE_
 
 
 class mh_server_opts(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("large_slots", ctypes.c_int32)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32), ("large_slots", ctypes.c_int32),
+                ("large_wait_ms", ctypes.c_int32)]
 
 
 class Server:
     """Served runtime (continuous batching): mh_server_create / mh_submit /
     mh_poll / mh_wait / mh_server_destroy."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 0, large_slots: int = 0):
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 0, large_slots: int = 0, large_wait_ms: int = 0):
         lib = load()
         if not hasattr(lib, "_server_typed"):
             lib.mh_server_create.restype = ctypes.c_int
@@ -395,9 +430,11 @@ class Server:
                                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
             lib.mh_server_destroy.restype = None
             lib.mh_server_destroy.argtypes = [_P]
+            lib.mh_cancel.restype = ctypes.c_int
+            lib.mh_cancel.argtypes = [_P, ctypes.c_uint64]
             lib._server_typed = True
         self.ptr = _P()
-        o = mh_server_opts(hbm_budget_bytes, slots, large_slots)
+        o = mh_server_opts(hbm_budget_bytes, slots, large_slots, large_wait_ms)
         _check(lib.mh_server_create(ctypes.byref(o), ctypes.byref(self.ptr)))
 
     def submit(self, bitmaps, G, Nt, Nn, h, alpha=(1, 10)) -> int:
@@ -405,6 +442,9 @@ class Server:
         t = ctypes.c_uint64()
         _check(load().mh_submit(self.ptr, bm.ctypes.data, G, Nt, Nn, h, mh_rational(*alpha), ctypes.byref(t)))
         return t.value
+
+    def cancel(self, ticket) -> None:
+        _check(load().mh_cancel(self.ptr, ticket))
 
     def poll(self, ticket):
         """Result if finished, None while queued or running."""

@@ -227,3 +227,36 @@ def stream(seed: int, n: int) -> np.ndarray:
 
 
 COHORTS = {"c1": c1, "c2": c2, "c3": c3}
+
+
+def split_samples(c: Cohort, train_frac: float = 0.75, seed: int = 7):
+    """A random train / test split of a cohort's samples (the 75% / 25% split of
+    §IV-B and §IV-D), tumors and normals each: (train bitmaps, Nt, Nn), (test
+    bitmaps, Nt, Nn).  The order comes from sorting xoshiro256** outputs seeded by
+    `seed` (tumors) and `seed + 1` (normals); every gene keeps its row."""
+    def order(n, sd):
+        return np.argsort(stream(sd, n), kind="stable") if n else np.zeros(0, dtype=np.int64)
+
+    Wt, Wn = c.Wt, c.Wn
+    T = np.unpackbits(np.ascontiguousarray(c.bitmaps[:, :Wt]).view(np.uint8), bitorder="little", axis=1)[:, :c.Nt]
+    N = np.unpackbits(np.ascontiguousarray(c.bitmaps[:, Wt:]).view(np.uint8), bitorder="little", axis=1)[:, :c.Nn]
+    pt, pn = order(c.Nt, seed), order(c.Nn, seed + 1)
+    kt, kn = int(round(train_frac * c.Nt)), int(round(train_frac * c.Nn))
+
+    def pack(Tm, Nm):
+        nt, nn = Tm.shape[1], Nm.shape[1]
+        wt, wn = (nt + 63) // 64, (nn + 63) // 64
+        out = np.zeros((c.G, wt + wn), dtype=np.uint64)
+        if nt:
+            b = np.packbits(Tm.astype(np.uint8), bitorder="little", axis=1)
+            b = np.concatenate([b, np.zeros((c.G, 8 * wt - b.shape[1]), np.uint8)], axis=1)
+            out[:, :wt] = np.ascontiguousarray(b).view(np.uint64)
+        if nn:
+            b = np.packbits(Nm.astype(np.uint8), bitorder="little", axis=1)
+            b = np.concatenate([b, np.zeros((c.G, 8 * wn - b.shape[1]), np.uint8)], axis=1)
+            out[:, wt:] = np.ascontiguousarray(b).view(np.uint64)
+        return out, nt, nn
+
+    train = pack(T[:, np.sort(pt[:kt])], N[:, np.sort(pn[:kn])])
+    test = pack(T[:, np.sort(pt[kt:])], N[:, np.sort(pn[kn:])])
+    return train, test

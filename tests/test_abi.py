@@ -86,3 +86,14 @@ def test_binding_structs_match_header_layout(tmp_path, struct, cls):
     got = _c_layout(tmp_path, struct, names)
     assert got[0] == ctypes.sizeof(c)
     assert got[1:] == [getattr(c, n).offset for n in names]
+
+
+def test_fault_specs_need_no_gpu(lib):
+    mh.load()
+    for ok in ("none", None, "alloc_fail=3", "timeout_after=1"):
+        mh.mh_set_fault(ok)
+    for bad in ("alloc_fail=0", "explode", "timeout_after=-2"):
+        with pytest.raises(mh.MHError) as e:
+            mh.mh_set_fault(bad)
+        assert e.value.code == mh.MH_EINVAL and "alloc_fail" in str(e.value)
+    mh.mh_set_fault(None)
