@@ -372,6 +372,8 @@ def run_ours(args):
             # the other plain single-cohort configurations (c1: h=2, G=1,000; c3: h=4,
             # G=19,000, 128-bit rows): CUDA events on the solving stream, L2 flushed
             line["plain_configs"] = {"c1": plain_config("c1", 5), "c3": plain_config("c3", 3)}
+            line["bound_mode"] = bound_comparison(c)
+            line["train_test"] = train_test_coverage()
             # the other two parts of the metric, after the timed c2 steps: batched
             # (16 uneven cohorts in one launch vs one after another) and served
             # (request trace: continuous batching vs a plain loop)
@@ -419,6 +421,51 @@ def plain_config(name, runs):
             "combos_scored_per_s": scored / t, "leaves_tested_per_s": int(r.visited[:, -1].sum()) / t,
             "prefixes_pruned_per_s": int(r.pruned[:, :-1].sum()) / t,
             "visited_fraction": int(r.visited[:, -1].sum()) / (r.rounds * _comb(c.G, spec.h)), "runs": runs}
+
+
+def bound_comparison(c):
+    """The score-bound mode on the timed workload: same selections, fewer nodes."""
+    import torch
+    from paper_2603_16721_gb300 import mh
+    out = {}
+    rounds = 1
+    with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as Hb:
+        for name, prune in (("paper", mh.MH_PRUNE_PAPER), ("bound", mh.MH_PRUNE_BOUND)):
+            r = mh.mh_solve_ex(Hb, H_HITS, ALPHA, prune=prune)
+            ms = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                r = mh.mh_solve_ex(Hb, H_HITS, ALPHA, prune=prune)
+                ms.append(r.kernel_ms)
+            rounds = r.rounds
+            out[name] = {"kernel_ms_per_solve": round(statistics.median(ms), 3), "records": r.records(),
+                         "visited_leaves": int(r.visited[:, -1].sum()), "visited_nodes": int(r.visited.sum()),
+                         "cut_prefixes": int(r.cut.sum())}
+    same = out["paper"].pop("records") == out["bound"].pop("records")
+    full = rounds * _comb(c.G, H_HITS)
+    return {"identical_selections": same,
+            "visited_fraction_paper": out["paper"]["visited_leaves"] / full,
+            "visited_fraction_bound": out["bound"]["visited_leaves"] / full,
+            "paper": out["paper"], "bound": out["bound"],
+            "note": "bound mode runs the node-by-node search (no per-sample sums); its counters depend on "
+                    "when candidates were found"}
+
+
+def train_test_coverage():
+    """§IV-D on the synthetic workload: learn on 75% of c2's samples, evaluate the
+    frozen combinations on the training and held-out samples (GPU coverage)."""
+    import synth
+    from paper_2603_16721_gb300 import mh
+    c = synth.generate(synth.c2())
+    (tr, nt, nn), (te, mt, mn) = synth.split_samples(c, 0.75, seed=7)
+    with mh.mh_create(tr, c.G, nt, nn) as Ht:
+        sol = mh.mh_solve(Ht, H_HITS, ALPHA)
+        train = mh.mh_evaluate(Ht, sol.genes)
+    with mh.mh_create(te, c.G, mt, mn) as He:
+        test = mh.mh_evaluate(He, sol.genes)
+    keys = ("tc", "tt", "nc", "nt", "sensitivity", "specificity")
+    return {"workload": "c2 samples split 75/25 (seed 7): learn on train, evaluate on both",
+            "combinations": sol.k, "train": {k: train[k] for k in keys}, "test": {k: test[k] for k in keys}}
 
 
 def _comb(n, k):
@@ -603,9 +650,9 @@ def main(argv=None):
                     help="c2: leave out the batched and served comparisons appended to the line")
     ap.add_argument("--mode", choices=["persistent", "launches"], default="persistent",
                     help="one persistent kernel per solve, or one launch per phase")
-    ap.add_argument("--workload", choices=["c2", "batch16", "served200"], default="c2",
-                    help="c2: the headline single-cohort solve; batch16: the batched workload; "
-                         "served200: the served request trace")
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "batch16", "served200"], default="c2",
+                    help="c2: the headline single-cohort solve; c1, c3: the other plain solves (their timing "
+                         "alone, --steps runs); batch16: the batched workload; served200: the served request trace")
     ap.add_argument("--requests", type=int, default=200, help="served200: requests replayed")
     ap.add_argument("--slots", type=int, default=8, help="served200: concurrent requests")
     ap.add_argument("--large-slots", type=int, default=0,
@@ -617,6 +664,11 @@ def main(argv=None):
         return run_batch16(args)
     if args.workload == "served200":
         return run_served(args)
+    if args.workload in ("c1", "c3"):
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(plain_config(args.workload, max(1, args.steps))))
+        return 0
     return run_ours(args)
 
 
