@@ -195,7 +195,8 @@ MH_API int mh_check_bounded_wait(int32_t *status);
  * Teams own whole SMs when the split allows it (blocks in multiples of the blocks
  * one SM holds).  blocks: n block counts (each >= 1, summing to at most the
  * co-resident grid of the three-blocks-per-SM build; kept fixed), or NULL to let
- * the autotuner choose the kernel build (three or four blocks per SM) and the
+ * the autotuner choose the kernel build (one block of 16 warps, or three or four
+ * blocks of 8 warps, per SM) and the
  * split: blocks ~ work^gamma with the per-cohort work estimated from the tumors'
  * mutation counts (the gene sets of size h-1, or of size h, that share a tumor);
  * build, model and gamma are picked by timing each candidate once per batch shape

@@ -1397,8 +1397,10 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     int rc = MH_OK, smm = 0, graphed = 0;
     // a choice of the autotuner, encoded as 100 * (build == 4) + 10 * model + gamma
     auto run_choice = [&](double choice, double *t, int *smm_out) {
-        const int build = choice >= 100.0 ? 4 : 3;
-        if (choice >= 100.0) choice -= 100.0;
+        // choice = 100 * (index of the build in kBatchBuilds) + 10 * model + gamma
+        const int bi = std::min(2, std::max(0, (int)(choice / 100.0)));
+        const int build = kBatchBuilds[bi];
+        choice -= 100.0 * bi;
         const bool leaves = choice >= 10.0;
         return run_batch(handles, opts, n, leaves ? work_l : work_p, choice - (leaves ? 10.0 : 0.0), build, nullptr,
                          t, smm_out, smm_out ? &graphed : nullptr);
@@ -1406,7 +1408,7 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     if (blocks) {
         rc = run_batch(handles, opts, n, work_p, 1.0, 3, &b, &ms, &smm, &graphed);
     } else {
-        // autotuner: the kernel build (3 or 4 blocks per SM), the work model and the
+        // autotuner: the kernel build (1, 3 or 4 blocks per SM), the work model and the
         // split exponent gamma (blocks ~ work^gamma) are chosen by timing each
         // candidate once per batch shape; the choice is cached on disk
         const std::string sig = batch_signature(handles, opts, n, grid);
@@ -1415,13 +1417,14 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
             rc = run_choice(choice, &ms, &smm);
         } else {
-            const double gammas[] = {0.5, 0.75, 1.0};
+            const double gammas[] = {0.5, 0.75, 1.0, 1.5, 2.0};
             double best_ms = 1e300, best = 1.0;
-            for (int build : kBatchBuilds) {
+            for (int bi = 0; bi < 3; ++bi) {
+                if (batch_grid(H0->num_sms, kBatchBuilds[bi]) < n) continue;  // a block per cohort at least
                 for (int model = 0; model < 2; ++model) {
                     for (double g : gammas) {
                         double t = 0.0;
-                        const double cand = (build == 4 ? 100.0 : 0.0) + 10.0 * model + g;
+                        const double cand = 100.0 * bi + 10.0 * model + g;
                         rc = run_choice(cand, &t, nullptr);
                         if (rc) return rc;
                         if (t < best_ms) {
@@ -1523,7 +1526,7 @@ int64_t estimate_footprint(const uint64_t *bm, int G, int Nt, int Nn, int h, dou
 
 // The batched kernel's build used by the server (four blocks per SM: the faster one
 // on a stream of large requests with small ones backfilling).
-constexpr int kServerBuild = 4;
+constexpr int kServerBuild = 1;  // one block of 16 warps per SM: teams of whole SMs
 
 struct mh_server {
     mh_server_opts o{};

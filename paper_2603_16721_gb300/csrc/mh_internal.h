@@ -171,12 +171,13 @@ struct Frontiers {
 // Device bytes of one frontier record slot with its incremental-round data.
 constexpr size_t kSlotBytes = sizeof(Rec) + 2 * sizeof(u64) + sizeof(Key);
 
-// Grid-wide barrier state of the persistent solve (zeroed before each launch);
-// flag: a decision taken by the block that releases a barrier (the batch's yield).
+// Grid-wide barrier state of the persistent solve (zeroed before each launch):
+// arrived counts the blocks' arrivals over the launch's barriers; flag is raised by
+// a block that found the batch's yield request set when it arrived.
 struct GridSync {
-    unsigned count, gen;
+    unsigned arrived;
     int flag;
-    unsigned arrived;  // barriers without a sampled decision: arrivals of the launch so far
+    unsigned pad[2];
 };
 
 // The persistent solve keeps the frontier counters (kCountWords) twice, by round
@@ -211,11 +212,12 @@ void launch_coverage(const Cohort &c, const int *genes, int k, int h, u64 *tcov,
 // It returns when the solve is done, a frontier overflowed (state) or a grid
 // barrier timed out (state error = kErrTimeout).
 int persistent_grid(int num_sms, bool large);
-// The batched kernel comes in two builds, 3 or 4 co-resident blocks per SM (more
-// registers per thread, or more warps); batch_grid / batch_blocks_per_sm take the build.
+// The batched kernel comes in three builds: one block of 16 warps per SM (the most
+// registers per thread), or 3 or 4 co-resident blocks of 8 warps per SM (more warps);
+// batch_grid / batch_blocks_per_sm take the build (its blocks per SM).
 int batch_grid(int num_sms, int build);
 int batch_blocks_per_sm(int build);
-constexpr int kBatchBuilds[2] = {3, 4};
+constexpr int kBatchBuilds[3] = {1, 3, 4};
 
 // One cohort of a batched solve: its device state and its share of the grid
 // (blocks [first_block, first_block + nblocks)).

@@ -1516,17 +1516,18 @@ __global__ void __launch_bounds__(kThreads) k_finalize_split(const __grid_consta
 
 // Grid barrier with a bounded wait: a block that waits longer than about two
 // seconds records a timeout in the state and returns false instead of hanging.
-// With `sample`, the block that releases the barrier copies *sample into g->flag
-// first, so every block reads the same value after the barrier.
+// One atomic per block: arrivals count up across the barriers of a launch (the
+// word starts at zero), so barrier k ends when the count reaches (k + 1) * nblocks,
+// and a block learns k from the count it found.  With `sample`, a block that finds
+// *sample set raises g->flag before it arrives; after the barrier every block reads
+// the same flag (the OR of what the blocks found), so they take the same decision.
 __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, const int *sample = nullptr)
 {
     __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0 && !sample) {
-        // one atomic per block: arrivals count up across the barriers of a launch
-        // (the word starts at zero), so barrier k ends when the count reaches
-        // (k + 1) * nblocks, and a block learns k from the count it found
+    if (threadIdx.x == 0) {
         ok = 1;
+        if (sample && *(volatile const int *)sample) *(volatile int *)&g->flag = 1;
         __threadfence();
         const unsigned old = atomicAdd(&g->arrived, 1u);
         const unsigned target = (old / (unsigned)nblocks + 1u) * (unsigned)nblocks;
@@ -1537,28 +1538,6 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, 
                 atomicExch(&state[kStError], kErrTimeout);
                 ok = 0;
                 break;
-            }
-        }
-        __threadfence();
-    } else if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned gen = *(volatile unsigned *)&g->gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&g->count, 1u) + 1u;
-        if (arrived == (unsigned)nblocks) {
-            if (sample) *(volatile int *)&g->flag = *(volatile const int *)sample;
-            atomicExch(&g->count, 0u);
-            __threadfence();
-            atomicAdd(&g->gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*(volatile unsigned *)&g->gen == gen) {
-                __nanosleep(64);
-                if (++spins > (1ull << 25)) {
-                    atomicExch(&state[kStError], kErrTimeout);
-                    ok = 0;
-                    break;
-                }
             }
         }
         __threadfence();
@@ -2809,11 +2788,11 @@ __device__ int sm_major_block(const BatchMap &m)
 // Batched solve: block b (SM-major number, or blockIdx.x if that numbering failed
 // anywhere in the grid) works on the cohort whose block range holds b, with the
 // blocks of that range as its team; cohorts progress independently.
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+template <int kMinBlocks, int kWarps>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     k_solve_batch(const BatchItem *items, int n, int *yield, BatchMap map)
 {
-    __shared__ Batch scratch[kWarpsPerBlock];
+    __shared__ Batch scratch[kWarps];
     __shared__ int vb_s;
     if (threadIdx.x == 0) {
         vb_s = sm_major_block(map);
@@ -2949,10 +2928,15 @@ cudaError_t launch_barrier_probe(GridSync *g, int *state, cudaStream_t st)
 int batch_blocks_per_sm(int build)
 {
     int per_sm = 0;
-    const cudaError_t e = build == 3
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<3>, kThreads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<4>, kThreads, 0);
-    return e == cudaSuccess ? per_sm : 0;
+    const cudaError_t e =
+        build == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<1, kSmallWarps>,
+                                                                   kSmallWarps * 32, 0)
+        : build == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<3, kWarpsPerBlock>,
+                                                                     kThreads, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batch<4, kWarpsPerBlock>,
+                                                                     kThreads, 0);
+    if (e != cudaSuccess) return 0;
+    return build == 1 ? (per_sm >= 1 ? 1 : 0) : per_sm;
 }
 
 int batch_grid(int num_sms, int build) { return batch_blocks_per_sm(build) * num_sms; }
@@ -2970,8 +2954,11 @@ cudaError_t launch_solve_batch(const BatchItem *d_items, int n, int *d_yield, co
     if (e != cudaSuccess) return e;
     void *args[] = {&items, &nn, &yield, &map};
     const int grid = map.per_sm * map.num_sms;
-    const void *fn = map.build == 3 ? (const void *)k_solve_batch<3> : (const void *)k_solve_batch<4>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
+    const void *fn = map.build == 1   ? (const void *)k_solve_batch<1, kSmallWarps>
+                     : map.build == 3 ? (const void *)k_solve_batch<3, kWarpsPerBlock>
+                                      : (const void *)k_solve_batch<4, kWarpsPerBlock>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(map.build == 1 ? kSmallWarps * 32 : kThreads), args, 0,
+                                       st);
 }
 
 cudaError_t launch_solve_persistent(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync,
