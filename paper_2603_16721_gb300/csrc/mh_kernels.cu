@@ -2134,6 +2134,9 @@ __device__ void phase_build1(const Cohort &c, const Solve &s, const Frontiers &f
 // thread of the block must call it; returns false (for every thread) if round 0
 // overflowed a frontier.
 constexpr int kScanIlp = 4;  // records whose signature and cached score a lane loads at once
+// changed leaf parents a block spreads over its warps per round (one-block-per-SM
+// builds; the smaller blocks keep their shared memory for occupancy)
+constexpr int kEvalQueue = 64;
 // soffs / nrec / tab_ok: the kept frontiers' shard offsets and sizes, read once per
 // launch (after round 0's build) into the block's shared memory.
 struct FrontTab {
@@ -2141,18 +2144,27 @@ struct FrontTab {
     long long n[kMaxH];
     int ok;
 };
+template <int kQueue>
 __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
                              Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft,
                              u64 *tot, int *tot_pending)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
+    __shared__ int qn;  // the block's queue of changed leaf parents
+    __shared__ Rec qrec[kQueue > 0 ? kQueue : 1];
+    __shared__ u32 qslot[kQueue > 0 ? kQueue : 1];
+    __shared__ u64 qlco[kQueue > 0 ? kQueue : 1];
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     const u64 *Ush = io.Ush;
     u64 *deep = acc + kAccDeep;  // deep[2l], deep[2l + 1]: depth l's two correction changes
-    if (threadIdx.x == 0) overflow = 0;
+    const int qcap = kQueue < 32 * nwarps ? kQueue : 32 * nwarps;
+    if (threadIdx.x == 0) {
+        overflow = 0;
+        qn = 0;
+    }
     acc_begin(acc);
     u64 csig = 0;
     for (int w = 0; w < c.Wt; ++w) csig |= Csh[w];
@@ -2311,9 +2323,22 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                         f.lc[l][slot[u]] = 0;
                         dL -= lco;
                     }
-                    if (__ballot_sync(kFull, eval)) {
-                        leaf_parents_eval(c, s, b, eval, l, lane);
-                        if (eval) {
+                    // changed leaf parents go to the block's queue (spread over its warps
+                    // below); what does not fit is evaluated by this warp
+                    bool queued = false;
+                    if (eval && !force) {
+                        const int pos = atomicAdd(&qn, 1);
+                        if (pos < qcap) {
+                            copy_rec(&qrec[pos], &r);
+                            qslot[pos] = slot[u];
+                            qlco[pos] = lco;
+                            queued = true;
+                        }
+                    }
+                    const bool here = eval && !queued;
+                    if (__ballot_sync(kFull, here)) {
+                        leaf_parents_eval(c, s, b, here, l, lane);
+                        if (here) {
                             const Key kb = b.rb[lane];
                             f.lb[l][slot[u]] = kb;
                             f.lc[l][slot[u]] = b.rc[lane];
@@ -2331,6 +2356,28 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     kc.t2 = __ldcg(&f.lb[l][slot[u]].t2);
                     if (key_better(kc, best)) best = kc;
                 }
+            }
+        }
+        if (leafp) {
+            // the queued leaf parents, whole records to warps in turn (entry q to warp
+            // q mod nwarps, lane q / nwarps), so that the block's changes spread over all
+            // of its warps; at most 32 entries per warp (qcap)
+            __syncthreads();
+            const int nq = qn < qcap ? qn : qcap;
+            const int q = warp + nwarps * lane;
+            const bool live = q < nq;
+            if (__ballot_sync(kFull, live)) {
+                if (live) copy_rec(&b.r[lane], &qrec[q]);
+                __syncwarp();
+                leaf_parents_eval(c, s, b, live, l, lane);
+                if (live) {
+                    const Key kb = b.rb[lane];
+                    f.lb[l][qslot[q]] = kb;
+                    f.lc[l][qslot[q]] = b.rc[lane];
+                    dL += b.rc[lane] - qlco[q];
+                    if (kb.s != 0 && key_better(kb, best)) best = kb;
+                }
+                __syncwarp();
             }
         }
         dA = warp_sum_u64(dA);
@@ -2593,6 +2640,7 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
 // before the previous round's last barrier).  Returns when the solve is done, a
 // frontier overflowed, a barrier timed out (recorded in the cohort's state) or,
 // in a batch, the barrier that ended a round carried a yield request.
+template <int kQueue>
 __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts_base,
                            const Team &t, Batch &b, int *yield = nullptr)
 {
@@ -2698,7 +2746,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
             lap(1);
-            if (!phase_update(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
+            if (!phase_update<kQueue>(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
                 overflow();
                 return;
             }
@@ -2757,7 +2805,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
             GridSync *gsync, u32 *counts, int *yield)
 {
     __shared__ Batch scratch[kWarps];
-    solve_team(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5], yield);
+    solve_team<kMinBlocks == 1 ? kEvalQueue : 0>(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5], yield);
 }
 
 // SM-major number of the calling block (thread 0): SMs are ranked in the order
@@ -2822,7 +2870,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
         const int nsm = it.nblocks / map.per_sm;
         t.rank = (t.rank % map.per_sm) * nsm + t.rank / map.per_sm;
     }
-    solve_team(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5], yield);
+    solve_team<kMinBlocks == 1 ? kEvalQueue : 0>(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5],
+                                                 yield);
 }
 
 }  // namespace
