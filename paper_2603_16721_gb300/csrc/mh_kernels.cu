@@ -2143,8 +2143,26 @@ struct FrontTab {
     int soff[kMaxH][kShards + 1];
     long long n[kMaxH];
     int ok;
+    // per warp: its list of live kept records (built in a round after round 0, when
+    // they fit) and, per depth, where the depth's entries start and how many there are
+    signed char lok[kMaxWarpsPerBlock];
+    short lbase[kMaxWarpsPerBlock][kMaxH];
+    short lcnt[kMaxWarpsPerBlock][kMaxH];
 };
-template <int kQueue>
+// Entries of a warp's list of live kept records (one-block-per-SM builds).  After
+// round 0 a record that no longer holds two uncovered tumors can never hold them
+// again (U only shrinks): DelCols has emptied it for good, and the list drops it.
+// The list keeps each live record's slot, sample signature and cached best score
+// on chip, so a round reads only the records that a covered tumor touches.
+constexpr int kList = 160;
+template <int kLWarps>
+struct LiveLists {
+    u32 slot[kLWarps][kList];
+    u64 sig[kLWarps][kList];
+    u64 ls[kLWarps][kList];
+    u16 dq[kLWarps][kList];  // a round's touched entries, by position
+};
+template <int kQueue, int kLWarps>
 __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
                              Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft,
                              u64 *tot, int *tot_pending)
@@ -2155,6 +2173,9 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     __shared__ Rec qrec[kQueue > 0 ? kQueue : 1];
     __shared__ u32 qslot[kQueue > 0 ? kQueue : 1];
     __shared__ u64 qlco[kQueue > 0 ? kQueue : 1];
+    __shared__ short qidx[kQueue > 0 ? kQueue : 1];  // list entry of a queued record (-1: none)
+    __shared__ signed char qwarp[kQueue > 0 ? kQueue : 1];
+    __shared__ LiveLists<(kLWarps > 0 ? kLWarps : 1)> lv;
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
@@ -2252,8 +2273,15 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         if (overflow) return false;
         if (threadIdx.x == 0) ft.ok = 1;
     }
+    // after round 0 a warp whose live records fit its list scans the list only; a warp
+    // builds its list in the first round after round 0 in which they fit
+    const bool use_list = kLWarps > 0 && !force && ft.lok[warp] == 1;
+    const bool build_list = kLWarps > 0 && !force && ft.lok[warp] == 0;
+    int lfill = 0;
+    bool lfit = true;
     for (int l = h == 2 ? 1 : 2; l <= h - 1; ++l) {
         const long long n_in = ft.n[l];
+        if (build_list && lane == 0) ft.lbase[warp][l] = (short)lfill;
         const int *soff = ft.soff[l];
         const bool leafp = l == h - 1;
         const int hiN = c.G - h + l;  // hi(l + 1), 0-based
@@ -2264,7 +2292,128 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         const u64 B = split ? (u64)(t.size - 1) : (u64)t.size, W = split ? (u64)(nwarps - 1) : (u64)nwarps;
         const u64 rk = split ? (u64)(t.rank - 1) : (u64)t.rank;
         const u64 n = (n_in < 0 || (split && (t.rank == 0 || warp == gwarp))) ? 0ull : (u64)n_in;
-        for (u64 k = 0; rk + B * ((u64)warp + W * 32ull * kScanIlp * k) < n; ++k) {
+        if (use_list) {
+            // this warp's live records: drop the dead ones, pick out those a covered tumor
+            // touches, and take the best cached leaf of the others
+            u32 *Lslot = lv.slot[warp] + ft.lbase[warp][l];
+            u64 *Lsig = lv.sig[warp] + ft.lbase[warp][l], *Lls = lv.ls[warp] + ft.lbase[warp][l];
+            u16 *dq = lv.dq[warp];
+            const int cnt = ft.lcnt[warp][l];
+            int wpos = 0, nd = 0;
+            u64 lmax = 0;
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                const int j = j0 + lane;
+                u32 sl = 0;
+                u64 sg = 0, lsv = 0;
+                if (j < cnt) {
+                    sl = Lslot[j];
+                    sg = Lsig[j];
+                    lsv = Lls[j];
+                }
+                const bool keep = sg != 0;
+                const unsigned km = __ballot_sync(kFull, keep);
+                __syncwarp();
+                const int pos = wpos + __popc(km & ((1u << lane) - 1u));
+                if (keep) {
+                    Lslot[pos] = sl;
+                    Lsig[pos] = sg;
+                    Lls[pos] = lsv;
+                }
+                wpos += __popc(km);
+                const bool dirty = keep && (sg & csig) != 0;
+                const unsigned dm = __ballot_sync(kFull, dirty);
+                if (dirty) dq[nd + __popc(dm & ((1u << lane) - 1u))] = (u16)pos;
+                nd += __popc(dm);
+                if (keep && !dirty && lsv > lmax) lmax = lsv;
+            }
+            __syncwarp();
+            if (lane == 0) ft.lcnt[warp][l] = (short)wpos;
+            const u64 wmax = leafp ? warp_max_u64(lmax) : 0ull;
+            if (wmax != 0 && wmax >= best.s) {  // the untouched records' best cached leaves
+                for (int j0 = 0; j0 < wpos; j0 += 32) {
+                    const int j = j0 + lane;
+                    if (j < wpos && Lls[j] == wmax && (Lsig[j] & csig) == 0) {
+                        const u32 sl = Lslot[j];
+                        Key kc;
+                        kc.s = wmax;
+                        kc.t0 = __ldcg(&f.lb[l][sl].t0);
+                        kc.t1 = __ldcg(&f.lb[l][sl].t1);
+                        kc.t2 = __ldcg(&f.lb[l][sl].t2);
+                        if (key_better(kc, best)) best = kc;
+                    }
+                }
+            }
+            for (int d0 = 0; d0 < nd; d0 += 32) {  // the touched ones, one per lane
+                const bool act = d0 + lane < nd;
+                const int pos = act ? (int)dq[d0 + lane] : 0;
+                const u32 sl = act ? Lslot[pos] : 0u;
+                Rec &r = b.r[lane];
+                bool changed = false;
+                int kyn = 0;
+                u64 lco = 0;
+                if (act) {
+                    load_rec(&r, f.F[l] + sl);
+                    if (leafp) lco = __ldcg(f.lc[l] + sl);
+                    const int kyo = (int)r.ky;
+                    changed = refresh_record(c, Ush, Csh, l, r, false);
+                    kyn = r.ky;
+                    if (changed) {
+                        const u64 nsg = kyn >= 2 ? sample_sig(r) : 0ull;
+                        f.sig[l][sl] = nsg;
+                        Lsig[pos] = nsg;
+                        copy_rec(f.F[l] + sl, &r);
+                        if (l >= 2) {
+                            const u64 fo = kyo >= 2 ? (u64)(kyo - 1) : 0ull, fn = kyn >= 2 ? (u64)(kyn - 1) : 0ull;
+                            dA += fn - fo;
+                            dV += (fn - fo) * (u64)(hiN - prefix_gene(r.p, l - 1));
+                        }
+                    } else if (leafp) {  // nothing covered in it after all: its cached best stands
+                        const u64 lsv = Lls[pos];
+                        if (lsv != 0 && lsv >= best.s) {
+                            Key kc;
+                            kc.s = lsv;
+                            kc.t0 = __ldcg(&f.lb[l][sl].t0);
+                            kc.t1 = __ldcg(&f.lb[l][sl].t1);
+                            kc.t2 = __ldcg(&f.lb[l][sl].t2);
+                            if (key_better(kc, best)) best = kc;
+                        }
+                    }
+                }
+                const bool eval = leafp && changed && kyn >= 2;
+                if (leafp && changed && kyn < 2) {
+                    f.lb[l][sl] = key_empty();
+                    f.lc[l][sl] = 0;
+                    dL -= lco;
+                    Lls[pos] = 0;
+                }
+                bool queued = false;
+                if (eval) {
+                    const int qp = atomicAdd(&qn, 1);
+                    if (qp < qcap) {
+                        copy_rec(&qrec[qp], &r);
+                        qslot[qp] = sl;
+                        qlco[qp] = lco;
+                        qidx[qp] = (short)(ft.lbase[warp][l] + pos);
+                        qwarp[qp] = (signed char)warp;
+                        queued = true;
+                    }
+                }
+                const bool here = eval && !queued;
+                if (__ballot_sync(kFull, here)) {
+                    leaf_parents_eval(c, s, b, here, l, lane);
+                    if (here) {
+                        const Key kb = b.rb[lane];
+                        f.lb[l][sl] = kb;
+                        f.lc[l][sl] = b.rc[lane];
+                        Lls[pos] = kb.s;
+                        dL += b.rc[lane] - lco;
+                        if (kb.s != 0 && key_better(kb, best)) best = kb;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        for (u64 k = 0; !use_list && rk + B * ((u64)warp + W * 32ull * kScanIlp * k) < n; ++k) {
             u32 slot[kScanIlp];
             u64 sg[kScanIlp], ls[kScanIlp];
 #pragma unroll
@@ -2282,11 +2431,12 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             for (int u = 0; u < kScanIlp; ++u) {
                 const bool dirty = sg[u] != 0 && (force || (sg[u] & csig) != 0);
                 bool cached = leafp && sg[u] != 0 && !dirty;
-                if (__ballot_sync(kFull, dirty)) {
+                if (__ballot_sync(kFull, dirty) || build_list) {
                     Rec &r = b.r[lane];
                     bool changed = false;
                     int kyn = 0;
                     u64 lco = 0;
+                    u64 nsg = sg[u];  // the record's signature after this round
                     if (dirty) {
                         load_rec(&r, f.F[l] + slot[u]);
                         if (leafp && !force) lco = __ldcg(f.lc[l] + slot[u]);
@@ -2306,7 +2456,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                             }
                         }
                         if (changed) {
-                            f.sig[l][slot[u]] = kyn >= 2 ? sample_sig(r) : 0ull;
+                            nsg = kyn >= 2 ? sample_sig(r) : 0ull;
+                            f.sig[l][slot[u]] = nsg;
                             copy_rec(f.F[l] + slot[u], &r);
                             if (l >= 2) {
                                 const u64 fo = kyo >= 2 ? (u64)(kyo - 1) : 0ull, fn = kyn >= 2 ? (u64)(kyn - 1) : 0ull;
@@ -2323,6 +2474,24 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                         f.lc[l][slot[u]] = 0;
                         dL -= lco;
                     }
+                    // the warp's list: the records still live after this round, with their
+                    // cached best scores (a changed leaf parent's is set when it is evaluated)
+                    int lpos = -1;
+                    if (build_list) {
+                        const bool keep = nsg != 0;
+                        const unsigned km = __ballot_sync(kFull, keep);
+                        if (lfill + __popc(km) > kList) {
+                            lfit = false;
+                        } else if (lfit) {
+                            if (keep) {
+                                lpos = lfill + __popc(km & ((1u << lane) - 1u));
+                                lv.slot[warp][lpos] = slot[u];
+                                lv.sig[warp][lpos] = nsg;
+                                lv.ls[warp][lpos] = leafp && !changed ? ls[u] : 0ull;
+                            }
+                            lfill += __popc(km);
+                        }
+                    }
                     // changed leaf parents go to the block's queue (spread over its warps
                     // below); what does not fit is evaluated by this warp
                     bool queued = false;
@@ -2332,6 +2501,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                             copy_rec(&qrec[pos], &r);
                             qslot[pos] = slot[u];
                             qlco[pos] = lco;
+                            qidx[pos] = (short)lpos;
+                            qwarp[pos] = (signed char)warp;
                             queued = true;
                         }
                     }
@@ -2342,6 +2513,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                             const Key kb = b.rb[lane];
                             f.lb[l][slot[u]] = kb;
                             f.lc[l][slot[u]] = b.rc[lane];
+                            if (lpos >= 0) lv.ls[warp][lpos] = kb.s;
                             dL += b.rc[lane] - lco;
                             if (kb.s != 0 && key_better(kb, best)) best = kb;
                         }
@@ -2374,12 +2546,14 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     const Key kb = b.rb[lane];
                     f.lb[l][qslot[q]] = kb;
                     f.lc[l][qslot[q]] = b.rc[lane];
+                    if (kLWarps > 0 && qidx[q] >= 0) lv.ls[qwarp[q]][qidx[q]] = kb.s;
                     dL += b.rc[lane] - qlco[q];
                     if (kb.s != 0 && key_better(kb, best)) best = kb;
                 }
                 __syncwarp();
             }
         }
+        if (build_list && lane == 0) ft.lcnt[warp][l] = (short)(lfill - ft.lbase[warp][l]);
         dA = warp_sum_u64(dA);
         dV = warp_sum_u64(dV);
         dL = warp_sum_u64(dL);
@@ -2389,6 +2563,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             acc_add(deep, 2 * h + 1, dL);
         }
     }
+    if (build_list && lane == 0) ft.lok[warp] = lfit ? 1 : 0;
     warp_cycles(acc, t0, lane);
     __syncthreads();
     if (threadIdx.x == 0) *tot_pending = 0;
@@ -2640,7 +2815,7 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
 // before the previous round's last barrier).  Returns when the solve is done, a
 // frontier overflowed, a barrier timed out (recorded in the cohort's state) or,
 // in a batch, the barrier that ended a round carried a yield request.
-template <int kQueue>
+template <int kQueue, int kLWarps>
 __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, GridSync *gsync, u32 *counts_base,
                            const Team &t, Batch &b, int *yield = nullptr)
 {
@@ -2664,6 +2839,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     if (*(volatile int *)&s.state[kStDone] | *(volatile int *)&s.state[kStError]) return;
     int round = *(volatile int *)&s.state[kStRound];
     const int maxr = *(volatile int *)&s.state[kStMaxRounds];
+    for (int w = (int)threadIdx.x; w < kMaxWarpsPerBlock; w += (int)blockDim.x) ftab.lok[w] = 0;
     if (threadIdx.x == 0) {
         ftab.ok = 0;
         kk_sh = *(volatile int *)&s.state[kStK];
@@ -2746,7 +2922,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
             lap(1);
-            if (!phase_update<kQueue>(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
+            if (!phase_update<kQueue, kLWarps>(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
                 overflow();
                 return;
             }
@@ -2805,7 +2981,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
             GridSync *gsync, u32 *counts, int *yield)
 {
     __shared__ Batch scratch[kWarps];
-    solve_team<kMinBlocks == 1 ? kEvalQueue : 0>(c, s, f, gsync, counts, grid_team(), scratch[threadIdx.x >> 5], yield);
+    solve_team<kMinBlocks == 1 ? kEvalQueue : 0, kMinBlocks == 1 ? kWarps : 0>(c, s, f, gsync, counts, grid_team(),
+                                                                                scratch[threadIdx.x >> 5], yield);
 }
 
 // SM-major number of the calling block (thread 0): SMs are ranked in the order
@@ -2870,8 +3047,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
         const int nsm = it.nblocks / map.per_sm;
         t.rank = (t.rank % map.per_sm) * nsm + t.rank / map.per_sm;
     }
-    solve_team<kMinBlocks == 1 ? kEvalQueue : 0>(it.c, it.s, it.f, it.gsync, it.counts, t, scratch[threadIdx.x >> 5],
-                                                 yield);
+    solve_team<kMinBlocks == 1 ? kEvalQueue : 0, kMinBlocks == 1 ? kWarps : 0>(it.c, it.s, it.f, it.gsync, it.counts, t,
+                                                                                scratch[threadIdx.x >> 5], yield);
 }
 
 }  // namespace
