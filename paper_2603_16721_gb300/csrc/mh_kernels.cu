@@ -132,17 +132,36 @@ __device__ __forceinline__ Key leaf_key(u64 s1, const int *po, int L, int o)
     return k;
 }
 
+// The warp's largest key: the largest score by two 32-bit warp reductions, then,
+// only when several lanes hold it, the smallest tuple among them, 32 bits at a
+// time; the winning lane's key is broadcast.
+__device__ __forceinline__ unsigned lanes_min_part(unsigned cand, u64 v, int lane)
+{
+    const bool in = (cand >> lane) & 1u;
+    const unsigned hi = __reduce_min_sync(kFull, in ? (unsigned)(v >> 32) : ~0u);
+    cand &= __ballot_sync(kFull, in && (unsigned)(v >> 32) == hi);
+    if (__popc(cand) == 1) return cand;
+    const bool in2 = (cand >> lane) & 1u;
+    const unsigned lo = __reduce_min_sync(kFull, in2 ? (unsigned)v : ~0u);
+    return cand & __ballot_sync(kFull, in2 && (unsigned)v == lo);
+}
 __device__ __forceinline__ Key warp_max_key(Key k)
 {
-    for (int off = 16; off; off >>= 1) {
-        Key o;
-        o.s = __shfl_xor_sync(kFull, k.s, off);
-        o.t0 = __shfl_xor_sync(kFull, k.t0, off);
-        o.t1 = __shfl_xor_sync(kFull, k.t1, off);
-        o.t2 = __shfl_xor_sync(kFull, k.t2, off);
-        if (key_better(o, k)) k = o;
-    }
-    return k;
+    const int lane = threadIdx.x & 31;
+    const unsigned hi = __reduce_max_sync(kFull, (unsigned)(k.s >> 32));
+    const bool top = (unsigned)(k.s >> 32) == hi;
+    const unsigned lo = __reduce_max_sync(kFull, top ? (unsigned)k.s : 0u);
+    unsigned cand = __ballot_sync(kFull, top && (unsigned)k.s == lo);
+    if (__popc(cand) > 1) cand = lanes_min_part(cand, k.t0, lane);
+    if (__popc(cand) > 1) cand = lanes_min_part(cand, k.t1, lane);
+    if (__popc(cand) > 1) cand = lanes_min_part(cand, k.t2, lane);
+    const int src = __ffs(cand) - 1;  // equal keys: any of them
+    Key o;
+    o.s = __shfl_sync(kFull, k.s, src);
+    o.t0 = __shfl_sync(kFull, k.t0, src);
+    o.t1 = __shfl_sync(kFull, k.t1, src);
+    o.t2 = __shfl_sync(kFull, k.t2, src);
+    return o;
 }
 
 __device__ __forceinline__ u64 warp_sum_u64(u64 v)
@@ -972,21 +991,33 @@ __device__ void phase_level1(const Cohort &c, const Solve &s, int round, const F
 
 // Per-warp cycle statistics of a phase (k = 0 expand, 1 leaf), for diagnostics,
 // into the block accumulator slots 5 (sum), 6 (max), 7 (count).
+__device__ __forceinline__ u64 *warp_cycle_slots()
+{
+    __shared__ u64 w[kMaxWarpsPerBlock];
+    return w;
+}
 __device__ __forceinline__ void warp_cycles(u64 *acc, long long t0, int lane)
 {
-    if (lane == 0) {
-        const u64 dt = (u64)(clock64() - t0);
-        atomicAdd(&acc[5], dt);
-        atomicMax(&acc[6], dt);
-        atomicAdd(&acc[7], 1ull);
-    }
+    (void)acc;
+    if (lane == 0) warp_cycle_slots()[threadIdx.x >> 5] = (u64)(clock64() - t0);
 }
 
 __device__ __forceinline__ void warp_cycles_flush(const Solve &s, const u64 *acc, int k, int par)
 {
-    if (threadIdx.x == 5 && acc[5]) atomicAdd(s.work + kWorkWarpSum + k, acc[5]);
-    if (threadIdx.x == 6 && acc[6]) atomicMax(s.work + (par ? kWorkWarpMaxOdd : kWorkWarpMax) + k, acc[6]);
-    if (threadIdx.x == 7 && acc[7]) atomicAdd(s.work + kWorkWarpN + k, acc[7]);
+    // after a block barrier: every warp's cycles of the phase are in its slot
+    (void)acc;
+    const int nw = (int)(blockDim.x >> 5);
+    if (threadIdx.x == 5 || threadIdx.x == 6) {
+        const u64 *w = warp_cycle_slots();
+        u64 sum = 0, mx = 0;
+        for (int i = 0; i < nw; ++i) {
+            sum += w[i];
+            mx = w[i] > mx ? w[i] : mx;
+        }
+        if (threadIdx.x == 5) atomicAdd(s.work + kWorkWarpSum + k, sum);
+        else atomicMax(s.work + (par ? kWorkWarpMaxOdd : kWorkWarpMax) + k, mx);
+    }
+    if (threadIdx.x == 7) atomicAdd(s.work + kWorkWarpN + k, (u64)nw);
 }
 
 // Depths 2 .. h-1: the non-empty children (all children with pruning off) of
@@ -2180,8 +2211,17 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     const u64 *Ush = io.Ush;
-    u64 *deep = acc + kAccDeep;  // deep[2l], deep[2l + 1]: depth l's two correction changes
     const int qcap = kQueue < 32 * nwarps ? kQueue : 32 * nwarps;
+    // the changes of the depths' corrections: per warp, summed over the warps at the
+    // end (one-block-per-SM builds), else block-wide in acc
+    __shared__ u64 wdeep[kLWarps > 0 ? kLWarps : 1][2 * kMaxH + 2];
+    u64 *deep = acc + kAccDeep;
+    if (kLWarps > 0)
+        for (int i = lane; i < 2 * kMaxH + 2; i += 32) wdeep[warp][i] = 0;
+    auto deep_add = [&](int i, u64 v) {
+        if (kLWarps > 0) wdeep[warp][i] += v;
+        else acc_add(deep, i, v);
+    };
     if (threadIdx.x == 0) {
         overflow = 0;
         qn = 0;
@@ -2199,22 +2239,31 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     const int sstride = force ? (int)blockDim.x : 32, sbase = force ? (int)threadIdx.x : lane;
     for (int smp = t.rank * sstride + sbase; side && smp < c.Nt; smp += t.size * sstride) {
         if (!in_mask(Ush, smp)) continue;
-        Key k;
+        Key k;  // the four words in one round trip
         k.s = __ldcg(&s.champ[smp].s);
-        if (k.s == 0 || k.s < best.s) continue;
         k.t0 = __ldcg(&s.champ[smp].t0);
         k.t1 = __ldcg(&s.champ[smp].t1);
         k.t2 = __ldcg(&s.champ[smp].t2);
-        if (key_better(k, best)) best = k;
+        if (k.s != 0 && key_better(k, best)) best = k;
     }
     // the lead's idle warps: the covered tumors leave the per-sample sums, and the
     // previous round's longest warps join the diagnostics
     if (t.rank == 0 && !side) {
-        if (*tot_pending) {
+        if (*tot_pending) {  // a warp per sum, its lanes over the tumors, four loads at a time
             const int h2 = 2 * h;
-            for (int i = (int)threadIdx.x; i < c.Nt * h2; i += gwarp * 32) {
-                const int smp = i / h2;
-                if (in_mask(Csh, smp)) atomicAdd(&tot[i - smp * h2], 0ull - __ldcg(s.ssum + i));
+            for (int e = warp; e < h2; e += gwarp) {
+                u64 v = 0;
+                for (int s0 = 0; s0 < c.Nt; s0 += 4 * 32) {
+                    u64 x[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int smp = s0 + 32 * k + lane;
+                        x[k] = (smp < c.Nt && in_mask(Csh, smp)) ? __ldcg(s.ssum + (size_t)smp * h2 + e) : 0ull;
+                    }
+                    v += x[0] + x[1] + x[2] + x[3];
+                }
+                v = warp_sum_u64(v);
+                if (lane == 0) tot[e] -= v;
             }
         }
         if (warp == 0 && lane < 2 && round > 0) {
@@ -2255,8 +2304,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         alive1 = warp_sum_u64(alive1);
         corrv = warp_sum_u64(corrv);
         if (lane == 0) {
-            acc_add(deep, 3, alive1);
-            acc_add(deep, 4, corrv);
+            deep_add(3, alive1);
+            deep_add(4, corrv);
         }
     }
     // kept records: depth 1 (h = 2) or 2 .. h-1; the deepest are the leaf parents
@@ -2558,9 +2607,9 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         dV = warp_sum_u64(dV);
         dL = warp_sum_u64(dL);
         if (lane == 0) {
-            acc_add(deep, 2 * l + 1, dA);
-            acc_add(deep, 2 * (l + 1), dV);
-            acc_add(deep, 2 * h + 1, dL);
+            deep_add(2 * l + 1, dA);
+            deep_add(2 * (l + 1), dV);
+            deep_add(2 * h + 1, dL);
         }
     }
     if (build_list && lane == 0) ft.lok[warp] = lfit ? 1 : 0;
@@ -2569,8 +2618,15 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     if (threadIdx.x == 0) *tot_pending = 0;
     const int e = (int)threadIdx.x - 32;  // depth e's two correction changes
     if (e >= 1 && e <= h) {
-        if (deep[2 * e]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, deep[2 * e]);
-        if (deep[2 * e + 1]) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2 + 1, deep[2 * e + 1]);
+        u64 d0 = deep[2 * e], d1 = deep[2 * e + 1];
+        if (kLWarps > 0) {
+            for (int w = 0; w < nwarps; ++w) {
+                d0 += wdeep[w][2 * e];
+                d1 += wdeep[w][2 * e + 1];
+            }
+        }
+        if (d0) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, d0);
+        if (d1) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2 + 1, d1);
     }
     warp_cycles_flush(s, acc, 1, io.par);
     block_commit_best(best, io.slots, t.rank, io.overwrite);
