@@ -469,7 +469,8 @@ struct Batch {
     int cx[33];                     // expansion: exclusive prefix sum of the lanes' child counts
     u16 po[kBatch][kMaxH - 1];      // leaves: ascending original indices of each record's prefix
     Key rb[kBatch];                 // incremental rounds: per leaf parent, its best leaf (TP >= 2)
-    u64 rc[kBatch];                 //   and the sum of TP - 1 over those leaves
+    u64 rc[kBatch];                 //   and the sum of TP - 1 over those leaves (rb[j].s holds
+                                    //   the packed best while a listed record's items merge)
 };
 
 // Depth-1 node of gene g (search order) built from its rows and U: y_1 = U & x_g,
@@ -1812,8 +1813,8 @@ __device__ __noinline__ void phase_sample_sums(const Cohort &c, const Solve &s, 
     }
 }
 
-// tot[0 .. 2h) = the per-sample sums over the uncovered tumors (the block's copy Ush).
-__device__ void block_sample_totals(const Cohort &c, const Solve &s, const u64 *Ush, u64 *tot)
+// tot[0 .. 2h) = the per-sample sums over all tumors.
+__device__ void block_sample_totals(const Cohort &c, const Solve &s, u64 *tot)
 {
     const int h2 = 2 * s.h, lane = threadIdx.x & 31;
     if (threadIdx.x < 2 * kMaxH) tot[threadIdx.x] = 0;
@@ -1821,7 +1822,7 @@ __device__ void block_sample_totals(const Cohort &c, const Solve &s, const u64 *
     for (int k = 0; k < h2; ++k) {
         u64 v = 0;
         for (int smp = threadIdx.x; smp < c.Nt; smp += blockDim.x)
-            if ((Ush[smp >> 6] >> (smp & 63)) & 1ull) v += __ldcg(s.ssum + (size_t)smp * h2 + k);
+            v += __ldcg(s.ssum + (size_t)smp * h2 + k);
         v = warp_sum_u64(v);
         if (lane == 0 && v) atomicAdd(&tot[k], v);
     }
@@ -1954,10 +1955,18 @@ __device__ bool refresh_record(const Cohort &c, const u64 *Ush, const u64 *Csh, 
 // bit-sliced TP counts; the normal columns, read only when m2 is non-empty, give
 // FP; the children in m2 are scored into best.
 constexpr int kEvalLoads = 8;
-__device__ __forceinline__ void leaf_item_eval(const Cohort &c, const Solve &s, const Batch &b, int j, int wi, u64 rw,
-                                               int L, u64 &corr, Key &best)
+// The leaves of one prefix, packed: (score + 1) << 16 | (0xffff - o), o the leaf
+// gene's original index.  Inserting a smaller o into the same sorted prefix gives
+// the lexicographically smaller tuple, so among the leaves of one prefix the larger
+// packed value is the larger key (scores below 2^44, genes below 2^16).
+__device__ __forceinline__ u64 pack_leaf(u64 s1, int o) { return (s1 << 16) | (u64)(0xffff - o); }
+__device__ __forceinline__ Key unpack_leaf(u64 p, const int *po, int L)
 {
-    const Rec &r = b.r[j];
+    return leaf_key(p >> 16, po, L, 0xffff - (int)(p & 0xffffull));
+}
+__device__ __forceinline__ void leaf_item_eval(const Cohort &c, const Solve &s, const Rec &r, int wi, u64 rw, u64 &corr,
+                                               u64 &pbest)
+{
     const int ky = r.ky, kn = r.kn;
     const int pt = bit_length(ky), pn = kn ? bit_length(kn) : 0;
     u64 tpl[kPlanesT] = {0, 0, 0, 0, 0};
@@ -1987,18 +1996,15 @@ __device__ __forceinline__ void leaf_item_eval(const Cohort &c, const Solve &s, 
 #pragma unroll
         for (int k = 0; k < kEvalLoads; ++k) planes_add(fpl, x[k], pn);
     }
-    int po[kMaxH - 1];
-#pragma unroll
-    for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[j][q] : 0;
     while (m2) {
         const int bt = __ffsll((long long)m2) - 1;
         m2 &= m2 - 1;
         const int tp = planes_get(tpl, bt, pt);
         const int fp = planes_get(fpl, bt, pn);
         const u64 s1 = s.a_num * (u64)tp + s.a_den * (u64)(c.Nn - fp) + 1;
-        if (s1 < best.s) continue;
-        const Key k = leaf_key(s1, po, L, c.orig[wi * 64 + bt]);
-        if (key_better(k, best)) best = k;
+        if (s1 < (pbest >> 16)) continue;
+        const u64 pk = pack_leaf(s1, c.orig[wi * 64 + bt]);
+        pbest = pk > pbest ? pk : pbest;
     }
 }
 
@@ -2006,24 +2012,46 @@ __device__ __forceinline__ void leaf_item_eval(const Cohort &c, const Solve &s, 
 // spare bytes (prefixes of up to kPadGenes genes).
 constexpr int kPadGenes = 6;
 __device__ __forceinline__ u16 *pad_po(Rec &r) { return reinterpret_cast<u16 *>(r.pad); }
+// The ascending original indices of a leaf parent's L prefix genes.
+__device__ __forceinline__ void record_po(const Cohort &c, Rec &r, int L, int *po)
+{
+#pragma unroll
+    for (int q = 0; q < kMaxH - 1; ++q) po[q] = 0;
+    if (L <= kPadGenes) {
+        for (int q = 0; q < L; ++q) po[q] = pad_po(r)[q];
+        return;
+    }
+    for (int q = 0; q < L; ++q) {
+        const int v = c.orig[prefix_gene(r.p, q)];
+        int k = q - 1;
+        while (k >= 0 && po[k] > v) {
+            po[k + 1] = po[k];
+            --k;
+        }
+        po[k + 1] = v;
+    }
+}
 
 // Merges the per-lane keys of one item step into the records' best keys: items of
 // a step sit on the lanes in record order, so a segmented warp maximum leaves each
 // record's best on its first lane, which merges it into rb.
-__device__ __forceinline__ void merge_item_keys(Batch &b, int jr, Key k, int lane)
+__device__ __forceinline__ void merge_item_keys(Batch &b, int jr, u64 p, u64 corr, int lane)
 {
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        Key o;
-        o.s = __shfl_down_sync(kFull, k.s, off);
-        o.t0 = __shfl_down_sync(kFull, k.t0, off);
-        o.t1 = __shfl_down_sync(kFull, k.t1, off);
-        o.t2 = __shfl_down_sync(kFull, k.t2, off);
+        const u64 po = __shfl_down_sync(kFull, p, off);
+        const u64 co = __shfl_down_sync(kFull, corr, off);
         const int jo = __shfl_down_sync(kFull, jr, off);
-        if (lane + off < 32 && jo == jr && key_better(o, k)) k = o;
+        if (lane + off < 32 && jo == jr) {
+            p = po > p ? po : p;
+            corr += co;
+        }
     }
     const int jp = __shfl_up_sync(kFull, jr, 1);
-    if (jr >= 0 && (lane == 0 || jp != jr) && k.s != 0 && key_better(k, b.rb[jr])) b.rb[jr] = k;
+    if (jr >= 0 && (lane == 0 || jp != jr)) {
+        b.rc[jr] += corr;
+        if (p > b.rb[jr].s) b.rb[jr].s = p;
+    }
     __syncwarp();
 }
 
@@ -2072,16 +2100,21 @@ __device__ void leaf_parents_eval(const Cohort &c, const Solve &s, Batch &b, boo
     for (int tb = 0; tb < total; tb += 32) {
         const int t = tb + lane;
         const bool valid = t < total;
-        Key ib = key_empty();
+        u64 ib = 0, corr = 0;
         if (valid) {
             while (t >= b.off[j + 1]) ++j;
             const int wi = (b.lo[j] >> 6) + (t - b.off[j]);
-            u64 corr = 0;
-            leaf_item_eval(c, s, b, j, wi, range_word(wi, b.lo[j], b.hi[j]), L, corr, ib);
-            if (corr) atomicAdd(&b.rc[j], corr);
+            leaf_item_eval(c, s, b.r[j], wi, range_word(wi, b.lo[j], b.hi[j]), corr, ib);
         }
-        merge_item_keys(b, valid ? j : -1, ib, lane);
+        merge_item_keys(b, valid ? j : -1, ib, corr, lane);
     }
+    if (live && !dense && b.rb[lane].s != 0) {  // the packed best of each listed record as its key
+        int po[kMaxH - 1];
+#pragma unroll
+        for (int q = 0; q < kMaxH - 1; ++q) po[q] = q < L ? b.po[lane][q] : 0;
+        b.rb[lane] = unpack_leaf(b.rb[lane].s, po, L);
+    }
+    __syncwarp();
     // unlisted records: the whole warp, one leaf gene per lane, on the rows
     while (dmask) {
         const int jd = __ffs(dmask) - 1;
@@ -2195,8 +2228,7 @@ struct LiveLists {
 };
 template <int kQueue, int kLWarps>
 __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const Frontiers &f, const u32 *counts,
-                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft,
-                             u64 *tot, int *tot_pending)
+                             Batch &b, const Team &t, const RoundIO &io, const u64 *Csh, bool force, FrontTab &ft)
 {
     __shared__ u64 acc[kAccN];
     __shared__ int overflow;
@@ -2206,6 +2238,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     __shared__ u64 qlco[kQueue > 0 ? kQueue : 1];
     __shared__ short qidx[kQueue > 0 ? kQueue : 1];  // list entry of a queued record (-1: none)
     __shared__ signed char qwarp[kQueue > 0 ? kQueue : 1];
+    __shared__ int qlo[kQueue > 0 ? kQueue : 1], qtoff[kQueue + 1];  // first leaf gene; tasks' prefix
+    __shared__ u64 qbest[kQueue > 0 ? kQueue : 1], qcorr[kQueue > 0 ? kQueue : 1];
     __shared__ LiveLists<(kLWarps > 0 ? kLWarps : 1)> lv;
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -2246,26 +2280,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         k.t2 = __ldcg(&s.champ[smp].t2);
         if (k.s != 0 && key_better(k, best)) best = k;
     }
-    // the lead's idle warps: the covered tumors leave the per-sample sums, and the
-    // previous round's longest warps join the diagnostics
+    // the lead's idle warps: the previous round's longest warps join the diagnostics
     if (t.rank == 0 && !side) {
-        if (*tot_pending) {  // a warp per sum, its lanes over the tumors, four loads at a time
-            const int h2 = 2 * h;
-            for (int e = warp; e < h2; e += gwarp) {
-                u64 v = 0;
-                for (int s0 = 0; s0 < c.Nt; s0 += 4 * 32) {
-                    u64 x[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int smp = s0 + 32 * k + lane;
-                        x[k] = (smp < c.Nt && in_mask(Csh, smp)) ? __ldcg(s.ssum + (size_t)smp * h2 + e) : 0ull;
-                    }
-                    v += x[0] + x[1] + x[2] + x[3];
-                }
-                v = warp_sum_u64(v);
-                if (lane == 0) tot[e] -= v;
-            }
-        }
         if (warp == 0 && lane < 2 && round > 0) {
             const int mx = (((round - 1) & 1) ? kWorkWarpMaxOdd : kWorkWarpMax) + lane;
             s.work[kWorkWarpMaxSum + lane] += __ldcg(&s.work[mx]);
@@ -2275,7 +2291,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     // depth 1
     if (side) {
         const int last1 = c.G - h, hi2 = c.G - h + 1;
-        u64 alive1 = 0, corrv = 0;
+        u64 alive1 = 0, corrv = 0, sv = 0;
         if (force) {  // the genes of a contiguous share, one per thread
             const int g0 = (int)((long long)c.G * t.rank / t.size), g1 = (int)((long long)c.G * (t.rank + 1) / t.size);
             for (int g = g0 + (int)threadIdx.x; g < g1; g += (int)blockDim.x) {
@@ -2286,9 +2302,18 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     if (k >= 2) corrv += (u64)(k - 1) * (u64)(hi2 - g);
                 }
             }
-        } else {  // each gene of a covered tumor loses one uncovered tumor
+        } else {
+            // each gene of a covered tumor loses one uncovered tumor, and the tumor's
+            // per-sample sums of depths 2..h leave the totals: they join the running
+            // totals that the end of the round subtracts (lane k < h - 1: the visited
+            // sum of depth k + 2, lane h - 1 + k: its surviving sum)
+            const int h2 = 2 * h;
+            const bool sl = lane < 2 * (h - 1);
+            const int sd = lane < h - 1 ? lane + 2 : lane - (h - 1) + 2;
+            const int sidx = lane < h - 1 ? h + sd - 1 : sd - 1;
             for (int smp = t.rank; smp < c.Nt; smp += t.size) {
                 if (!in_mask(Csh, smp)) continue;
+                if (sl) sv += __ldcg(s.ssum + (size_t)smp * h2 + sidx);
                 const u32 off = __ldg(c.SO + smp);
                 const int m = (int)(__ldg(c.SO + smp + 1) - off);
                 for (int q = lane; q < m; q += 32) {
@@ -2307,6 +2332,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             deep_add(3, alive1);
             deep_add(4, corrv);
         }
+        __syncwarp();
+        if (sv) deep_add(lane < h - 1 ? 2 * (lane + 2) : 2 * (lane - (h - 1) + 2) + 1, sv);
     }
     // kept records: depth 1 (h = 2) or 2 .. h-1; the deepest are the leaf parents
     if (force || !ft.ok) {  // their sizes and shard offsets, once per launch
@@ -2436,7 +2463,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     Lls[pos] = 0;
                 }
                 bool queued = false;
-                if (eval) {
+                if (eval && !is_dense(r.ky, r.kn)) {
                     const int qp = atomicAdd(&qn, 1);
                     if (qp < qcap) {
                         copy_rec(&qrec[qp], &r);
@@ -2544,7 +2571,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     // changed leaf parents go to the block's queue (spread over its warps
                     // below); what does not fit is evaluated by this warp
                     bool queued = false;
-                    if (eval && !force) {
+                    if (eval && !force && !is_dense(r.ky, r.kn)) {
                         const int pos = atomicAdd(&qn, 1);
                         if (pos < qcap) {
                             copy_rec(&qrec[pos], &r);
@@ -2580,26 +2607,61 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             }
         }
         if (leafp) {
-            // the queued leaf parents, whole records to warps in turn (entry q to warp
-            // q mod nwarps, lane q / nwarps), so that the block's changes spread over all
-            // of its warps; at most 32 entries per warp (qcap)
+            // the queued leaf parents: their (record, column word) items spread over all
+            // warps of the block, in tasks of up to 32 items of one record; a record's
+            // best leaf (packed) and its sum of TP - 1 meet in shared memory
             __syncthreads();
             const int nq = qn < qcap ? qn : qcap;
-            const int q = warp + nwarps * lane;
-            const bool live = q < nq;
-            if (__ballot_sync(kFull, live)) {
-                if (live) copy_rec(&b.r[lane], &qrec[q]);
-                __syncwarp();
-                leaf_parents_eval(c, s, b, live, l, lane);
-                if (live) {
-                    const Key kb = b.rb[lane];
-                    f.lb[l][qslot[q]] = kb;
-                    f.lc[l][qslot[q]] = b.rc[lane];
-                    if (kLWarps > 0 && qidx[q] >= 0) lv.ls[qwarp[q]][qidx[q]] = kb.s;
-                    dL += b.rc[lane] - qlco[q];
+            if (nq > 0) {
+                if (warp == 0) {
+                    int base = 0;
+                    for (int j0 = 0; j0 < nq; j0 += 32) {
+                        const int j = j0 + lane;
+                        int tasks = 0;
+                        if (j < nq) {
+                            const int lo = prefix_gene(qrec[j].p, l - 1) + 1;
+                            qlo[j] = lo;
+                            tasks = (((c.G - 1) >> 6) - (lo >> 6) + 1 + 31) >> 5;
+                            qbest[j] = 0;
+                            qcorr[j] = 0;
+                        }
+                        const int incl = warp_incl_scan(tasks, lane);
+                        if (j < nq) qtoff[j + 1] = base + incl;
+                        base += __shfl_sync(kFull, incl, 31);
+                    }
+                    if (lane == 0) qtoff[0] = 0;
+                }
+                __syncthreads();
+                const int T = qtoff[nq], nwg = ((c.G - 1) >> 6) + 1;
+                for (int tau = warp; tau < T; tau += nwarps) {
+                    int j = 0;
+                    while (qtoff[j + 1] <= tau) ++j;
+                    const int lo = qlo[j];
+                    const int it = (tau - qtoff[j]) * 32 + lane, wi = (lo >> 6) + it;
+                    u64 pk = 0, corr = 0;
+                    if (wi < nwg) leaf_item_eval(c, s, qrec[j], wi, range_word(wi, lo, c.G - 1), corr, pk);
+                    pk = warp_max_u64(pk);
+                    corr = warp_sum_u64(corr);
+                    if (lane == 0) {
+                        if (pk) atomicMax(&qbest[j], pk);
+                        if (corr) atomicAdd(&qcorr[j], corr);
+                    }
+                }
+                __syncthreads();
+                const int j = (int)threadIdx.x;
+                if (j < nq) {
+                    Key kb = key_empty();
+                    if (qbest[j]) {
+                        int po[kMaxH - 1];
+                        record_po(c, qrec[j], l, po);
+                        kb = unpack_leaf(qbest[j], po, l);
+                    }
+                    f.lb[l][qslot[j]] = kb;
+                    f.lc[l][qslot[j]] = qcorr[j];
+                    if (kLWarps > 0 && qidx[j] >= 0) lv.ls[qwarp[j]][qidx[j]] = kb.s;
+                    dL += qcorr[j] - qlco[j];
                     if (kb.s != 0 && key_better(kb, best)) best = kb;
                 }
-                __syncwarp();
             }
         }
         if (build_list && lane == 0) ft.lcnt[warp][l] = (short)(lfill - ft.lbase[warp][l]);
@@ -2615,7 +2677,6 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     if (build_list && lane == 0) ft.lok[warp] = lfit ? 1 : 0;
     warp_cycles(acc, t0, lane);
     __syncthreads();
-    if (threadIdx.x == 0) *tot_pending = 0;
     const int e = (int)threadIdx.x - 32;  // depth e's two correction changes
     if (e >= 1 && e <= h) {
         u64 d0 = deep[2 * e], d1 = deep[2 * e + 1];
@@ -2752,14 +2813,13 @@ __device__ bool end_of_round(const Cohort &c, const Solve &s, int round, const K
 // covers, applies DelCols to the block's copy of U and keeps the covered tumors
 // (Csh) for the next round's update.  The lead block (rank 0) also records the
 // selection and finishes the round's counters: depth 1 from its surviving count,
-// depths 2..h as the per-sample sums over the round's U (tot) minus the running
-// totals of the corrections (run, to which it adds the round's changes, read
-// together with the slots).  Taking the covered tumors out of tot waits for the
-// lead's idle warps in the next round's update (*tot_pending).  kk: the lead's
+// depths 2..h as the per-sample sums over all tumors (tot) minus the running
+// totals (run, to which it adds the round's changes, read together with the
+// slots): the corrections, and the per-sample sums of the tumors covered so far,
+// which each round's update adds for the tumors the last winner covered.  kk: the lead's
 // count of selections; maxr: the round limit.  Returns true when the solve is done.
 __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, const Key *slots, int nslots,
-                                 const Team &t, u64 *Ush, const u64 *tot, u64 *Csh, u64 *run, int *kk, int maxr,
-                                 int *tot_pending)
+                                 const Team &t, u64 *Ush, const u64 *tot, u64 *Csh, u64 *run, int *kk, int maxr)
 {
     __shared__ int os[kMaxH];
     __shared__ int done_sh;
@@ -2854,7 +2914,6 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
             if (lead) {
                 s.state[kStRound] = round + 1;
                 if (done) s.state[kStDone] = 1;
-                *tot_pending = done ? 0 : 1;
             }
         }
     }
@@ -2881,7 +2940,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     __shared__ u64 Csh[kMaxWords];
     __shared__ u64 run[2 * (kMaxH + 1)];  // incremental rounds, rank 0: the corrections' running totals
     __shared__ FrontTab ftab;
-    __shared__ int fm_sh, kk_sh, tot_pending;
+    __shared__ int fm_sh, kk_sh;
     const int h = s.h;
     const bool timer = t.rank == 0 && threadIdx.x == 0;
     u64 tm = timer ? global_ns() : 0;
@@ -2899,7 +2958,6 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
     if (threadIdx.x == 0) {
         ftab.ok = 0;
         kk_sh = *(volatile int *)&s.state[kStK];
-        tot_pending = 0;
     }
     // start of a launch: U and the candidates left by the previous round
     for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x) Ush[i] = i < c.WTp ? __ldcg(&s.U[i]) : 0ull;
@@ -2929,7 +2987,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
             if (!__ldcg(s.champ_ok + i)) fm_sh = 0;
         __syncthreads();
         fm = fm_sh != 0;
-        if (fm && t.rank == 0) block_sample_totals(c, s, Ush, tot);
+        if (fm && t.rank == 0) block_sample_totals(c, s, tot);
         // incremental rounds: the tumors covered by the last round's winner
         for (int i = threadIdx.x; i < kMaxWords; i += blockDim.x)
             Csh[i] = (fm && round > 0 && i < c.WTp) ? __ldcg(&s.cov[i]) : 0ull;
@@ -2978,7 +3036,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
                 }
             }
             lap(1);
-            if (!phase_update<kQueue, kLWarps>(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab, tot, &tot_pending)) {
+            if (!phase_update<kQueue, kLWarps>(c, s, round, f, counts, b, t, io, Csh, round == 0, ftab)) {
                 overflow();
                 return;
             }
@@ -3003,8 +3061,7 @@ __device__ void solve_team(const Cohort &c, const Solve &s, const Frontiers &f, 
         if (!grid_sync(gsync, s.state, t.size, yield)) return;
         const bool stop = yield && *(volatile int *)&gsync->flag;
         lap(2);
-        const bool done = fm ? end_of_round_inc(c, s, round, io.slots, t.size, t, Ush, tot, Csh, run, &kk_sh, maxr,
-                                                &tot_pending)
+        const bool done = fm ? end_of_round_inc(c, s, round, io.slots, t.size, t, Ush, tot, Csh, run, &kk_sh, maxr)
                              : end_of_round(c, s, round, io.slots, t.size, t, Ush, cand_sh, s.best_hint + (par ^ 1));
         lap(3);
         if (done) {
