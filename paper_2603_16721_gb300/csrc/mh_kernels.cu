@@ -1553,6 +1553,21 @@ __global__ void __launch_bounds__(kThreads) k_finalize_split(const __grid_consta
 // and a block learns k from the count it found.  With `sample`, a block that finds
 // *sample set raises g->flag before it arrives; after the barrier every block reads
 // the same flag (the OR of what the blocks found), so they take the same decision.
+// Arrival with release and acquire semantics at GPU scope (the block's writes,
+// ordered before thread 0 by the block barrier, become visible to the blocks that
+// see the arrival), and the waiters' acquiring load.
+__device__ __forceinline__ unsigned arrive_acq_rel(unsigned *p)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned load_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, const int *sample = nullptr)
 {
     __shared__ int ok;
@@ -1560,11 +1575,11 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, 
     if (threadIdx.x == 0) {
         ok = 1;
         if (sample && *(volatile const int *)sample) *(volatile int *)&g->flag = 1;
-        __threadfence();
-        const unsigned old = atomicAdd(&g->arrived, 1u);
+        const unsigned old = arrive_acq_rel(&g->arrived);
         const unsigned target = (old / (unsigned)nblocks + 1u) * (unsigned)nblocks;
+        // the last block to arrive goes on at once; the others wait for the count
         unsigned long long spins = 0;
-        while ((int)(*(volatile unsigned *)&g->arrived - target) < 0) {
+        while (old + 1u != target && (int)(load_acquire(&g->arrived) - target) < 0) {
             __nanosleep(32);
             if (++spins > (1ull << 25)) {
                 atomicExch(&state[kStError], kErrTimeout);
@@ -1572,7 +1587,6 @@ __device__ __forceinline__ bool grid_sync(GridSync *g, int *state, int nblocks, 
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
