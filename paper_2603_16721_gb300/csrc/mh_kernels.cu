@@ -190,9 +190,16 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 
 // Block-wide best key -> slots[rank]: stored (overwrite), or merged with what an
 // earlier launch of the same round left there.  All threads of the block must call it.
+// The warps' best keys on their way to a block maximum (one array for every phase:
+// each use ends at a block barrier before the next begins).
+__device__ __forceinline__ Key *warp_keys()
+{
+    __shared__ Key w[kMaxWarpsPerBlock];
+    return w;
+}
 __device__ void block_commit_best(Key best, Key *slots, int rank, bool overwrite)
 {
-    __shared__ Key wbest[kMaxWarpsPerBlock];
+    Key *wbest = warp_keys();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     best = warp_max_key(best);
     if (lane == 0) wbest[warp] = best;
@@ -2689,22 +2696,45 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         }
     }
     if (build_list && lane == 0) ft.lok[warp] = lfit ? 1 : 0;
+    // one block barrier, then three jobs on three warps: the block's best to its slot
+    // (first, the round's grid barrier waits for it), the depths' correction changes
+    // to the round's counters, the phase's warp cycles to the diagnostics
+    Key *wkey = warp_keys();
     warp_cycles(acc, t0, lane);
-    __syncthreads();
-    const int e = (int)threadIdx.x - 32;  // depth e's two correction changes
-    if (e >= 1 && e <= h) {
-        u64 d0 = deep[2 * e], d1 = deep[2 * e + 1];
-        if (kLWarps > 0) {
-            for (int w = 0; w < nwarps; ++w) {
-                d0 += wdeep[w][2 * e];
-                d1 += wdeep[w][2 * e + 1];
-            }
-        }
-        if (d0) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2, d0);
-        if (d1) atomicAdd(s.cnt + ((size_t)round * h + (e - 1)) * 2 + 1, d1);
+    {
+        const Key wb = warp_max_key(best);
+        if (lane == 0) wkey[warp] = wb;
     }
-    warp_cycles_flush(s, acc, 1, io.par);
-    block_commit_best(best, io.slots, t.rank, io.overwrite);
+    __syncthreads();
+    if (warp == 0) {
+        const Key k = warp_max_key(lane < nwarps ? wkey[lane] : key_empty());
+        if (lane == 0 && io.overwrite) {
+            io.slots[t.rank] = k;
+        } else if (lane == 0 && k.s != 0) {
+            const Key old = io.slots[t.rank];
+            if (key_better(k, old)) io.slots[t.rank] = k;
+        }
+    }
+    if (warp == (nwarps > 1 ? 1 : 0)) {  // deep[i], i = 2e and 2e + 1 for depths e = 1 .. h
+        const int i = lane + 2;
+        if (i <= 2 * h + 1) {
+            u64 d = deep[i];
+            if (kLWarps > 0) {
+#pragma unroll 4
+                for (int w = 0; w < nwarps; ++w) d += wdeep[w][i];
+            }
+            if (d) atomicAdd(s.cnt + ((size_t)round * h + (i / 2 - 1)) * 2 + (i & 1), d);
+        }
+    }
+    if (warp == (nwarps > 2 ? 2 : nwarps - 1)) {
+        const u64 v = lane < nwarps ? warp_cycle_slots()[lane] : 0ull;
+        const u64 sum = warp_sum_u64(v), mx = warp_max_u64(v);
+        if (lane == 0) {
+            atomicAdd(s.work + kWorkWarpSum + 1, sum);
+            atomicMax(s.work + (io.par ? kWorkWarpMaxOdd : kWorkWarpMax) + 1, mx);
+            atomicAdd(s.work + kWorkWarpN + 1, (u64)nwarps);
+        }
+    }
     return true;
 }
 
@@ -2837,18 +2867,13 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
 {
     __shared__ int os[kMaxH];
     __shared__ int done_sh;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Key *wbest = warp_keys();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int h = s.h;
     const bool lead = t.rank == 0;
-    if (warp == 0) {
-        u64 dv = 0, da = 0;
-        u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
-        if (lead && lane < h) {
-            dv = __ldcg(cv);
-            da = __ldcg(cv + 1);
-        }
+    {  // the slots, one per thread (all loads of a thread in flight together)
         Key best = key_empty();
-        for (int i = lane; i < nslots; i += 32) {
+        for (int i = (int)threadIdx.x; i < nslots; i += (int)blockDim.x) {
             Key k;
             k.s = __ldcg(&slots[i].s);
             k.t0 = __ldcg(&slots[i].t0);
@@ -2857,6 +2882,17 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
             if (key_better(k, best)) best = k;
         }
         best = warp_max_key(best);
+        if (lane == 0) wbest[warp] = best;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        u64 dv = 0, da = 0;
+        u64 *cv = s.cnt + ((size_t)round * h + lane) * 2;
+        if (lead && lane < h) {
+            dv = __ldcg(cv);
+            da = __ldcg(cv + 1);
+        }
+        const Key best = warp_max_key(lane < nwarps ? wbest[lane] : key_empty());
         bool done = true;
         u64 ycov = 0;
         if (best.s != 0) {
@@ -2881,11 +2917,8 @@ __device__ bool end_of_round_inc(const Cohort &c, const Solve &s, int round, con
                 for (int i = 0; i < kMaxH; ++i)
                     if (i < h) n &= __ldg(NR + (size_t)ri[i] * c.WNp + lane);
             }
-            int tp = __popcll(y), fp = __popcll(n);
-            for (int off = 16; off; off >>= 1) {
-                tp += __shfl_xor_sync(kFull, tp, off);
-                fp += __shfl_xor_sync(kFull, fp, off);
-            }
+            const int tp = (int)__reduce_add_sync(kFull, (unsigned)__popcll(y));
+            const int fp = (int)__reduce_add_sync(kFull, (unsigned)__popcll(n));
             if (lane < c.Wt) {
                 ycov = y;
                 u &= ~y;
