@@ -2259,8 +2259,17 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     __shared__ u64 qlco[kQueue > 0 ? kQueue : 1];
     __shared__ short qidx[kQueue > 0 ? kQueue : 1];  // list entry of a queued record (-1: none)
     __shared__ signed char qwarp[kQueue > 0 ? kQueue : 1];
-    __shared__ int qlo[kQueue > 0 ? kQueue : 1], qtoff[kQueue + 1];  // first leaf gene; tasks' prefix
-    __shared__ u64 qbest[kQueue > 0 ? kQueue : 1], qcorr[kQueue > 0 ? kQueue : 1];
+    __shared__ int qlo[kQueue > 0 ? kQueue : 1], qtasks[kQueue > 0 ? kQueue : 1];  // first leaf gene, tasks
+    __shared__ u64 qbest[kQueue > 0 ? kQueue : 1];
+    __shared__ u32 qcorr[kQueue > 0 ? kQueue : 1];  // a record's sum of TP - 1 stays below 2^27
+    // a queued leaf parent's first leaf gene and tasks of 32 column words (set when it is queued)
+    auto queue_tasks = [&](int q, const Rec &r, int L) {
+        const int lo = prefix_gene(r.p, L - 1) + 1;
+        qlo[q] = lo;
+        qtasks[q] = (((c.G - 1) >> 6) - (lo >> 6) + 1 + 31) >> 5;
+        qbest[q] = 0;
+        qcorr[q] = 0;
+    };
     __shared__ LiveLists<(kLWarps > 0 ? kLWarps : 1)> lv;
     const long long t0 = clock64();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -2425,18 +2434,41 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             }
             __syncwarp();
             if (lane == 0) ft.lcnt[warp][l] = (short)wpos;
+            // the untouched records' best cached leaves: a lane's first record with the
+            // warp's largest cached score is read now and merged after the touched
+            // records (their loads overlap); further ties, rare, after that
             const u64 wmax = leafp ? warp_max_u64(lmax) : 0ull;
-            if (wmax != 0 && wmax >= best.s) {  // the untouched records' best cached leaves
+            int hitj = -1;
+            bool more = false;
+            Key kc = key_empty();
+            if (wmax != 0) {  // warp-uniform (the lanes' bests differ)
+                const bool want = wmax >= best.s;
                 for (int j0 = 0; j0 < wpos; j0 += 32) {
                     const int j = j0 + lane;
-                    if (j < wpos && Lls[j] == wmax && (Lsig[j] & csig) == 0) {
-                        const u32 sl = Lslot[j];
-                        Key kc;
-                        kc.s = wmax;
-                        kc.t0 = __ldcg(&f.lb[l][sl].t0);
-                        kc.t1 = __ldcg(&f.lb[l][sl].t1);
-                        kc.t2 = __ldcg(&f.lb[l][sl].t2);
-                        if (key_better(kc, best)) best = kc;
+                    if (want && j < wpos && Lls[j] == wmax && (Lsig[j] & csig) == 0) {
+                        if (hitj < 0) hitj = j;
+                        else more = true;
+                    }
+                }
+                if (hitj >= 0) {
+                    const u32 sl = Lslot[hitj];
+                    kc.s = wmax;
+                    kc.t0 = __ldcg(&f.lb[l][sl].t0);
+                    kc.t1 = __ldcg(&f.lb[l][sl].t1);
+                    kc.t2 = __ldcg(&f.lb[l][sl].t2);
+                }
+                if (__any_sync(kFull, more)) {  // before any touched record changes its entry
+                    for (int j0 = 0; j0 < wpos; j0 += 32) {
+                        const int j = j0 + lane;
+                        if (j < wpos && j != hitj && Lls[j] == wmax && (Lsig[j] & csig) == 0) {
+                            const u32 sl = Lslot[j];
+                            Key k2;
+                            k2.s = wmax;
+                            k2.t0 = __ldcg(&f.lb[l][sl].t0);
+                            k2.t1 = __ldcg(&f.lb[l][sl].t1);
+                            k2.t2 = __ldcg(&f.lb[l][sl].t2);
+                            if (key_better(k2, best)) best = k2;
+                        }
                     }
                 }
             }
@@ -2488,6 +2520,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     const int qp = atomicAdd(&qn, 1);
                     if (qp < qcap) {
                         copy_rec(&qrec[qp], &r);
+                        queue_tasks(qp, r, l);
                         qslot[qp] = sl;
                         qlco[qp] = lco;
                         qidx[qp] = (short)(ft.lbase[warp][l] + pos);
@@ -2509,6 +2542,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                     __syncwarp();
                 }
             }
+            if (hitj >= 0 && key_better(kc, best)) best = kc;
         }
         for (u64 k = 0; !use_list && rk + B * ((u64)warp + W * 32ull * kScanIlp * k) < n; ++k) {
             u32 slot[kScanIlp];
@@ -2596,6 +2630,7 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
                         const int pos = atomicAdd(&qn, 1);
                         if (pos < qcap) {
                             copy_rec(&qrec[pos], &r);
+                            queue_tasks(pos, r, l);
                             qslot[pos] = slot[u];
                             qlco[pos] = lco;
                             qidx[pos] = (short)lpos;
@@ -2634,38 +2669,26 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             __syncthreads();
             const int nq = qn < qcap ? qn : qcap;
             if (nq > 0) {
-                if (warp == 0) {
-                    int base = 0;
-                    for (int j0 = 0; j0 < nq; j0 += 32) {
-                        const int j = j0 + lane;
-                        int tasks = 0;
-                        if (j < nq) {
-                            const int lo = prefix_gene(qrec[j].p, l - 1) + 1;
-                            qlo[j] = lo;
-                            tasks = (((c.G - 1) >> 6) - (lo >> 6) + 1 + 31) >> 5;
-                            qbest[j] = 0;
-                            qcorr[j] = 0;
-                        }
-                        const int incl = warp_incl_scan(tasks, lane);
-                        if (j < nq) qtoff[j + 1] = base + incl;
-                        base += __shfl_sync(kFull, incl, 31);
-                    }
-                    if (lane == 0) qtoff[0] = 0;
-                }
-                __syncthreads();
-                const int T = qtoff[nq], nwg = ((c.G - 1) >> 6) + 1;
+                // every warp forms the records' task prefix itself (nq <= 64: two chunks)
+                const int i0 = lane < nq ? qtasks[lane] : 0, i1 = lane + 32 < nq ? qtasks[lane + 32] : 0;
+                const int inc0 = warp_incl_scan(i0, lane);
+                const int inc1 = __shfl_sync(kFull, inc0, 31) + warp_incl_scan(i1, lane);
+                const int T = __shfl_sync(kFull, inc1, 31), nwg = ((c.G - 1) >> 6) + 1;
                 for (int tau = warp; tau < T; tau += nwarps) {
-                    int j = 0;
-                    while (qtoff[j + 1] <= tau) ++j;
+                    // its record: the number of records whose tasks end at or before tau
+                    const int j = __popc(__ballot_sync(kFull, lane < nq && inc0 <= tau)) +
+                                  __popc(__ballot_sync(kFull, lane + 32 < nq && inc1 <= tau));
+                    const int e0 = __shfl_sync(kFull, inc0, (j - 1) & 31), e1 = __shfl_sync(kFull, inc1, (j - 33) & 31);
+                    const int first = j == 0 ? 0 : (j <= 32 ? e0 : e1);
                     const int lo = qlo[j];
-                    const int it = (tau - qtoff[j]) * 32 + lane, wi = (lo >> 6) + it;
+                    const int it = (tau - first) * 32 + lane, wi = (lo >> 6) + it;
                     u64 pk = 0, corr = 0;
                     if (wi < nwg) leaf_item_eval(c, s, qrec[j], wi, range_word(wi, lo, c.G - 1), corr, pk);
                     pk = warp_max_u64(pk);
-                    corr = warp_sum_u64(corr);
+                    const u32 cs = __reduce_add_sync(kFull, (u32)corr);
                     if (lane == 0) {
                         if (pk) atomicMax(&qbest[j], pk);
-                        if (corr) atomicAdd(&qcorr[j], corr);
+                        if (cs) atomicAdd(&qcorr[j], cs);
                     }
                 }
                 __syncthreads();
