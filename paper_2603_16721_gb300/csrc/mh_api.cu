@@ -1355,6 +1355,63 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
     return MH_OK;
 }
 
+// The cohorts one after another, each solved by the single-cohort persistent kernel
+// over the whole grid: every cohort's round-state initialisation and launch are
+// queued back to back on the stream and the host synchronises once for the batch.
+// A cohort whose frontier overflowed is grown and solved again on its own.
+// *ms receives the batch's time (CUDA events).
+constexpr double kInTurn = 1000.0;  // the autotuner's code for this schedule
+int run_in_turn(mh_handle *const *hs, const mh_solve_opts *opts, int n, double *ms)
+{
+    cudaStream_t st = hs[0]->stream;
+    std::vector<Solve> ss(n);
+    std::vector<int> maxr(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = prepare_solve(hs[i], &opts[i], &ss[i], &maxr[i]);
+        if (rc) return rc;
+    }
+    cudaEvent_t a, b;
+    MH_CUDA(cudaEventCreate(&a));
+    MH_CUDA(cudaEventCreate(&b));
+    MH_CUDA(cudaEventRecord(a, st));
+    for (int i = 0; i < n; ++i) {
+        mh_handle *H = hs[i];
+        launch_solve_init(H->c, ss[i], H->ws_rounds, maxr[i], H->dCounts, kCountSets, st);
+        if (H->Nt == 0) continue;
+        MH_CUDA(cudaMemsetAsync(H->dSync, 0, sizeof(GridSync), st));
+        const bool large = use_large_build(H, opts[i].h);
+        MH_CUDA(launch_solve_persistent(H->c, ss[i], frontiers_of(H), H->dSync, H->dCounts,
+                                        persistent_grid(H->num_sms, large), large, st));
+    }
+    MH_CUDA(cudaEventRecord(b, st));
+    MH_CUDA(cudaEventSynchronize(b));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    double total = t;
+    for (int i = 0; i < n; ++i) {
+        mh_handle *H = hs[i];
+        MH_CUDA(cudaMemcpy(H->hState, H->dState, sizeof(int) * kStateWords, cudaMemcpyDeviceToHost));
+        if (H->hState[2]) return fail(MH_ETIMEOUT, "a grid barrier of the batched solve timed out");
+        if (H->hState[3]) {  // overflowed: grown and solved again from the start
+            const int r = H->hState[4];
+            MH_CUDA(cudaMemcpy(H->hState + kStateWords, H->dCounts + (size_t)(r & 1) * kCountWords,
+                               sizeof(u32) * kCountWords, cudaMemcpyDeviceToHost));
+            int rc = grow_overflowed(H, opts[i].h, (const u32 *)(H->hState + kStateWords));
+            if (rc) return rc;
+            MH_CUDA(cudaMemsetAsync(H->dCounts, 0, sizeof(u32) * kCountSets * kCountWords, st));
+            std::vector<double> w(1, 1.0);
+            double t1 = 0.0;
+            rc = run_batch(&hs[i], &opts[i], 1, w, 1.0, kBatchBuilds[0], nullptr, &t1);
+            if (rc) return rc;
+            total += t1;
+        }
+    }
+    *ms = total;
+    return MH_OK;
+}
+
 }  // namespace
 
 extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n,
@@ -1397,6 +1454,10 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     int rc = MH_OK, smm = 0, graphed = 0;
     // a choice of the autotuner, encoded as 100 * (build == 4) + 10 * model + gamma
     auto run_choice = [&](double choice, double *t, int *smm_out) {
+        if (choice >= kInTurn) {  // one cohort after another over the whole grid
+            if (smm_out) *smm_out = 1;
+            return run_in_turn(handles, opts, n, t);
+        }
         // choice = 100 * (index of the build in kBatchBuilds) + 10 * model + gamma
         const int bi = std::min(2, std::max(0, (int)(choice / 100.0)));
         const int build = kBatchBuilds[bi];
@@ -1408,9 +1469,10 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     if (blocks) {
         rc = run_batch(handles, opts, n, work_p, 1.0, 3, &b, &ms, &smm, &graphed);
     } else {
-        // autotuner: the kernel build (1, 3 or 4 blocks per SM), the work model and the
-        // split exponent gamma (blocks ~ work^gamma) are chosen by timing each
-        // candidate once per batch shape; the choice is cached on disk
+        // autotuner: the cohorts in turn over the whole grid, or concurrently on a split
+        // of it -- the kernel build (1, 3 or 4 blocks per SM), the work model and the
+        // split exponent gamma (blocks ~ work^gamma) -- chosen by timing each candidate
+        // once per batch shape; the choice is cached on disk
         const std::string sig = batch_signature(handles, opts, n, grid);
         double choice = 1.0;
         const char *off = getenv("MH_AUTOTUNE");
@@ -1419,6 +1481,13 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         } else {
             const double gammas[] = {0.5, 0.75, 1.0, 1.5, 2.0};
             double best_ms = 1e300, best = 1.0;
+            {  // the cohorts in turn, each over the whole grid
+                double t = 0.0;
+                rc = run_choice(kInTurn, &t, nullptr);
+                if (rc) return rc;
+                best_ms = t;
+                best = kInTurn;
+            }
             for (int bi = 0; bi < 3; ++bi) {
                 if (batch_grid(H0->num_sms, kBatchBuilds[bi]) < n) continue;  // a block per cohort at least
                 for (int model = 0; model < 2; ++model) {
