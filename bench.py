@@ -344,6 +344,7 @@ def run_ours(args):
         vis_leaves = int(r0.visited[:, -1].sum())
         pruned_prefixes = int(r0.pruned[:, :-1].sum())
         cb = cpu_baseline_measure(c) if world == 1 else None
+        peaks = int_peaks()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
@@ -361,7 +362,7 @@ def run_ours(args):
                       "combos_scored_per_s": scored * value / world, "leaves_tested_per_s": vis_leaves * value / world,
                       "prefixes_pruned_per_s": pruned_prefixes * value / world,
                       "visited_fraction": vis_leaves / (r0.rounds * _comb(c.G, H_HITS))},
-            "roofline": solve_roofline(results, c.Nt, c.Nn, int_peaks()),
+            "roofline": solve_roofline(results, c.Nt, c.Nn, peaks),
             "cpu_baseline": cb,
             "e2e": {"value": world / (e2e_max / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(c.bitmaps.nbytes), "d2h_bytes_per_step": int(d2h)},
@@ -371,7 +372,7 @@ def run_ours(args):
         if world == 1 and not args.no_extras:
             # the other plain single-cohort configurations (c1: h=2, G=1,000; c3: h=4,
             # G=19,000, 128-bit rows): CUDA events on the solving stream, L2 flushed
-            line["plain_configs"] = {"c1": plain_config("c1", 5), "c3": plain_config("c3", 3)}
+            line["plain_configs"] = {"c1": plain_config("c1", 5, peaks), "c3": plain_config("c3", 3, peaks)}
             line["bound_mode"] = bound_comparison(c)
             line["train_test"] = train_test_coverage()
             # the other two parts of the metric, after the timed c2 steps: batched
@@ -388,9 +389,11 @@ def run_ours(args):
     return 0
 
 
-def plain_config(name, runs):
+def plain_config(name, runs, peaks_int=None):
     """One plain single-cohort configuration: the median of `runs` solves (after one
-    warm-up) of its synthetic cohort, timed with CUDA events, L2 flushed between."""
+    warm-up) of its synthetic cohort, timed with CUDA events, L2 flushed between;
+    with the measured integer peaks, the solve kernel's roofline when a committed ncu
+    summary of the current kernel source on this configuration exists."""
     import torch
     import synth
     from paper_2603_16721_gb300 import mh
@@ -398,7 +401,7 @@ def plain_config(name, runs):
     c = synth.generate(spec)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ms, kms = [], []
+    ms, kms, rs = [], [], []
     with mh.mh_create(c.bitmaps, c.G, c.Nt, c.Nn) as Hc:
         mh.mh_set_stream(Hc, stream.cuda_stream)
         r = mh.mh_solve(Hc, spec.h, ALPHA)
@@ -413,6 +416,7 @@ def plain_config(name, runs):
             ev1.synchronize()
             ms.append(ev0.elapsed_time(ev1))
             kms.append(r.kernel_ms)
+            rs.append(r)
     t = statistics.median(ms) / 1e3
     scored = int((r.visited[:, -1] - r.pruned[:, -1]).sum())
     return {"workload": f"{name}: h={spec.h}, G={c.G}, Nt={c.Nt}, Nn={c.Nn}, seed {spec.seed}, alpha=1/10",
@@ -420,7 +424,9 @@ def plain_config(name, runs):
             "solves_per_s": round(1.0 / t, 3), "rounds": r.rounds, "selected": r.k,
             "combos_scored_per_s": scored / t, "leaves_tested_per_s": int(r.visited[:, -1].sum()) / t,
             "prefixes_pruned_per_s": int(r.pruned[:, :-1].sum()) / t,
-            "visited_fraction": int(r.visited[:, -1].sum()) / (r.rounds * _comb(c.G, spec.h)), "runs": runs}
+            "visited_fraction": int(r.visited[:, -1].sum()) / (r.rounds * _comb(c.G, spec.h)), "runs": runs,
+            "roofline": (solve_roofline(rs, c.Nt, c.Nn, peaks_int, f"k_solve_{name}.md")
+                         if peaks_int and _profiled_fields(f"k_solve_{name}.md") else None)}
 
 
 def bound_comparison(c):
