@@ -2276,6 +2276,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
     const int h = s.h;
     const u64 *Ush = io.Ush;
     const int qcap = kQueue < 32 * nwarps ? kQueue : 32 * nwarps;
+    // each tumor's offset into the per-sample gene lists, on chip (one-block-per-SM builds)
+    __shared__ u32 so_sh[kLWarps > 0 ? kMaxWords * 64 + 1 : 1];
     // the changes of the depths' corrections: per warp, summed over the warps at the
     // end (one-block-per-SM builds), else block-wide in acc
     __shared__ u64 wdeep[kLWarps > 0 ? kLWarps : 1][2 * kMaxH + 2];
@@ -2290,6 +2292,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
         overflow = 0;
         qn = 0;
     }
+    if (kLWarps > 0 && (force || !ft.ok))  // once per launch, published by acc_begin's barrier
+        for (int i = (int)threadIdx.x; i <= c.Nt; i += (int)blockDim.x) so_sh[i] = __ldg(c.SO + i);
     acc_begin(acc);
     u64 csig = 0;
     for (int w = 0; w < c.Wt; ++w) csig |= Csh[w];
@@ -2344,8 +2348,8 @@ __device__ bool phase_update(const Cohort &c, const Solve &s, int round, const F
             for (int smp = t.rank; smp < c.Nt; smp += t.size) {
                 if (!in_mask(Csh, smp)) continue;
                 if (sl) sv += __ldcg(s.ssum + (size_t)smp * h2 + sidx);
-                const u32 off = __ldg(c.SO + smp);
-                const int m = (int)(__ldg(c.SO + smp + 1) - off);
+                const u32 off = kLWarps > 0 ? so_sh[smp] : __ldg(c.SO + smp);
+                const int m = (int)((kLWarps > 0 ? so_sh[smp + 1] : __ldg(c.SO + smp + 1)) - off);
                 for (int q = lane; q < m; q += 32) {
                     const int g = (int)__ldg(c.SL + off + q);
                     const u32 old = atomicSub(s.gk + g, 1u);
