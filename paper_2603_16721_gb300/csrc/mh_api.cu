@@ -1187,7 +1187,8 @@ bool capturable(cudaStream_t st)
 }
 
 int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, double gamma,
-              int build, const std::vector<int> *fixed, double *ms, int *sm_major = nullptr, int *graphed = nullptr)
+              int build, const std::vector<int> *fixed, double *ms, int *sm_major = nullptr, int *graphed = nullptr,
+              bool graph_ok = true)
 {
     if (sm_major) *sm_major = 1;
     if (graphed) *graphed = 0;
@@ -1256,7 +1257,7 @@ int run_batch(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std:
         };
         // the start of the solve from a captured graph (see StartGraph)
         bool started = false;
-        if (init_pending && act.size() > 1 && capturable(st)) {
+        if (graph_ok && init_pending && act.size() > 1 && capturable(st)) {
             std::vector<char> key(sizeof(BatchItem) * items.size());
             memcpy(key.data(), items.data(), key.size());
             auto put = [&](const void *p, size_t bytes) {
@@ -1412,6 +1413,39 @@ int run_in_turn(mh_handle *const *hs, const mh_solve_opts *opts, int n, double *
     return MH_OK;
 }
 
+// Groups of k cohorts of similar work (largest first), one group after another; the
+// cohorts of a group run concurrently on a split of the grid (blocks ~ work, whole
+// SMs, the one-block-per-SM build).  Between the in-turn schedule (k = 1) and the
+// whole batch at once.  *ms receives the sum of the groups' times.
+constexpr double kGroups = 2000.0;  // the autotuner's code for this schedule is kGroups + k
+int run_groups(mh_handle *const *hs, const mh_solve_opts *opts, int n, const std::vector<double> &work, int k,
+               double *ms)
+{
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
+    double total = 0.0;
+    for (int g0 = 0; g0 < n; g0 += k) {
+        const int m = std::min(k, n - g0);
+        std::vector<mh_handle *> gh(m);
+        std::vector<mh_solve_opts> go(m);
+        std::vector<double> gw(m);
+        for (int i = 0; i < m; ++i) {
+            gh[i] = hs[idx[g0 + i]];
+            go[i] = opts[idx[g0 + i]];
+            gw[i] = work[idx[g0 + i]];
+        }
+        double t = 0.0;
+        const int rc = m == 1 ? run_in_turn(gh.data(), go.data(), 1, &t)
+                              : run_batch(gh.data(), go.data(), m, gw, 1.0, kBatchBuilds[0], nullptr, &t, nullptr,
+                                          nullptr, false);
+        if (rc) return rc;
+        total += t;
+    }
+    *ms = total;
+    return MH_OK;
+}
+
 }  // namespace
 
 extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_opts *opts, int32_t n,
@@ -1454,6 +1488,10 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
     int rc = MH_OK, smm = 0, graphed = 0;
     // a choice of the autotuner, encoded as 100 * (build == 4) + 10 * model + gamma
     auto run_choice = [&](double choice, double *t, int *smm_out) {
+        if (choice >= kGroups) {  // groups of k cohorts, one group after another
+            if (smm_out) *smm_out = 1;
+            return run_groups(handles, opts, n, work_p, (int)(choice - kGroups), t);
+        }
         if (choice >= kInTurn) {  // one cohort after another over the whole grid
             if (smm_out) *smm_out = 1;
             return run_in_turn(handles, opts, n, t);
@@ -1487,6 +1525,16 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
                 if (rc) return rc;
                 best_ms = t;
                 best = kInTurn;
+            }
+            for (int k : {2, 4}) {  // groups of k cohorts, one group after another
+                if (k >= n) break;
+                double t = 0.0;
+                rc = run_choice(kGroups + k, &t, nullptr);
+                if (rc) return rc;
+                if (t < best_ms) {
+                    best_ms = t;
+                    best = kGroups + k;
+                }
             }
             for (int bi = 0; bi < 3; ++bi) {
                 if (batch_grid(H0->num_sms, kBatchBuilds[bi]) < n) continue;  // a block per cohort at least
