@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmh.so")
 
-SOURCES = ["mh_kernels.cu", "mh_api.cu", "mh_noalloc.cu", "mh_diag.cu"]
+SOURCES = ["mh_kernels.cu", "mh_api.cu", "mh_noalloc.cu", "mh_diag.cu", "mh_store.cu"]
 HEADERS = ["mh_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -266,144 +266,81 @@ int build_store(mh_handle *H, const uint64_t *bm)
 {
     const int G = H->G, Nt = H->Nt, Nn = H->Nn;
     const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64, W = Wt + Wn;
+    // one pass over the rows: padding bits, each gene's tumor mutations, each
+    // tumor's mutated genes
+    std::vector<int> pc(G);
+    H->m_s.assign(Nt, 0);
     for (int g = 0; g < G; ++g) {
         const uint64_t *row = bm + (size_t)g * W;
         if (Nt % 64 && Wt && (row[Wt - 1] >> (Nt % 64)))
             return fail(MH_EINVAL, "gene %d: tumor padding bits past Nt=%d are set", g, Nt);
         if (Nn % 64 && Wn && (row[Wt + Wn - 1] >> (Nn % 64)))
             return fail(MH_EINVAL, "gene %d: normal padding bits past Nn=%d are set", g, Nn);
+        int k = 0;
+        for (int w = 0; w < Wt; ++w) {
+            k += __builtin_popcountll(row[w]);
+            for (uint64_t x = row[w]; x; x &= x - 1) ++H->m_s[w * 64 + __builtin_ctzll(x)];
+        }
+        pc[g] = k;
     }
-    // search order: ascending tumor mutation count, ties by original index (§III-C)
-    std::vector<int> order(G);
-    std::vector<int> pc(G);
-    for (int g = 0; g < G; ++g) {
-        order[g] = g;
-        pc[g] = popcount_words(bm + (size_t)g * W, Wt);
+    // search order: ascending tumor mutation count, ties by original index (§III-C),
+    // by a counting sort (stable)
+    std::vector<u32> order(G);
+    {
+        std::vector<int> start((size_t)Nt + 2, 0);
+        for (int g = 0; g < G; ++g) ++start[pc[g] + 1];
+        for (int k = 0; k <= Nt; ++k) start[k + 1] += start[k];
+        for (int g = 0; g < G; ++g) order[start[pc[g]]++] = (u32)g;
     }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pc[a] < pc[b]; });
-    H->m_s.assign(Nt, 0);
-    for (int g = 0; g < G; ++g)
-        for (int w = 0; w < Wt; ++w)
-            for (uint64_t x = bm[(size_t)g * W + w]; x; x &= x - 1) ++H->m_s[w * 64 + __builtin_ctzll(x)];
-
     Cohort &c = H->c;
     c.G = G; c.Nt = Nt; c.Nn = Nn; c.Wt = Wt; c.Wn = Wn;
     c.WTp = std::max(2, (Wt + 1) & ~1);
     c.WNp = std::max(2, (Wn + 1) & ~1);
     c.GW = std::max(2, (((G + 63) / 64) + 1) & ~1);
-
-    std::vector<u64> T((size_t)G * c.WTp, 0), N((size_t)G * c.WNp, 0);
-    std::vector<u16> orig(G);
-    std::vector<u32> inv(G);
-    for (int i = 0; i < G; ++i) {
-        const int g = order[i];
-        const uint64_t *row = bm + (size_t)g * W;
-        for (int w = 0; w < Wt; ++w) T[(size_t)i * c.WTp + w] = row[w];
-        for (int w = 0; w < Wn; ++w) N[(size_t)i * c.WNp + w] = row[Wt + w];
-        orig[i] = (u16)g;
-        inv[g] = (u32)i;
-    }
-    // sample-major copies: bit i of column s is set iff sorted gene i has sample s
-    // (a scatter of the set bits: the rows are sparse)
-    std::vector<u64> CT((size_t)Nt * c.GW, 0), CN((size_t)Nn * c.GW, 0);
-    for (int i = 0; i < G; ++i) {
-        const u64 bit = 1ull << (i & 63);
-        for (int w = 0; w < Wt; ++w)
-            for (u64 x = T[(size_t)i * c.WTp + w]; x; x &= x - 1)
-                CT[(size_t)(w * 64 + __builtin_ctzll(x)) * c.GW + (i >> 6)] |= bit;
-        for (int w = 0; w < Wn; ++w)
-            for (u64 x = N[(size_t)i * c.WNp + w]; x; x &= x - 1)
-                CN[(size_t)(w * 64 + __builtin_ctzll(x)) * c.GW + (i >> 6)] |= bit;
-    }
-    // running counts of each column's set bits, word by word (closed-form counts of
-    // the subtrees whose tumor intersection is one sample)
-    std::vector<u16> CC((size_t)Nt * (c.GW + 1), 0);
+    // each tumor's genes start at SO[s] in the per-sample lists (its column's popcount
+    // is its number of mutated genes)
     std::vector<u32> SO((size_t)Nt + 1, 0);
-    for (int sm = 0; sm < Nt; ++sm) {
-        int run = 0;
-        for (int w = 0; w <= c.GW; ++w) {
-            CC[(size_t)sm * (c.GW + 1) + w] = (u16)run;
-            if (w < c.GW) run += __builtin_popcountll(CT[(size_t)sm * c.GW + w]);
-        }
-        SO[sm + 1] = SO[sm] + (u32)run;
-    }
-    // each sample's genes in ascending search order
-    std::vector<u16> SL(std::max<size_t>(SO[Nt], 1));
-    for (int sm = 0; sm < Nt; ++sm) {
-        u32 k = SO[sm];
-        for (int w = 0; w < c.GW; ++w)
-            for (u64 x = CT[(size_t)sm * c.GW + w]; x; x &= x - 1) SL[k++] = (u16)(w * 64 + __builtin_ctzll(x));
-    }
-    // and as original row indices, ascending (the order of the leaf keys' tuples)
-    std::vector<u16> SLo(SL.size());
-    for (int sm = 0; sm < Nt; ++sm) {
-        for (u32 k = SO[sm]; k < SO[sm + 1]; ++k) SLo[k] = orig[SL[k]];
-        std::sort(SLo.begin() + SO[sm], SLo.begin() + SO[sm + 1]);
-    }
-    // static depth-1 record of every gene (search order): all its tumors and
-    // normals, listed when few; a round filters the listed tumors by U
-    std::vector<Rec> GR((size_t)G);
-    std::vector<u64> GS((size_t)G, 0);
-    for (int i = 0; i < G; ++i) {
-        Rec &r = GR[i];
-        memset(&r, 0, sizeof r);
-        r.p.w0 = (u64)i;
-        int ky = 0, kn = 0;
-        for (int w = 0; w < Wt; ++w) ky += __builtin_popcountll(T[(size_t)i * c.WTp + w]);
-        for (int w = 0; w < Wn; ++w) kn += __builtin_popcountll(N[(size_t)i * c.WNp + w]);
-        r.ky = (u16)std::min(ky, 0xffff);
-        r.kn = (u16)std::min(kn, 0xffff);
-        if (ky <= kListT) {
-            int k = 0;
-            for (int w = 0; w < Wt; ++w)
-                for (u64 x = T[(size_t)i * c.WTp + w]; x; x &= x - 1) r.ids[k++] = (u16)(w * 64 + __builtin_ctzll(x));
-        }
-        if (kn <= kListN) {
-            int k = kListT;
-            for (int w = 0; w < Wn; ++w)
-                for (u64 x = N[(size_t)i * c.WNp + w]; x; x &= x - 1) r.ids[k++] = (u16)(w * 64 + __builtin_ctzll(x));
-        }
-        for (int w = 0; w < Wt; ++w) GS[i] |= T[(size_t)i * c.WTp + w];  // bit s & 63 of every tumor s
-    }
+    for (int s = 0; s < Nt; ++s) SO[s + 1] = SO[s] + (u32)H->m_s[s];
+    const size_t nSL = std::max<size_t>(SO[Nt], 1);
+
     int rc;
     cudaStream_t st = H->stream;
-    // the whole store in one device block, filled by one copy (256-byte aligned pieces)
+    // the whole store in one device block (256-byte aligned pieces), written by the
+    // store kernels from the uploaded rows and permutation
     size_t off = 0;
     auto piece = [&](size_t bytes) {
         const size_t o = off;
         off += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
         return o;
     };
-    const size_t oT = piece(T.size() * sizeof(u64)), oN = piece(N.size() * sizeof(u64));
-    const size_t oCT = piece(CT.size() * sizeof(u64)), oCN = piece(CN.size() * sizeof(u64));
-    const size_t oCC = piece(CC.size() * sizeof(u16)), oSL = piece(SL.size() * sizeof(u16));
-    const size_t oSLo = piece(SLo.size() * sizeof(u16)), oSO = piece(SO.size() * sizeof(u32));
+    const size_t rowsT = (size_t)G * c.WTp, rowsN = (size_t)G * c.WNp;
+    const size_t oT = piece(rowsT * sizeof(u64)), oN = piece(rowsN * sizeof(u64));
+    const size_t oCT = piece((size_t)Nt * c.GW * sizeof(u64)), oCN = piece((size_t)Nn * c.GW * sizeof(u64));
+    const size_t oCC = piece((size_t)Nt * (c.GW + 1) * sizeof(u16)), oSL = piece(nSL * sizeof(u16));
+    const size_t oSLo = piece(nSL * sizeof(u16)), oSO = piece(SO.size() * sizeof(u32));
     const size_t oOrig = piece((size_t)G * sizeof(u16)), oInv = piece((size_t)G * sizeof(u32));
     const size_t oGR = piece((size_t)G * sizeof(Rec)), oGS = piece((size_t)G * sizeof(u64));
-    const size_t oTO = piece(T.size() * sizeof(u64)), oNO = piece(N.size() * sizeof(u64));
-    std::vector<unsigned char> host(off, 0);
-    auto put = [&](size_t o, const void *src, size_t bytes) {
-        if (bytes) memcpy(host.data() + o, src, bytes);
+    const size_t oTO = piece(rowsT * sizeof(u64)), oNO = piece(rowsN * sizeof(u64));
+    // scratch for the build: the rows as given, the permutation, the original-order
+    // sample-major copy (freed in stream order after the build)
+    size_t toff = 0;
+    auto tpiece = [&](size_t bytes) {
+        const size_t o = toff;
+        toff += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+        return o;
     };
-    put(oT, T.data(), T.size() * sizeof(u64));
-    put(oN, N.data(), N.size() * sizeof(u64));
-    put(oCT, CT.data(), CT.size() * sizeof(u64));
-    put(oCN, CN.data(), CN.size() * sizeof(u64));
-    put(oCC, CC.data(), CC.size() * sizeof(u16));
-    put(oSL, SL.data(), SL.size() * sizeof(u16));
-    put(oSLo, SLo.data(), SLo.size() * sizeof(u16));
-    put(oSO, SO.data(), SO.size() * sizeof(u32));
-    put(oOrig, orig.data(), (size_t)G * sizeof(u16));
-    put(oInv, inv.data(), (size_t)G * sizeof(u32));
-    put(oGR, GR.data(), (size_t)G * sizeof(Rec));
-    put(oGS, GS.data(), (size_t)G * sizeof(u64));
-    for (int g = 0; g < G; ++g) {  // original order: row g of the caller's input
-        const int i = (int)inv[g];
-        memcpy(host.data() + oTO + (size_t)g * c.WTp * sizeof(u64), &T[(size_t)i * c.WTp], c.WTp * sizeof(u64));
-        memcpy(host.data() + oNO + (size_t)g * c.WNp * sizeof(u64), &N[(size_t)i * c.WNp], c.WNp * sizeof(u64));
-    }
+    const size_t tBm = tpiece((size_t)G * W * sizeof(u64)), tOrder = tpiece((size_t)G * sizeof(u32));
+    const size_t tCTo = tpiece((size_t)Nt * c.GW * sizeof(u64));
     if ((rc = dalloc(&H->dStore, off, &H->device_bytes, H->dev, st))) return rc;
-    MH_CUDA(cudaMemcpyAsync(H->dStore, host.data(), off, cudaMemcpyHostToDevice, st));
+    unsigned char *scratch = nullptr;
+    if ((rc = dalloc(&scratch, toff, nullptr, H->dev, st))) {
+        dfree(H->dStore, st);
+        H->dStore = nullptr;
+        return rc;
+    }
+    if ((size_t)G * W) MH_CUDA(cudaMemcpyAsync(scratch + tBm, bm, (size_t)G * W * sizeof(u64), cudaMemcpyHostToDevice, st));
+    if (G) MH_CUDA(cudaMemcpyAsync(scratch + tOrder, order.data(), (size_t)G * sizeof(u32), cudaMemcpyHostToDevice, st));
+    MH_CUDA(cudaMemcpyAsync(H->dStore + oSO, SO.data(), SO.size() * sizeof(u32), cudaMemcpyHostToDevice, st));
     H->dT = (u64 *)(H->dStore + oT);
     H->dN = (u64 *)(H->dStore + oN);
     H->dCT = (u64 *)(H->dStore + oCT);
@@ -423,7 +360,22 @@ int build_store(mh_handle *H, const uint64_t *bm)
     c.GS = (const u64 *)(H->dStore + oGS);
     c.TO = (const u64 *)(H->dStore + oTO);
     c.NO = (const u64 *)(H->dStore + oNO);
-    MH_CUDA(cudaStreamSynchronize(st));  // host vectors go out of scope
+    StoreBuild b;
+    b.c = c;
+    b.bm = (const u64 *)(scratch + tBm);
+    b.order = (const u32 *)(scratch + tOrder);
+    b.SO = H->dSO;
+    b.T = H->dT; b.N = H->dN;
+    b.TO = (u64 *)(H->dStore + oTO);
+    b.NO = (u64 *)(H->dStore + oNO);
+    b.CT = H->dCT; b.CN = H->dCN;
+    b.CTo = (u64 *)(scratch + tCTo);
+    b.CC = H->dCC; b.SL = H->dSL; b.SLo = H->dSLo; b.orig = H->dOrig; b.inv = H->dInv;
+    b.GR = (Rec *)(H->dStore + oGR);
+    b.GS = (u64 *)(H->dStore + oGS);
+    MH_CUDA(launch_store_build(b, st));
+    dfree(scratch, st);
+    MH_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope; build errors surface here
     return MH_OK;
 }
 

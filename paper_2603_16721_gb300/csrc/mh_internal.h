@@ -93,6 +93,20 @@ struct __align__(16) Rec {
 };
 static_assert(sizeof(Rec) == 96, "frontier records are 96 bytes");
 
+// Device build of a cohort's store (mh_store.cu): the uploaded rows and the
+// sparsity permutation in, every piece of the store out.
+struct StoreBuild {
+    Cohort c;          // sizes: G, Nt, Nn, Wt, Wn, WTp, WNp, GW
+    const u64 *bm;     // the packed rows as given, G x (Wt + Wn)
+    const u32 *order;  // search position -> original row index
+    const u32 *SO;     // each tumor's offset into SL / SLo (Nt + 1)
+    u64 *T, *N, *TO, *NO, *CT, *CN, *CTo;  // CTo: sample-major copy of TO (scratch)
+    u16 *CC, *SL, *SLo, *orig;
+    u32 *inv;
+    Rec *GR;
+    u64 *GS;
+};
+
 // Per-solve device state.
 struct Solve {
     int h;
@@ -186,6 +200,7 @@ constexpr int kCountSets = 2;
 
 // Launchers (mh_kernels.cu).
 void launch_transpose(const Cohort &c, const u64 *rows, int row_stride, int samples, u64 *cols, cudaStream_t st);
+cudaError_t launch_store_build(const StoreBuild &b, cudaStream_t st);
 // Rounds run on the device: every kernel reads the round index and the done /
 // overflow flags from Solve::state, so the host can enqueue many rounds ahead.
 // counts: kCountWords u32 (see shard_slot); cap values are per shard.
