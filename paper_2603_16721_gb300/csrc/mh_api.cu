@@ -261,8 +261,9 @@ int validate_dims(int32_t G, int32_t Nt, int32_t Nn)
     return MH_OK;
 }
 
-// Builds the device store from host rows (already validated).
-int build_store(mh_handle *H, const uint64_t *bm)
+// Builds the device store from host rows (validated here) on the handle's stream;
+// with sync, waits for the build to finish.
+int build_store(mh_handle *H, const uint64_t *bm, bool sync = true)
 {
     const int G = H->G, Nt = H->Nt, Nn = H->Nn;
     const int Wt = (Nt + 63) / 64, Wn = (Nn + 63) / 64, W = Wt + Wn;
@@ -375,11 +376,12 @@ int build_store(mh_handle *H, const uint64_t *bm)
     b.GS = (u64 *)(H->dStore + oGS);
     MH_CUDA(launch_store_build(b, st));
     dfree(scratch, st);
-    MH_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope; build errors surface here
+    if (sync) MH_CUDA(cudaStreamSynchronize(st));  // build errors surface here
     return MH_OK;
 }
 
-int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStream_t stream, mh_handle **out)
+int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStream_t stream, mh_handle **out,
+                  bool sync = true)
 {
     mh_handle *H = new (std::nothrow) mh_handle();
     if (!H) return fail(MH_ENOMEM, "host allocation of the handle failed");
@@ -394,7 +396,7 @@ int create_common(const uint64_t *bm, int32_t G, int32_t Nt, int32_t Nn, cudaStr
         delete H;
         return fail(MH_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
     }
-    int rc = build_store(H, bm);
+    int rc = build_store(H, bm, sync);
     if (rc) {
         delete H;
         return rc;
@@ -1560,6 +1562,7 @@ struct ServerReq {
     bool large = false;  // work above kLargeWork
     bool cancel = false; // mh_cancel on an admitted request: retired at the next round boundary
     double t_ran = 0.0;  // last launch that included it (its admission before the first)
+    cudaEvent_t built = nullptr;  // end of its store build on the upload stream
 };
 
 // Device memory a request needs: its store, workspace and (for h >= 3) the
@@ -1624,11 +1627,12 @@ struct mh_server {
         if (r->res) r->res->solve_ms = (r->t_done - r->t_submit) * 1e3;
     }
 
-    // Admission of the queue head when a slot and memory are free: the cohort is
-    // packed on the host and uploaded on the upload stream (copies and pool
-    // allocations only, no kernel), so it can run while a launch is on the GPU.
-    // The admitted request waits in `ready` for the next launch.  Returns true
-    // if the head was taken (admitted, or finished with an error).
+    // Admission of the queue head when a slot and memory are free: the cohort's
+    // rows are uploaded and its store is built on the upload stream without the
+    // host waiting (the build's kernels find SMs when the running launch ends at its
+    // next round boundary, which the admission asks for); the next launch waits for
+    // the build on the device.  The admitted request waits in `ready` for that
+    // launch.  Returns true if the head was taken (admitted, or finished with an error).
     bool admit_one()
     {
         ServerReq *r = nullptr;
@@ -1654,12 +1658,17 @@ struct mh_server {
             queue.erase(it);
             in_use += r->footprint;
         }
-        int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st_up, &r->H);
+        int rc = create_common(r->bm.data(), r->G, r->Nt, r->Nn, st_up, &r->H, false);
         int maxr = 0;
         if (rc == MH_OK) rc = prepare_solve(r->H, &r->opts, &r->s, &maxr);
-        if (rc == MH_OK && cudaStreamSynchronize(st_up) != cudaSuccess) rc = fail(MH_ECUDA, "upload failed");
+        if (rc == MH_OK && (cudaEventCreateWithFlags(&r->built, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventRecord(r->built, st_up) != cudaSuccess))
+            rc = fail(MH_ECUDA, "upload failed");
         std::lock_guard<std::mutex> lock(mu);
         if (rc != MH_OK) {
+            if (r->built) cudaStreamSynchronize(st_up);  // nothing of it left in flight
+            if (r->built) cudaEventDestroy(r->built);
+            r->built = nullptr;
             if (r->H) mh_destroy(r->H);
             r->H = nullptr;
             in_use -= r->footprint;
@@ -1687,6 +1696,11 @@ struct mh_server {
                     keep.push_back(r);
                     continue;
                 }
+                if (r->built) {
+                    cudaEventSynchronize(r->built);
+                    cudaEventDestroy(r->built);
+                    r->built = nullptr;
+                }
                 mh_destroy(r->H);
                 r->H = nullptr;
                 in_use -= r->footprint;
@@ -1698,6 +1712,11 @@ struct mh_server {
         const double t0 = now_s();
         for (ServerReq *r : ready) {
             r->t_ran = t0;
+            if (r->built) {  // its store, built on the upload stream
+                cudaStreamWaitEvent(st, r->built, 0);
+                cudaEventDestroy(r->built);
+                r->built = nullptr;
+            }
             launch_solve_init(r->H->c, r->s, r->H->ws_rounds, r->maxr, r->H->dCounts, kCountSets, st);
             if (r->Nt == 0) {
                 const int one = 1;
