@@ -1468,7 +1468,11 @@ extern "C" MH_API int mh_solve_batch(mh_handle *const *handles, const mh_solve_o
         const std::string sig = batch_signature(handles, opts, n, grid);
         double choice = 1.0;
         const char *off = getenv("MH_AUTOTUNE");
-        if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
+        const char *forced = getenv("MH_BATCH_CHOICE");  // a schedule code, bypassing the tuner
+        if (forced && *forced) {
+            choice = atof(forced);
+            rc = run_choice(choice, &ms, &smm);
+        } else if ((off && off[0] == '0') || tune_lookup(sig, &choice)) {
             rc = run_choice(choice, &ms, &smm);
         } else {
             const double gammas[] = {0.5, 0.75, 1.0, 1.5, 2.0};

@@ -51,6 +51,24 @@ def test_batch_equals_alone_and_oracle(mh, tmp_path, monkeypatch):
         H.close()
 
 
+@pytest.mark.parametrize("choice", ["1000", "2002", "2004", "1", "12", "101.5", "210.75"])
+def test_every_batch_schedule_equals_alone(mh, monkeypatch, choice):
+    """Each schedule the autotuner can pick -- in turn (1000), groups of 2 and 4
+    (2002, 2004), and concurrent launches of each build, work model and split
+    exponent (100 * build + 10 * model + gamma) -- gives every cohort the result it
+    gets alone."""
+    monkeypatch.setenv("MH_BATCH_CHOICE", choice)
+    cohorts = _mixed_cohorts()
+    handles = [mh.mh_create(bm, G, Nt, Nn) for bm, G, Nt, Nn, h in cohorts]
+    hs = [c[4] for c in cohorts]
+    alone = [mh.mh_solve(H, h) for H, h in zip(handles, hs)]
+    got = mh.mh_solve_batch(handles, hs)
+    for g, a in zip(got, alone):
+        _same(g, a)
+    for H in handles:
+        H.close()
+
+
 def test_batch_of_c2_law_cohorts(mh, tmp_path, monkeypatch):
     """Sixteen cohorts drawn like the batched workload's members, at reduced sizes."""
     monkeypatch.setenv("MH_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
