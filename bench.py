@@ -204,7 +204,25 @@ def solve_roofline(res_list, Nt, Nn, peaks_int, kernel_file="k_solve_c2.md"):
             "int_peaks": {k: round(v, 3) for k, v in peaks_int.items()},
             "work_equiv": {"ops_per_launch": round(sum(o[0] for o in ops) / launches),
                            "achieved": round(wequiv, 4), "work_equiv_frac": round(wequiv / peak, 4)},
-            "ncu": ncu}
+            "ncu": ncu,
+            "latency": latency_chain(res_list, avg_s)}
+
+
+def latency_chain(res_list, avg_s):
+    """The solve's time in the unit that bounds it: a round is a chain of dependent
+    steps (block barriers, the grid barrier, L2 round trips), so the kernel's time
+    per round is given beside one dependent L2 load measured on this GPU
+    (mh_l2_latency), as the number of such loads it equals."""
+    from paper_2603_16721_gb300 import mh
+    try:
+        ns = mh.mh_l2_latency()
+    except Exception:  # a diagnostic: the line stands without it
+        return None
+    rounds = sum(r.rounds for r in res_list) / max(1, len(res_list))
+    us_round = avg_s * 1e6 / max(1.0, rounds)
+    return {"rounds_per_launch": rounds, "us_per_round": round(us_round, 3),
+            "l2_dependent_load_us": round(ns / 1e3, 4),
+            "l2_loads_per_round": round(us_round * 1e3 / ns, 1) if ns > 0 else None}
 
 
 def cpu_threads():

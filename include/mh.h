@@ -318,6 +318,14 @@ MH_API int mh_solve_noalloc(const uint64_t *d_bitmaps, int32_t G, int32_t Nt, in
  * Errors: MH_EINVAL (bad op or NULL ops_per_s), MH_ECUDA. */
 MH_API int mh_int_peak(int32_t op, double *ops_per_s, double *kernel_ms);
 
+/* Diagnostic (no counterpart in the paper): the time of one dependent load served
+ * by L2 on the current GPU, the unit of the persistent solve's per-round latency
+ * chain.  One thread follows a chain of loads (L1 bypassed) through a 4 MB buffer,
+ * one 128-byte line per load, twice; *ns_per_load receives the second pass's
+ * device-clock time per load.  Allocates 4 MB with cudaMalloc.  Errors: MH_EINVAL
+ * (NULL), MH_ECUDA. */
+MH_API int mh_l2_latency(double *ns_per_load);
+
 /* ---- Split search: one solve divided over processes --------------------------
  * The paper runs each greedy round's search over many workers by handing out the
  * lambda units of the search (§III-E) and reducing their best candidates; here a

@@ -45,11 +45,65 @@ __global__ void __launch_bounds__(kPeakThreads) k_int_peak(unsigned seed, int it
     if (x == seed) out[blockIdx.x * blockDim.x + threadIdx.x] = x;  // keeps the chains live
 }
 
+// One thread follows a chain of dependent loads through a buffer resident in L2
+// (ld.global.cg: L1 bypassed), each load on its own 128-byte line; the device
+// clock (globaltimer) around the second pass gives the round-trip time of one
+// dependent L2 load, the unit of the persistent solve's per-round latency chain.
+__global__ void k_l2_fill(u32 *next, u32 n, u32 stride)
+{
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) next[i] = (u32)(((unsigned long long)i + stride) % n);
+}
+__global__ void k_l2_chase(const u32 *next, int steps, unsigned long long *out)
+{
+    u32 idx = 0;
+    unsigned long long t[2] = {0, 0};
+    for (int pass = 0; pass < 2; ++pass) {
+        unsigned long long t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (int k = 0; k < steps; ++k) idx = __ldcg(next + idx);
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1) : "r"(idx));
+        t[pass] = t1 - t0;
+    }
+    out[0] = t[1];
+    out[1] = idx;  // keeps the chain live
+}
+
 }  // namespace
 
 }  // namespace mh
 
 using namespace mh;
+
+extern "C" MH_API int mh_l2_latency(double *ns_per_load)
+{
+    if (!ns_per_load) {
+        set_error_text("mh_l2_latency: ns_per_load is NULL");
+        return MH_EINVAL;
+    }
+    constexpr u32 kN = 1u << 20;             // 4 MB of u32: in L2, far beyond L1
+    constexpr u32 kStride = 32u * 4099u;      // 128-byte lines apart, visiting many lines
+    constexpr int kSteps = 4096;
+    u32 *next = nullptr;
+    unsigned long long *out = nullptr, h[2] = {0, 0};
+    cudaError_t e = cudaMalloc((void **)&next, sizeof(u32) * kN);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&out, sizeof(h));
+    if (e == cudaSuccess) {
+        k_l2_fill<<<(kN + 255) / 256, 256>>>(next, kN, kStride);
+        k_l2_chase<<<1, 1>>>(next, kSteps, out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(next);
+    cudaFree(out);
+    if (e != cudaSuccess) {
+        set_error_text(cudaGetErrorString(e));
+        return MH_ECUDA;
+    }
+    *ns_per_load = (double)h[0] / kSteps;
+    return MH_OK;
+}
 
 extern "C" MH_API int mh_int_peak(int32_t op, double *ops_per_s, double *kernel_ms)
 {

@@ -225,6 +225,16 @@ def mh_int_peak(op: int = 0):
     return float(v.value), float(ms.value)
 
 
+def mh_l2_latency() -> float:
+    """Time of one dependent L2 load on the current GPU, in ns."""
+    lib = load()
+    lib.mh_l2_latency.restype = ctypes.c_int
+    lib.mh_l2_latency.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    v = ctypes.c_double(0.0)
+    _check(lib.mh_l2_latency(ctypes.byref(v)))
+    return float(v.value)
+
+
 def mh_last_error() -> str:
     return load().mh_last_error().decode()
 
