@@ -2208,16 +2208,20 @@ __device__ void phase_build1(const Cohort &c, const Solve &s, const Frontiers &f
 // every depth (record i to block i mod B, then to warp (i / B) mod W, so that
 // records appended together spread out), brings up to date those holding a
 // covered tumor (their signature meets the covered tumors'), re-evaluates the leaf
-// parents among them, and takes the others' best keys from the caches.  What it
-// adds to the round's counter slots are CHANGES of the corrections (in round 0,
-// the corrections themselves), which the end of the round adds to running totals:
-// depth 1's surviving count; (k - 1)(hi(2) - g) over the genes shared by k >= 2
+// parents among them, and takes the others' best keys from the caches.  After
+// round 0 each warp keeps its live records in an on-chip list (built once they
+// fit) and reads from L2 only the records a covered tumor touches; changed leaf
+// parents are evaluated by the whole block through a queue of tasks.  What it
+// adds to the round's counter slots are CHANGES of the running totals (in round
+// 0, the corrections themselves), which the end of the round accumulates: depth
+// 1's surviving count; (k - 1)(hi(2) - g) over the genes shared by k >= 2
 // uncovered tumors; for a kept node of depth l >= 2 with k >= 2 tumors, k - 1 to
 // depth l and (k - 1)(hi(l+1) - last) to depth l + 1; the leaf parents' sums of
-// TP - 1 to depth h.  The block's best key (leaf caches, and the champions of its
-// uncovered tumors, which stand for the TP = 1 leaves) goes to its slot.  Every
-// thread of the block must call it; returns false (for every thread) if round 0
-// overflowed a frontier.
+// TP - 1 to depth h; and the per-sample sums of the tumors the last winner
+// covered.  The block's best key (leaf caches, and the champions of its uncovered
+// tumors, which stand for the TP = 1 leaves) goes to its slot.  Every thread of
+// the block must call it; returns false (for every thread) if round 0 overflowed
+// a frontier.
 constexpr int kScanIlp = 4;  // records whose signature and cached score a lane loads at once
 // changed leaf parents a block spreads over its warps per round (one-block-per-SM
 // builds; the smaller blocks keep their shared memory for occupancy)
