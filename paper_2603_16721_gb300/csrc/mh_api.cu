@@ -186,6 +186,41 @@ void pinned_state_put(int *p)
     g_pinned_free.push_back(p);
 }
 
+// Pinned host buffers for reading a solve's results back (selections, counters,
+// cuts, diagnostics in one asynchronous batch of copies), recycled the same way:
+// the smallest free one that is large enough, else a new one.
+std::vector<std::pair<void *, size_t>> g_pinned_res_free;
+
+void *pinned_res_get(size_t bytes, size_t *got)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_pinned_mutex);
+        int best = -1;
+        for (int i = 0; i < (int)g_pinned_res_free.size(); ++i)
+            if (g_pinned_res_free[i].second >= bytes &&
+                (best < 0 || g_pinned_res_free[i].second < g_pinned_res_free[best].second))
+                best = i;
+        if (best >= 0) {
+            auto e = g_pinned_res_free[best];
+            g_pinned_res_free.erase(g_pinned_res_free.begin() + best);
+            *got = e.second;
+            return e.first;
+        }
+    }
+    const size_t want = std::max<size_t>(bytes, 64 << 10);
+    void *p = nullptr;
+    if (cudaMallocHost(&p, want) != cudaSuccess) return nullptr;
+    *got = want;
+    return p;
+}
+
+void pinned_res_put(void *p, size_t bytes)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mutex);
+    g_pinned_res_free.emplace_back(p, bytes);
+}
+
 }  // namespace
 
 namespace mh {
@@ -218,6 +253,8 @@ struct mh_handle {
     u32 *dGK = nullptr;                   // per gene: uncovered tumors carrying it (incremental rounds)
     u64 *dCov = nullptr;                  // tumors covered by the last round's winner
     int *hState = nullptr;                // pinned: state + frontier counts
+    void *hRes = nullptr;                 // pinned: a solve's results on their way back
+    size_t hRes_bytes = 0;
     GridSync *dSync = nullptr;            // barrier of the persistent solve
     int coop = 0, pgrid = 0;              // cooperative launch supported; persistent grid size
     std::vector<int> m_s;                 // mutated genes per tumor sample (work estimate of a batch)
@@ -241,6 +278,7 @@ struct mh_handle {
         dfree(dGK, stream);
         dfree(dCov, stream);
         pinned_state_put(hState);
+        pinned_res_put(hRes, hRes_bytes);
     }
 };
 
@@ -634,11 +672,40 @@ int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const 
                    int64_t launches, int64_t leaf_launches, mh_result **out, double kernel_ms = 0.0)
 {
     cudaStream_t st = H->stream;
-    int hs[kStateWords];
-    MH_CUDA(cudaMemcpyAsync(hs, H->dState, sizeof hs, cudaMemcpyDeviceToHost, st));
-    MH_CUDA(cudaStreamSynchronize(st));
+    // the state, selections, counters, cuts and diagnostics (the arrays at their
+    // capacity: Nt + 2 rounds) into one pinned buffer, one wait
+    const int cap = std::max(1, H->ws_rounds);
+    const size_t bState = sizeof(int) * kStateWords;
+    const size_t oRes = (bState + 15) & ~(size_t)15;
+    const size_t bRes = sizeof(int) * (size_t)cap * (h + 2);
+    const size_t bCnt = sizeof(u64) * (size_t)cap * h * 2;
+    const size_t bCut = sizeof(u64) * (size_t)cap * h;
+    const size_t oCnt = (oRes + bRes + 15) & ~(size_t)15, oCut = oCnt + bCnt, oWork = oCut + bCut;
+    const size_t need = oWork + sizeof(u64) * kWorkCount;
+    if (H->hRes_bytes < need) {
+        pinned_res_put(H->hRes, H->hRes_bytes);
+        H->hRes_bytes = 0;
+        H->hRes = pinned_res_get(need, &H->hRes_bytes);
+        if (!H->hRes) {
+            H->hRes_bytes = 0;
+            return fail(MH_ENOMEM, "pinned host allocation of the result failed");
+        }
+    }
+    unsigned char *hb = (unsigned char *)H->hRes;
+    cudaError_t e = cudaMemcpyAsync(hb, H->dState, bState, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && H->dRes) e = cudaMemcpyAsync(hb + oRes, H->dRes, bRes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && H->dCnt) e = cudaMemcpyAsync(hb + oCnt, H->dCnt, bCnt, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && H->dCut) e = cudaMemcpyAsync(hb + oCut, H->dCut, bCut, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hb + oWork, H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
+    const int *hs = (const int *)hb;
+    const int *res = (const int *)(hb + oRes);
+    const u64 *cnt = (const u64 *)(hb + oCnt), *cut = (const u64 *)(hb + oCut), *work = (const u64 *)(hb + oWork);
     const int k = hs[0];
     const int rounds = hs[4];
+    if (k < 0 || rounds < 0 || rounds > cap || k > cap) return fail(MH_ECUDA, "inconsistent solve state (k=%d, rounds=%d)", k, rounds);
     mh_result *R = (mh_result *)calloc(1, sizeof(mh_result));
     if (!R) return fail(MH_ENOMEM, "host allocation of the result failed");
     R->h = h;
@@ -654,22 +721,7 @@ int collect_result(mh_handle *H, int h, bool persistent, double solve_ms, const 
         mh_result_free(R);
         return fail(MH_ENOMEM, "host allocation of the result failed");
     }
-    std::vector<int> res((size_t)std::max(1, k) * (h + 2));
-    std::vector<u64> cnt((size_t)std::max(1, rounds) * h * 2);
-    std::vector<u64> work(kWorkCount);
-    cudaError_t e = cudaSuccess;
-    if (k) e = cudaMemcpyAsync(res.data(), H->dRes, sizeof(int) * (size_t)k * (h + 2), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && rounds)
-        e = cudaMemcpyAsync(cnt.data(), H->dCnt, sizeof(u64) * (size_t)rounds * h * 2, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && rounds)
-        e = cudaMemcpyAsync(R->cut, H->dCut, sizeof(u64) * (size_t)rounds * h, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(work.data(), H->dWork, sizeof(u64) * kWorkCount, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) {
-        mh_result_free(R);
-        return fail(MH_ECUDA, "reading the result back failed: %s", cudaGetErrorString(e));
-    }
+    if (rounds) memcpy(R->cut, cut, sizeof(u64) * (size_t)rounds * h);
     for (int i = 0; i < k; ++i) {
         for (int j = 0; j < h; ++j) R->genes[i * h + j] = res[(size_t)i * (h + 2) + j];
         R->tp[i] = res[(size_t)i * (h + 2) + h];
