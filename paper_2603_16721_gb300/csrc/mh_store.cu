@@ -41,24 +41,42 @@ __global__ void k_store_rows(const u64 *bm, int W, int Wt, int Wn, int WTp, int 
 
 // Per tumor s: running popcounts of its sample-major column (CC, GW + 1 entries),
 // its genes in search order (SL, from CT) and in original order (SLo, from the
-// column over the original-order rows).  One thread per tumor.
+// column over the original-order rows).  One warp per tumor: a lane per column
+// word, a warp prefix sum of the words' popcounts placing each word's genes.
+__device__ __forceinline__ int warp_incl_sum(int v, int lane)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    return v;
+}
 __global__ void k_store_lists(const u64 *CT, const u64 *CTo, int Nt, int GW, const u32 *SO, u16 *CC, u16 *SL,
                               u16 *SLo)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= Nt) return;
+    const int lane = threadIdx.x & 31;
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (s >= Nt) return;  // whole warps leave together
     const u64 *col = CT + (size_t)s * GW, *colo = CTo + (size_t)s * GW;
     u16 *cc = CC + (size_t)s * (GW + 1);
-    u32 k = SO[s], ko = SO[s];
+    u32 base = SO[s], baseo = SO[s];
     int run = 0;
-    for (int w = 0; w < GW; ++w) {
-        cc[w] = (u16)run;
-        const u64 x = col[w];
-        run += __popcll(x);
+    for (int w0 = 0; w0 < GW; w0 += 32) {
+        const int w = w0 + lane;
+        const u64 x = w < GW ? col[w] : 0ull, xo = w < GW ? colo[w] : 0ull;
+        const int n = __popcll(x), no = __popcll(xo);
+        const int inc = warp_incl_sum(n, lane), inco = warp_incl_sum(no, lane);
+        if (w < GW) cc[w] = (u16)(run + inc - n);
+        u32 k = base + (u32)(inc - n), ko = baseo + (u32)(inco - no);
         for (u64 y = x; y; y &= y - 1) SL[k++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
-        for (u64 y = colo[w]; y; y &= y - 1) SLo[ko++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        for (u64 y = xo; y; y &= y - 1) SLo[ko++] = (u16)(w * 64 + __ffsll((long long)y) - 1);
+        const int tot = __shfl_sync(0xffffffffu, inc, 31), toto = __shfl_sync(0xffffffffu, inco, 31);
+        run += tot;
+        base += (u32)tot;
+        baseo += (u32)toto;
     }
-    cc[GW] = (u16)run;
+    if (lane == 0) cc[GW] = (u16)run;
 }
 
 // Static depth-1 record of every gene (search order): all its tumors and normals,
@@ -112,7 +130,7 @@ cudaError_t launch_store_build(const StoreBuild &b, cudaStream_t st)
     }
     if (c.Nn > 0) launch_transpose(c, b.N, c.WNp, c.Nn, b.CN, st);
     if (c.Nt > 0)
-        k_store_lists<<<(c.Nt + 127) / 128, 128, 0, st>>>(b.CT, b.CTo, c.Nt, c.GW, b.SO, b.CC, b.SL, b.SLo);
+        k_store_lists<<<(c.Nt + 3) / 4, 128, 0, st>>>(b.CT, b.CTo, c.Nt, c.GW, b.SO, b.CC, b.SL, b.SLo);
     if (c.G > 0) k_store_records<<<(c.G + 127) / 128, 128, 0, st>>>(b.T, b.N, c.G, c.Wt, c.Wn, c.WTp, c.WNp, b.GR, b.GS);
     return cudaGetLastError();
 }
