@@ -284,13 +284,6 @@ struct mh_handle {
 
 namespace {
 
-int popcount_words(const uint64_t *w, int n)
-{
-    int c = 0;
-    for (int i = 0; i < n; ++i) c += __builtin_popcountll(w[i]);
-    return c;
-}
-
 int validate_dims(int32_t G, int32_t Nt, int32_t Nn)
 {
     if (G < 1 || G > kMaxGenes) return fail(MH_EINVAL, "G=%d outside [1, %d]", G, kMaxGenes);
