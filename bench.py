@@ -178,7 +178,8 @@ def solve_roofline(res_list, Nt, Nn, peaks_int, kernel_file="k_solve_c2.md"):
     launch's duration measured here (CUDA events around each cooperative launch on
     the solving stream); peak = the measured LOP3 rate of this GPU (mh_int_peak).
     work_equiv = the paper's per-node cost of the same search (algorithmic_ops,
-    SURVEY-style units: every visited node and scored leaf of the exact counters)
+    units: every visited node and scored leaf of the exact counters, each at the
+    per-node cost of a node-by-node search)
     over the same duration: the rate a kernel doing the paper's work would need;
     the kernel reaches the same counters with far fewer operations, so this is not
     pipe utilisation."""
